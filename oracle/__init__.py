@@ -1,0 +1,248 @@
+"""CPU oracle for the integer matrix power A^n (arXiv 1204.3052).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg (and its ``--impl reference`` arm) may import
+this package.  It shares no code with the CUDA library and imports nothing
+from it; the two meet only through the seeded inputs of
+``paper_1204_3052_gb300.workloads``, which the callers pass in.
+
+Functions and the passage each follows:
+
+* ``gemm_f64``, ``gemm_modp``: the plain triple-loop product (Sec. 4.1), in C.
+* ``matpow_f64(A, n, mode)``: A^n in float64, as mantissa and power-of-two
+  exponent.  ``mode="sqmul"`` is the log2(n)-product method (Sec. 4.3),
+  ``mode="brute"`` the n-1 repeated products (Sec. 4.1, 4.2).
+* ``matpow_modp(A, n, p, mode)``: the same over the integers mod p, exact.
+* ``schedule(n)``: the right-to-left binary level plan and the product count
+  G(n) = floor(log2 n) + popcount(n) - 1 (Sec. 4.3's "log(N)" products).
+* ``rel_frobenius``: the error measure ||X - Y||_F / ||Y||_F in float64.
+* ``stationary(A)``: the limit 1 pi^T of A^n for a positive row-stochastic A,
+  by float64 power iteration (a closed form for large n).
+* ``fp32_sqmul(A, n)``: the same square-and-multiply with every product
+  rounded to float32 (numpy float32 matmul as the product step).  It is an
+  error yardstick, not a parity target: parity unpinned (its output is only
+  used to size the error a float32-class method attains).
+
+Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): Fibonacci, rotation,
+diagonal, nilpotent shift, permutation and identity closed forms; A^(m+k) =
+A^m A^k; exact row sums of stochastic powers and their 1 pi^T limit; brute
+force against square-and-multiply; the mod-p path against Python integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "matpow_oracle.c")
+_LIB = os.path.join(_HERE, "libmatpow_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (IEEE float64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            up = ctypes.POINTER(ctypes.c_uint64)
+            ip = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
+            lib.oracle_gemm_f64.argtypes = [ctypes.c_int, dp, dp, dp]
+            lib.oracle_gemm_f64.restype = None
+            lib.oracle_matpow_f64.argtypes = [ctypes.c_int, dp, ctypes.c_uint64, ctypes.c_int,
+                                              dp, ip, ip]
+            lib.oracle_matpow_f64.restype = ctypes.c_int
+            lib.oracle_gemm_modp.argtypes = [ctypes.c_int, up, up, ctypes.c_uint64, up]
+            lib.oracle_gemm_modp.restype = None
+            lib.oracle_matpow_modp.argtypes = [ctypes.c_int, up, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_int, up, ip]
+            lib.oracle_matpow_modp.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def set_threads(threads: int) -> int:
+    """OpenMP threads for the product loops (<= 0: all cores); returns the count."""
+    return _load().oracle_set_threads(int(threads))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _uptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _square(A) -> int:
+    if A.ndim != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be square")
+    return A.shape[0]
+
+
+def gemm_f64(A, B) -> np.ndarray:
+    """A @ B by the plain triple loop (Sec. 4.1), float64."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    N = _square(A)
+    C = np.empty((N, N), dtype=np.float64)
+    _load().oracle_gemm_f64(N, _dptr(A), _dptr(B), _dptr(C))
+    return C
+
+
+def gemm_modp(A, B, p: int) -> np.ndarray:
+    """(A @ B) mod p by the plain triple loop, exact."""
+    A = np.ascontiguousarray(A, dtype=np.uint64)
+    B = np.ascontiguousarray(B, dtype=np.uint64)
+    N = _square(A)
+    C = np.empty((N, N), dtype=np.uint64)
+    _load().oracle_gemm_modp(N, _uptr(A), _uptr(B), int(p), _uptr(C))
+    return C
+
+
+_MODES = {"sqmul": 0, "brute": 1}
+
+
+def matpow_f64(A, n: int, mode: str = "sqmul"):
+    """A^n as (M, e, gemms): A^n = M * 2**e with max|M| in [0.5, 1) or M = 0."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    N = _square(A)
+    M = np.empty((N, N), dtype=np.float64)
+    e = ctypes.c_int64(0)
+    g = ctypes.c_int64(0)
+    rc = _load().oracle_matpow_f64(N, _dptr(A), int(n), _MODES[mode], _dptr(M),
+                                   ctypes.byref(e), ctypes.byref(g))
+    if rc != 0:
+        raise RuntimeError("oracle_matpow_f64 failed: %d" % rc)
+    return M, int(e.value), int(g.value)
+
+
+def matpow_value(A, n: int, mode: str = "sqmul") -> np.ndarray:
+    """A^n in float64 (M * 2**e; may overflow to inf for huge results)."""
+    M, e, _ = matpow_f64(A, n, mode)
+    return np.ldexp(M, e)
+
+
+def matpow_modp(A, n: int, p: int, mode: str = "sqmul"):
+    """(A^n mod p, gemms) with entries of A in [0, p)."""
+    A = np.ascontiguousarray(A, dtype=np.uint64)
+    N = _square(A)
+    out = np.empty((N, N), dtype=np.uint64)
+    g = ctypes.c_int64(0)
+    rc = _load().oracle_matpow_modp(N, _uptr(A), int(n), int(p), _MODES[mode], _uptr(out),
+                                    ctypes.byref(g))
+    if rc != 0:
+        raise RuntimeError("oracle_matpow_modp failed: %d" % rc)
+    return out, int(g.value)
+
+
+def schedule(n: int):
+    """Right-to-left binary plan for A^n (Sec. 4.3).
+
+    Returns a list of levels; level k is a tuple (multiply, square) of
+    booleans: ``multiply`` when bit k of n is set and a partial result already
+    exists (R <- R * P), ``square`` when a higher bit remains (P <- P * P).
+    The first set bit only copies P into R.
+    """
+    levels = []
+    have_r = False
+    bits = int(n)
+    while bits:
+        mul = False
+        if bits & 1:
+            if have_r:
+                mul = True
+            have_r = True
+        bits >>= 1
+        levels.append((mul, bits != 0))
+    return levels
+
+
+def gemm_count(n: int) -> int:
+    """G(n): products the square-and-multiply method performs for A^n."""
+    return sum(int(m) + int(s) for m, s in schedule(n))
+
+
+def rel_frobenius(M, e, M_ref, e_ref) -> float:
+    """||M*2^e - M_ref*2^e_ref||_F / ||M_ref*2^e_ref||_F, in float64.
+
+    Both sides are brought to the reference's exponent first, so results far
+    outside the float range compare without overflow.
+    """
+    X = np.ldexp(np.asarray(M, dtype=np.float64), int(e) - int(e_ref))
+    Y = np.asarray(M_ref, dtype=np.float64)
+    den = np.linalg.norm(Y)
+    num = np.linalg.norm(X - Y)
+    if den == 0.0:
+        return 0.0 if num == 0.0 else math.inf
+    return float(num / den)
+
+
+def stationary(A, iters: int = 200000, tol: float = 1e-15) -> np.ndarray:
+    """pi with pi^T A = pi^T, sum(pi) = 1, by float64 power iteration.
+
+    For a positive row-stochastic A, A^n -> 1 pi^T as n grows; the rate is
+    |lambda_2|^n.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    N = _square(A)
+    pi = np.full(N, 1.0 / N)
+    for _ in range(iters):
+        nxt = pi @ A
+        nxt /= nxt.sum()
+        if np.max(np.abs(nxt - pi)) <= tol:
+            return nxt
+        pi = nxt
+    return pi
+
+
+def fp32_sqmul(A, n: int):
+    """Square-and-multiply with float32 products (error yardstick; parity unpinned).
+
+    Returns (M, e): A^n ~ M * 2**e, each product rounded to float32 by numpy's
+    float32 matmul and rescaled by an exact power of two.
+    """
+    A = np.asarray(A, dtype=np.float32)
+    N = _square(A)
+
+    def norm(X, e):
+        mx = float(np.max(np.abs(X))) if X.size else 0.0
+        if mx == 0.0 or not math.isfinite(mx):
+            return X, e
+        _, s = math.frexp(mx)
+        return np.ldexp(X, -s).astype(np.float32), e + s
+
+    if n == 0:
+        return np.eye(N, dtype=np.float32), 0
+    P, ep = norm(A.copy(), 0)
+    R, er = None, 0
+    bits = int(n)
+    while bits:
+        if bits & 1:
+            if R is None:
+                R, er = P.copy(), ep
+            else:
+                R, er = norm(np.matmul(R, P), er + ep)
+        bits >>= 1
+        if bits:
+            P, ep = norm(np.matmul(P, P), 2 * ep)
+    return R, er

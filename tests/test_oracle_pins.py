@@ -1,0 +1,317 @@
+"""Pins for the CPU oracle: closed forms, invariants, brute force (CPU only).
+
+Each test fixes the oracle against something other than itself: exact integer
+arithmetic in Python, libm, the definition of the power, or an invariant of
+the mathematics.  The cases are chosen so that a dropped product, a wrong
+exponent bit, a transposed operand or a wrong index fails at least one test.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1204_3052_gb300 import workloads as wl
+
+
+def _fib(m):
+    a, b = 0, 1
+    for _ in range(m):
+        a, b = b, a + b
+    return a
+
+
+def _int_matmul(A, B, p=None):
+    n = len(A)
+    C = [[sum(A[i][k] * B[k][j] for k in range(n)) for j in range(n)] for i in range(n)]
+    if p is not None:
+        C = [[c % p for c in row] for row in C]
+    return C
+
+
+def _int_matpow_brute(A, n, p):
+    N = len(A)
+    R = [[int(i == j) % p for j in range(N)] for i in range(N)]
+    for _ in range(n):
+        R = _int_matmul(R, A, p)
+    return R
+
+
+# ---------------------------------------------------------------- products
+
+def test_gemm_f64_exact_on_small_integers_nonsymmetric():
+    # integer entries: the float64 product is exact, so it must equal Python ints.
+    g = wl.rng(3)
+    for N in (1, 2, 5, 7):
+        A = g.integers(-50, 50, size=(N, N))
+        B = g.integers(-50, 50, size=(N, N))
+        ref = np.array(_int_matmul(A.tolist(), B.tolist()), dtype=np.float64)
+        got = oracle.gemm_f64(A, B)
+        assert np.array_equal(got, ref)  # A@B, not B@A or A^T@B
+
+
+def test_gemm_modp_matches_python_ints():
+    g = wl.rng(4)
+    for p in (2, 7, 65521, 4294967291):
+        for N in (1, 3, 8):
+            A = g.integers(0, p, size=(N, N), dtype=np.uint64)
+            B = g.integers(0, p, size=(N, N), dtype=np.uint64)
+            ref = _int_matmul([[int(x) for x in r] for r in A], [[int(x) for x in r] for r in B], p)
+            got = oracle.gemm_modp(A, B, p)
+            assert got.tolist() == ref
+
+
+# ---------------------------------------------------------------- schedule
+
+@pytest.mark.parametrize("n,G", [(1, 0), (2, 1), (3, 2), (16, 4), (100, 8), (128, 7),
+                                 (1024, 10), (2 ** 20, 20), (2 ** 30, 30),
+                                 (2 ** 30 - 1, 29 + 29)])
+def test_gemm_count_closed_form(n, G):
+    # G(n) = floor(log2 n) + popcount(n) - 1
+    assert oracle.gemm_count(n) == G
+    assert G == (n.bit_length() - 1) + bin(n).count("1") - 1
+
+
+def test_gemm_count_matches_c_oracle():
+    A = wl.gaussian(3, 1)
+    for n in (1, 2, 5, 6, 7, 13, 64, 100, 1000):
+        _, _, g = oracle.matpow_f64(A, n, "sqmul")
+        assert g == oracle.gemm_count(n)
+        _, _, gb = oracle.matpow_f64(A, n, "brute")
+        assert gb == n - 1
+
+
+# ---------------------------------------------------------------- closed forms (float64)
+
+@pytest.mark.parametrize("mode", ["sqmul", "brute"])
+def test_fibonacci_exact(mode):
+    nmax = 77 if mode == "sqmul" else 40
+    for N in (2, 16, 17):
+        A = wl.fibonacci_blocks(N)
+        for n in range(0, nmax + 1):
+            got = oracle.matpow_value(A, n, mode)
+            for b in range(0, N - 1, 2):
+                blk = got[b:b + 2, b:b + 2]
+                want = [[_fib(n + 1), _fib(n)], [_fib(n), _fib(n - 1) if n > 0 else 1]]
+                assert blk.tolist() == want, (N, n, b)
+            if N % 2:
+                assert got[N - 1, N - 1] == 1.0
+            # off-block entries are exactly zero
+            mask = np.ones((N, N), bool)
+            for b in range(0, N - 1, 2):
+                mask[b:b + 2, b:b + 2] = False
+            if N % 2:
+                mask[N - 1, N - 1] = False
+            assert not np.any(got[mask])
+
+
+def test_rotation_closed_form():
+    for theta in (0.1, 1.0, 2.5):
+        R = wl.rotation(theta)
+        for n in (1, 2, 3, 7, 64, 100, 1000, 4097):
+            got = oracle.matpow_value(R, n)
+            want = wl.rotation(n * theta)
+            assert np.max(np.abs(got - want)) <= 8 * n * 2.0 ** -52 + 1e-15, (theta, n)
+
+
+def test_diagonal_matches_libm_pow():
+    g = wl.rng(5)
+    # entries close to 1: every d_i^n stays within float64's range relative to
+    # the largest one, so each entry is checked to its own relative error.
+    d = g.uniform(0.9, 1.1, size=9) * np.where(g.random(9) < 0.5, -1.0, 1.0)
+    A = np.diag(d)
+    for n in (1, 2, 3, 10, 77, 500, 1023):
+        M, e, _ = oracle.matpow_f64(A, n)
+        got = np.diag(np.ldexp(M, e))
+        want = np.array([math.pow(x, n) for x in d])
+        assert np.all(np.abs(got - want) <= 4 * n * 2.0 ** -52 * np.abs(want))
+        off = np.ldexp(M, e) - np.diag(got)
+        assert not np.any(off)
+
+
+def test_diagonal_wide_range_relative_to_largest():
+    # A^n shares one exponent, so entries far below the largest lose bits
+    # (eventually to zero); the error is bounded relative to max|A^n|.
+    g = wl.rng(5)
+    d = g.uniform(0.5, 2.0, size=9) * np.where(g.random(9) < 0.5, -1.0, 1.0)
+    A = np.diag(d)
+    for n in (10, 500, 1023):
+        M, e, _ = oracle.matpow_f64(A, n)
+        want = np.array([math.pow(x, n) for x in d])
+        got = np.diag(M)
+        scale = np.ldexp(1.0, -e)
+        assert np.all(np.abs(got - want * scale) <= 4 * n * 2.0 ** -52 * np.max(np.abs(want * scale)))
+
+
+def test_diagonal_huge_exponent_keeps_range():
+    # 3^(2^30) overflows float64; the mantissa/exponent form must carry it.
+    A = np.diag([3.0, 0.5, 1.0])
+    n = 2 ** 30
+    M, e, _ = oracle.matpow_f64(A, n)
+    # log2 of each diagonal entry of A^n = n*log2(d)
+    l0 = math.log2(abs(M[0, 0])) + e
+    assert abs(l0 - n * math.log2(3.0)) <= 1e-6 * n
+    assert M[1, 1] == 0.0  # 2^-n relative to 3^n underflows the mantissa to zero
+
+
+@pytest.mark.parametrize("mode", ["sqmul", "brute"])
+def test_nilpotent_shift(mode):
+    N = 9
+    S = wl.shift(N)
+    for n in range(0, 13):
+        got = oracle.matpow_value(S, n, mode)
+        want = np.eye(N, k=n) if n < N else np.zeros((N, N))
+        assert np.array_equal(got, want), n  # superdiagonal, not subdiagonal
+
+
+@pytest.mark.parametrize("mode", ["sqmul", "brute"])
+def test_permutation_composed(mode):
+    N = 13
+    P, perm = wl.permutation(N, 7)
+    idx = np.arange(N)
+    for n in range(0, 30):
+        got = oracle.matpow_value(P, n, mode)
+        want = np.zeros((N, N))
+        want[np.arange(N), idx] = 1.0
+        assert np.array_equal(got, want), n
+        idx = perm[idx]  # P^(n+1)[i] = perm(P^n[i])
+
+
+def test_identity_and_zero_power():
+    for N in (1, 4, 33):
+        A = wl.gaussian(N, 2)
+        assert np.array_equal(oracle.matpow_value(A, 0), np.eye(N))
+        assert np.array_equal(oracle.matpow_value(np.eye(N), 12345), np.eye(N))
+
+
+def test_n1_is_copy():
+    A = wl.gaussian(11, 3)
+    assert np.array_equal(oracle.matpow_value(A, 1), A.astype(np.float64))
+
+
+def test_zero_matrix():
+    A = np.zeros((5, 5), np.float32)
+    assert not np.any(oracle.matpow_value(A, 7))
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_power_addition_law():
+    g = wl.rng(6)
+    A = wl.gaussian(12, 4)
+    for _ in range(6):
+        m, k = int(g.integers(1, 200)), int(g.integers(1, 200))
+        Mm, em, _ = oracle.matpow_f64(A, m)
+        Mk, ek, _ = oracle.matpow_f64(A, k)
+        prod = oracle.gemm_f64(Mm, Mk)
+        Ms, es, _ = oracle.matpow_f64(A, m + k)
+        assert oracle.rel_frobenius(prod, em + ek, Ms, es) <= 1e-11
+
+
+@pytest.mark.parametrize("N", [2, 5, 16])
+def test_brute_equals_sqmul(N):
+    A = wl.gaussian(N, N)
+    for n in range(1, 65):
+        Ms, es, _ = oracle.matpow_f64(A, n, "sqmul")
+        Mb, eb, _ = oracle.matpow_f64(A, n, "brute")
+        assert oracle.rel_frobenius(Ms, es, Mb, eb) <= 1e-12 * max(n, 1)
+
+
+def test_exact_stochastic_generator_rows_sum_to_one():
+    for N in (1, 3, 64, 257):
+        A = wl.stochastic_exact(N, 1)
+        assert A.dtype == np.float32 and np.all(A >= 0)
+        # float64 sum of float32 entries with a common 2^-s grid is exact
+        sums = A.astype(np.float64).sum(axis=1)
+        assert np.all(sums == 1.0)
+
+
+def test_stochastic_row_sums_stay_one():
+    A = wl.stochastic_exact(32, 0)
+    for n in (2, 100, 2 ** 10, 2 ** 20):
+        got = oracle.matpow_value(A, n)
+        assert np.max(np.abs(got.sum(axis=1) - 1.0)) <= 1e-12
+
+
+def test_stochastic_limit_is_one_pi_transpose():
+    A = wl.stochastic_exact(64, 0)
+    pi = oracle.stationary(A)
+    want = np.outer(np.ones(64), pi)
+    for n in (100, 2 ** 20):
+        M, e, _ = oracle.matpow_f64(A, n)
+        assert oracle.rel_frobenius(M, e, want, 0) <= 1e-12
+
+
+def test_rel_frobenius_definition():
+    X = np.array([[1.0, 2.0], [3.0, 4.0]])
+    Y = np.array([[1.0, 2.0], [3.0, 5.0]])
+    assert oracle.rel_frobenius(X, 0, Y, 0) == pytest.approx(1.0 / math.sqrt(39.0))
+    # exponent alignment: X*2^3 vs (X*8)*2^0
+    assert oracle.rel_frobenius(X, 3, X * 8.0, 0) == 0.0
+
+
+# ---------------------------------------------------------------- mod p
+
+@pytest.mark.parametrize("p", [2, 3, 101, 65521])
+def test_modp_matches_python_bruteforce(p):
+    g = wl.rng(p)
+    for N in (1, 2, 4, 8):
+        A = g.integers(0, p, size=(N, N), dtype=np.uint64)
+        Ai = [[int(x) for x in r] for r in A]
+        for n in (0, 1, 2, 3, 17, 64, 129, 200):
+            got, _ = oracle.matpow_modp(A, n, p)
+            assert got.tolist() == _int_matpow_brute(Ai, n, p), (p, N, n)
+
+
+def test_modp_fibonacci_huge_power():
+    p = 65521
+    A = wl.fibonacci_blocks(4).astype(np.uint64)
+    for n in (10 ** 6, 2 ** 30, 2 ** 30 - 1, 123456789):
+        got, _ = oracle.matpow_modp(A, n, p)
+        # Python's pow on the 2x2 Fibonacci matrix by a separate exact method:
+        # fast doubling F(2k) = F(k)(2F(k+1) - F(k)), F(2k+1) = F(k)^2 + F(k+1)^2
+        def fd(m):
+            if m == 0:
+                return (0, 1)
+            a, b = fd(m // 2)
+            c = (a * ((2 * b - a) % p)) % p
+            d = (a * a + b * b) % p
+            return (d, (c + d) % p) if m % 2 else (c, d)
+        Fn, Fn1 = fd(n)
+        Fnm1 = (Fn1 - Fn) % p
+        assert got[:2, :2].tolist() == [[Fn1, Fn], [Fn, Fnm1]]
+        assert got[2:, 2:].tolist() == [[Fn1, Fn], [Fn, Fnm1]]
+
+
+def test_modp_diagonal_matches_pow():
+    p = 65521
+    d = [2, 3, 65520, 12345, 0, 1]
+    A = np.diag(np.array(d, dtype=np.uint64))
+    for n in (1, 5, 2 ** 30, 999999937):
+        got, _ = oracle.matpow_modp(A, n, p)
+        assert np.diag(got).tolist() == [pow(x, n, p) for x in d]
+
+
+def test_modp_power_of_power():
+    p = 65521
+    A = wl.modp_uniform(6, p, 9).astype(np.uint64)
+    for m, k in ((3, 5), (7, 11), (64, 2)):
+        Am, _ = oracle.matpow_modp(A, m, p)
+        Amk, _ = oracle.matpow_modp(Am, k, p)
+        direct, _ = oracle.matpow_modp(A, m * k, p)
+        assert np.array_equal(Amk, direct)
+
+
+def test_modp_brute_equals_sqmul():
+    p = 65521
+    A = wl.modp_uniform(16, p, 1).astype(np.uint64)
+    for n in range(0, 65):
+        s, _ = oracle.matpow_modp(A, n, p, "sqmul")
+        b, _ = oracle.matpow_modp(A, n, p, "brute")
+        assert np.array_equal(s, b), n
+
+
+def test_modp_rejects_unreduced_entries():
+    A = np.array([[5, 1], [0, 2]], dtype=np.uint64)
+    with pytest.raises(RuntimeError):
+        oracle.matpow_modp(A, 3, 5)
