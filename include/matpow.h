@@ -1,0 +1,229 @@
+/*
+ * libmatpow — the integer matrix power A^n of a dense square matrix on one
+ * NVIDIA GB300 GPU (sm_103a), by binary square-and-multiply.
+ *
+ * Operation (arXiv 1204.3052): given a dense N x N matrix A and an integer
+ * power n, return A^n.  The paper's CPU method repeats the triple-loop matrix
+ * product of Sec. 4.1 n-1 times; its GPU method (Sec. 4.3) multiplies "log(N)
+ * times" instead of N times, i.e. binary square-and-multiply with
+ * G(n) = floor(log2 n) + popcount(n) - 1 products, and moves the data between
+ * host and device only a few times (Sec. 4.3.8).  This library keeps A, every
+ * partial product and the result on the device and runs each product as a
+ * hand-written CUDA kernel.
+ *
+ * Conventions for every call:
+ *  - Matrices are row-major, N x N, densely packed (leading dimension N).
+ *  - "device" pointers are CUDA global-memory addresses on the plan's device;
+ *    "host" pointers are ordinary process memory.  The caller owns all memory
+ *    it passes in; the library never frees it and keeps no reference after
+ *    the work enqueued by the call has finished.
+ *  - `stream` is a cudaStream_t (NULL: the legacy default stream).  Work is
+ *    enqueued asynchronously on it; argument checks are synchronous.  Errors
+ *    that only the device can see (a float result out of range, an entry >= p)
+ *    are recorded in the plan and returned by matpow_sync().
+ *  - No C++ exception crosses this interface.  Every call returns a
+ *    matpow_status; matpow_last_error() gives a message for the last failure.
+ *  - A plan is not thread-safe: use one plan per host thread.  A server
+ *    (matpow_server_*) is internally locked and may be shared.
+ */
+#ifndef MATPOW_H
+#define MATPOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MATPOW_VERSION 1
+
+typedef enum matpow_status {
+  MATPOW_OK = 0,
+  MATPOW_EINVAL = 1,      /* bad argument (null pointer, N < 0, N > max_n, p out of range, entry >= p) */
+  MATPOW_ENOMEM = 2,      /* device allocation failed or exceeds the plan's workspace limit */
+  MATPOW_ECUDA = 3,       /* a CUDA runtime or driver call failed */
+  MATPOW_EAGAIN = 4,      /* matpow_poll: the request is not finished yet */
+  MATPOW_EBUSY = 5,       /* matpow_submit: the server's admission queue is full */
+  MATPOW_ETIMEDOUT = 6,   /* a bounded wait (host or device) gave up */
+  MATPOW_ERANGE = 7,      /* float result left the float32 range (the mantissa form is exact) */
+  MATPOW_EUNSUPPORTED = 8 /* device is not sm_103 or the option is not supported */
+} matpow_status;
+
+/* Arithmetic of the float path (matpow_f32 / matpow_batched). */
+typedef enum matpow_precision {
+  MATPOW_FP32_SIMT = 0, /* float32 fused multiply-add products on the CUDA cores */
+  MATPOW_BF16 = 1,      /* one bfloat16 tensor-core product per term, float32 accumulation */
+  MATPOW_BF16X3 = 2     /* each operand split x = hi + lo into two bfloat16 parts;
+                           hi*hi + hi*lo + lo*hi tensor-core products, float32 accumulation */
+} matpow_precision;
+
+typedef struct matpow_plan_s* matpow_plan_t;
+
+/* ---- plan ---------------------------------------------------------------- */
+
+/*
+ * Create a plan on CUDA device `device` for matrices of order up to `max_n`
+ * (>= 1) with float arithmetic `precision`.  The plan allocates its device
+ * workspace here (partial products, scale exponents, status words); no later
+ * call allocates device memory except matpow_batched, which grows a plan-owned
+ * descriptor table on first use of a larger batch.  `workspace_bytes` = 0
+ * lets the plan take what max_n needs (matpow_workspace_size); a nonzero
+ * value is an upper limit, and the call fails with MATPOW_ENOMEM if the need
+ * exceeds it.  Fails with MATPOW_EUNSUPPORTED if the device is not sm_103.
+ * On success *plan owns the workspace until matpow_plan_destroy.
+ */
+matpow_status matpow_plan(matpow_plan_t* plan, int max_n, matpow_precision precision,
+                          size_t workspace_bytes, int device);
+
+/* Bytes of device workspace a plan for (max_n, precision) allocates. */
+size_t matpow_workspace_size(int max_n, matpow_precision precision);
+
+/* Free the plan and its workspace (synchronises the plan's device first). */
+matpow_status matpow_plan_destroy(matpow_plan_t plan);
+
+/* NUL-terminated message for the plan's last failure ("" if none).  Valid
+ * until the next call on the plan.  plan may be NULL (last global error). */
+const char* matpow_last_error(matpow_plan_t plan);
+
+/*
+ * Plan options (key, value):
+ *   MATPOW_OPT_GRAPHS   1 (default): replay the level launches of a repeated
+ *                       call from a cached CUDA graph; 0: launch directly.
+ *   MATPOW_OPT_TIMING   1: record CUDA events around every product kernel on
+ *                       the caller's stream (read with matpow_kernel_time); 0 (default).
+ *   MATPOW_OPT_TINY_MAX largest N handled by the single-kernel whole-chain path
+ *                       (0 disables it; default 64).
+ *   MATPOW_OPT_TILE     tensor-core tile override for matpow_f32 (0 = autotuned
+ *                       table; otherwise one of the MATPOW_TILE_* codes).
+ */
+enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4 };
+matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
+
+/* ---- the power ------------------------------------------------------------ */
+
+/*
+ * A^n for float32 A (arXiv 1204.3052, Sec. 4.3: square-and-multiply, about
+ * log2(n) products; the product itself is Sec. 4.1's c_ij = sum_k a_ik b_kj).
+ *   dA          device, N*N float32, row-major; read only.
+ *   N           matrix order, 0 <= N <= max_n (N = 0: nothing to do).
+ *   n           power, any uint64 (n = 0: identity, n = 1: copy of A).
+ *   dOut        device, N*N float32; may alias dA.
+ *   dLog2Scale  device int64 or NULL.  If non-NULL the result is returned in
+ *               mantissa form: dOut holds M and *dLog2Scale holds e with
+ *               A^n = M * 2^e (max|M| <= N; never overflows).  If NULL, dOut
+ *               holds A^n rounded to float32 (rescaled in float64 on the
+ *               device); entries beyond the float32 range become +-inf or 0
+ *               and matpow_sync() then returns MATPOW_ERANGE.
+ *   stream      cudaStream_t.
+ * Intermediate powers are kept with a per-matrix power-of-two exponent so
+ * that n up to 2^64-1 never overflows.  Asynchronous.
+ */
+matpow_status matpow_f32(matpow_plan_t plan, const float* dA, int N, uint64_t n, float* dOut,
+                         int64_t* dLog2Scale, void* stream);
+
+/*
+ * A^n mod p for integer A (exact; the same square-and-multiply over Z/pZ).
+ *   dA     device, N*N uint32 with every entry in [0, p); read only.
+ *   p      modulus, 2 <= p <= 65536.
+ *   dOut   device, N*N uint32, entries in [0, p); may alias dA.
+ * An entry >= p is detected on the device: dOut is then unspecified and
+ * matpow_sync() returns MATPOW_EINVAL.  Bit-exact.  Asynchronous.
+ */
+matpow_status matpow_mod_p(matpow_plan_t plan, const uint32_t* dA, int N, uint64_t n, uint32_t p,
+                           uint32_t* dOut, void* stream);
+
+/*
+ * `count` independent float32 powers A_i^(n_i) of uneven orders, run level by
+ * level: all products of one squaring level of all matrices go into one
+ * grouped kernel launch (Sec. 4.3's method applied to a batch).
+ *   dA, dOut     host arrays of `count` device pointers (N_i*N_i float32 each;
+ *                dOut[i] may alias dA[i]).
+ *   N, n         host arrays of `count` orders (0 <= N_i <= max_n) and powers.
+ *   dLog2Scale   device array of `count` int64, or NULL (as in matpow_f32).
+ * Asynchronous; the host arrays may be reused as soon as the call returns.
+ */
+matpow_status matpow_batched(matpow_plan_t plan, int count, const float* const* dA, const int* N,
+                             const uint64_t* n, float* const* dOut, int64_t* dLog2Scale,
+                             void* stream);
+
+/*
+ * Wait for the work enqueued on `stream` and return the first deferred
+ * device status of the plan since the last matpow_sync (MATPOW_OK,
+ * MATPOW_ERANGE, MATPOW_EINVAL for an entry >= p), then clear it.
+ */
+matpow_status matpow_sync(matpow_plan_t plan, void* stream);
+
+/* G(n) = floor(log2 n) + popcount(n) - 1 (0 for n <= 1): products that A^n takes. */
+int matpow_gemm_count(uint64_t n);
+
+/*
+ * Timing of product kernels recorded under MATPOW_OPT_TIMING since the last
+ * reset: kernel class `kind` (MATPOW_KERNEL_*), number of launches, total
+ * milliseconds (CUDA events on the caller's stream; synchronises it), and the
+ * algorithmic work those launches did (2*N^3 per product, summed) in flop.
+ * reset != 0 clears the record afterwards.
+ */
+enum { MATPOW_KERNEL_SIMT = 0, MATPOW_KERNEL_TC = 1, MATPOW_KERNEL_TINY = 2, MATPOW_KERNEL_MODP = 3,
+       MATPOW_KERNEL_AUX = 4, MATPOW_KERNEL_KINDS = 5 };
+matpow_status matpow_kernel_time(matpow_plan_t plan, int kind, int64_t* launches, double* total_ms,
+                                 double* flop, int reset);
+
+/* Kernel launches the plan has issued since creation (all kernels, cumulative). */
+int64_t matpow_launch_count(matpow_plan_t plan);
+
+/* ---- serving ---------------------------------------------------------------- */
+
+/*
+ * A request server: continuous batching of independent A^n requests on one
+ * device (the paper's method run for many users at once).  Requests are
+ * admitted while their device footprint fits `hbm_budget_bytes` and fewer
+ * than `max_inflight` are running; each scheduler step groups the next
+ * product of every admitted request into one launch, so requests that
+ * arrive later join the running batch at their own first level.
+ */
+typedef struct matpow_server_s* matpow_server_t;
+
+typedef struct matpow_server_desc {
+  int device;
+  int max_n;                  /* largest order accepted */
+  matpow_precision precision; /* float requests */
+  size_t hbm_budget_bytes;    /* device bytes for in-flight partial products */
+  int max_inflight;           /* admitted requests at most */
+  int max_queue;              /* queued (not yet admitted) requests at most */
+} matpow_server_desc;
+
+typedef struct matpow_request {
+  int N;               /* order, 1 <= N <= max_n */
+  uint64_t n;          /* power */
+  int kind;            /* 0: float32 A^n; 1: A^n mod p */
+  uint32_t p;          /* modulus for kind 1 (2 <= p <= 65536) */
+  const void* dA;      /* device input (float32 or uint32), read only, kept valid until done */
+  void* dOut;          /* device output (float32 or uint32) */
+  int64_t* dLog2Scale; /* kind 0: device int64 or NULL, as in matpow_f32 */
+} matpow_request;
+
+matpow_status matpow_server_create(matpow_server_t* server, const matpow_server_desc* desc);
+
+/* Queue a request (non-blocking).  *ticket identifies it for matpow_poll.
+ * MATPOW_EBUSY if the queue holds max_queue requests; MATPOW_EINVAL for a
+ * bad request. */
+matpow_status matpow_submit(matpow_server_t server, const matpow_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us microseconds for request `ticket`: MATPOW_OK once its
+ * output is complete on the device (the ticket is then retired),
+ * MATPOW_EAGAIN / MATPOW_ETIMEDOUT if not finished (EAGAIN when
+ * timeout_us == 0), or the request's error status. */
+matpow_status matpow_poll(matpow_server_t server, uint64_t ticket, uint32_t timeout_us);
+
+/* Latency record of retired requests: submit-to-completion microseconds for
+ * up to `cap` requests (oldest first); returns how many were written. */
+int64_t matpow_server_latencies(matpow_server_t server, double* us, int64_t cap);
+
+/* Stop the scheduler, wait for in-flight work and free the server. */
+matpow_status matpow_server_destroy(matpow_server_t server);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MATPOW_H */

@@ -1,0 +1,255 @@
+// matpow_batched: many independent powers A_i^(n_i) of uneven orders.
+//
+// Small matrices (N <= the plan's whole-chain limit) run their entire chain
+// in one CTA each, all in a single launch.  Larger ones are prepared by two
+// grouped kernels (absmax, conversion) and then advanced level by level: the
+// products of one squaring level of every matrix (arXiv 1204.3052 Sec. 4.3)
+// form one grouped launch over a device table of product descriptors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "plan.h"
+
+using namespace mp;
+
+#define CK(plan, call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(plan, e_, #call); \
+  } while (0)
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+void mp::batch_free(matpow_plan_s* p) {
+  BatchState& b = p->batch;
+  if (b.ws) cudaFree(b.ws);
+  if (b.scales) cudaFree(b.scales);
+  if (b.descs) cudaFree(b.descs);
+  if (b.h_descs) cudaFreeHost(b.h_descs);
+  if (b.staged) cudaEventDestroy(b.staged);
+  b = BatchState();
+}
+
+static matpow_status grow(matpow_plan_s* p, void** ptr, size_t* cap, size_t need, bool host) {
+  if (*cap >= need) return MATPOW_OK;
+  size_t n = std::max(need, *cap * 3 / 2);
+  void* q = nullptr;
+  cudaError_t e;
+  if (host) {
+    if (p->batch.staged) cudaEventSynchronize(p->batch.staged);
+    e = cudaMallocHost(&q, n);
+  } else {
+    cudaDeviceSynchronize();  // the old array may still be in use by queued work
+    e = cudaMalloc(&q, n);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, MATPOW_ENOMEM, "matpow_batched: allocation of %zu bytes failed", n);
+  }
+  if (*ptr) {
+    if (host) cudaFreeHost(*ptr); else cudaFree(*ptr);
+  }
+  *ptr = q;
+  *cap = n;
+  return MATPOW_OK;
+}
+
+extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float* const* dA,
+                                        const int* N, const uint64_t* n, float* const* dOut,
+                                        int64_t* dLog2Scale, void* stream) {
+  if (!p) return fail(nullptr, MATPOW_EINVAL, "matpow_batched: plan is NULL");
+  if (count < 0) return fail(p, MATPOW_EINVAL, "matpow_batched: count < 0");
+  if (count == 0) return MATPOW_OK;
+  if (!dA || !N || !n || !dOut) return fail(p, MATPOW_EINVAL, "matpow_batched: NULL array");
+  for (int i = 0; i < count; ++i) {
+    if (N[i] < 0 || N[i] > p->max_n)
+      return fail(p, MATPOW_EINVAL, "matpow_batched: N[%d]=%d outside [0, %d]", i, N[i], p->max_n);
+    if (N[i] > 0 && (!dA[i] || !dOut[i]))
+      return fail(p, MATPOW_EINVAL, "matpow_batched: NULL matrix pointer at %d", i);
+    if (((uintptr_t)dA[i] & 3) || ((uintptr_t)dOut[i] & 3))
+      return fail(p, MATPOW_EINVAL, "matpow_batched: misaligned pointer at %d", i);
+  }
+  if ((uintptr_t)dLog2Scale & 7) return fail(p, MATPOW_EINVAL, "matpow_batched: misaligned dLog2Scale");
+  int prev = 0;
+  cudaGetDevice(&prev);
+  if (prev != p->device) cudaSetDevice(p->device);
+  struct Restore {
+    int d;
+    ~Restore() { cudaSetDevice(d); }
+  } restore{prev};
+  cudaStream_t s = (cudaStream_t)stream;
+  const int fmt = float_fmt(p->prec);
+  const bool tc = p->prec != MATPOW_FP32_SIMT;
+
+  // ---- classify
+  std::vector<TinyDesc> tiny;
+  std::vector<PrepDesc> prep;
+  struct Big {
+    int i;
+    int slot0;
+    size_t off;  // byte offset of this matrix's four buffers in the batch workspace
+    size_t mb;   // bytes of one buffer
+    std::vector<LevelOps> levels;
+  };
+  std::vector<Big> big;
+  size_t ws_need = 0;
+  int slots = 0;
+  for (int i = 0; i < count; ++i) {
+    if (N[i] == 0) continue;
+    long long* lg = dLog2Scale ? (long long*)(dLog2Scale + i) : nullptr;
+    if (N[i] <= p->tiny_max) {
+      tiny.push_back({dA[i], dOut[i], lg, (unsigned long long)n[i], N[i], 0});
+      continue;
+    }
+    if (n[i] <= 1) {
+      PrepDesc d{};
+      d.A = dA[i];
+      d.dst = dOut[i];
+      d.log2 = lg;
+      d.N = N[i];
+      d.kind = n[i] == 0 ? 1 : 2;
+      prep.push_back(d);
+      continue;
+    }
+    Big b;
+    b.i = i;
+    b.slot0 = slots;
+    b.mb = matrix_bytes(N[i], fmt);
+    b.off = ws_need;
+    ws_need += 4 * b.mb;
+    slots += 2 + matpow_gemm_count(n[i]);
+    build_schedule(n[i], &b.levels);
+    PrepDesc d{};
+    d.A = dA[i];
+    d.N = N[i];
+    d.fmt = fmt;
+    d.plane = plane_offset_elems(N[i], fmt);
+    d.slot_raw = b.slot0;
+    d.slot_stored = b.slot0 + 1;
+    d.kind = 0;
+    prep.push_back(d);
+    big.push_back(std::move(b));
+  }
+  matpow_status st;
+  if ((st = grow(p, &p->batch.ws, &p->batch.ws_bytes, std::max<size_t>(ws_need, 1), false))) return st;
+  size_t sc_bytes = sizeof(Scale) * std::max(slots, 1);
+  if ((st = grow(p, (void**)&p->batch.scales, &p->batch.scale_cap, sc_bytes, false))) return st;
+  // prep descriptors point into the workspace
+  {
+    size_t bi = 0;
+    for (auto& d : prep)
+      if (d.kind == 0) {
+        d.dst = (char*)p->batch.ws + big[bi].off;
+        ++bi;
+      }
+  }
+  // ---- product descriptors per level
+  int max_levels = 0;
+  for (auto& b : big) max_levels = std::max(max_levels, (int)b.levels.size());
+  std::vector<GemmDesc> gd;
+  std::vector<int> lvl_begin, lvl_count, lvl_tiles;
+  for (int L = 0; L < max_levels; ++L) {
+    int begin = (int)gd.size(), tiles = 0;
+    for (auto& b : big) {
+      if (L >= (int)b.levels.size()) continue;
+      const int Ni = N[b.i];
+      const bool final_level = L + 1 == (int)b.levels.size();
+      const LevelOps& lv = b.levels[L];
+      for (size_t k = 0; k < lv.ops.size(); ++k) {
+        const Op& op = lv.ops[k];
+        const bool last = final_level && k + 1 == lv.ops.size();
+        char* base = (char*)p->batch.ws + b.off;
+        GemmDesc d{};
+        d.X = base + op.xb * b.mb;
+        d.Y = base + op.yb * b.mb;
+        d.C = last ? nullptr : base + op.cb * b.mb;
+        d.out = last ? (void*)dOut[b.i] : nullptr;
+        d.out_log2 = last && dLog2Scale ? (long long*)(dLog2Scale + b.i) : nullptr;
+        d.plane = plane_offset_elems(Ni, fmt);
+        d.N = Ni;
+        d.ld = ld_for(Ni, fmt);
+        d.sx = b.slot0 + op.sx;
+        d.sy = b.slot0 + op.sy;
+        d.sc = b.slot0 + op.sc;
+        d.mode = last ? (dLog2Scale ? OUT_USER_MANT : OUT_USER_VALUE) : OUT_INTERNAL;
+        d.tile_begin = tiles;
+        if (tc) {
+          int nt = 0;
+          if ((st = tc_fill_desc(p, &d, &nt))) return st;
+          tiles += nt;
+        } else {
+          d.tiles_n = (Ni + simt_tile_edge() - 1) / simt_tile_edge();
+          tiles += d.tiles_n * d.tiles_n;
+        }
+        gd.push_back(d);
+      }
+    }
+    lvl_begin.push_back(begin);
+    lvl_count.push_back((int)gd.size() - begin);
+    lvl_tiles.push_back(tiles);
+  }
+  // prep CTAs: about one CTA per 16K entries
+  int prep_blocks = 0;
+  for (auto& d : prep) {
+    size_t e = (size_t)d.N * d.N;
+    d.blocks = (int)std::min<size_t>(std::max<size_t>((e + 16383) / 16384, 1), 1024);
+    d.block_begin = prep_blocks;
+    prep_blocks += d.blocks;
+  }
+  // ---- stage the three tables in one pinned buffer, upload once
+  size_t o_tiny = 0;
+  size_t o_prep = align_up(o_tiny + tiny.size() * sizeof(TinyDesc), 256);
+  size_t o_gd = align_up(o_prep + prep.size() * sizeof(PrepDesc), 256);
+  size_t total = std::max<size_t>(align_up(o_gd + gd.size() * sizeof(GemmDesc), 256), 256);
+  if ((st = grow(p, &p->batch.h_descs, &p->batch.h_desc_bytes, total, true))) return st;
+  if ((st = grow(p, &p->batch.descs, &p->batch.desc_bytes, total, false))) return st;
+  if (!p->batch.staged) CK(p, cudaEventCreateWithFlags(&p->batch.staged, cudaEventDisableTiming));
+  CK(p, cudaEventSynchronize(p->batch.staged));  // previous upload finished reading h_descs
+  char* h = (char*)p->batch.h_descs;
+  if (!tiny.empty()) memcpy(h + o_tiny, tiny.data(), tiny.size() * sizeof(TinyDesc));
+  if (!prep.empty()) memcpy(h + o_prep, prep.data(), prep.size() * sizeof(PrepDesc));
+  if (!gd.empty()) memcpy(h + o_gd, gd.data(), gd.size() * sizeof(GemmDesc));
+  CK(p, cudaMemcpyAsync(p->batch.descs, h, total, cudaMemcpyHostToDevice, s));
+  CK(p, cudaEventRecord(p->batch.staged, s));
+  char* dd = (char*)p->batch.descs;
+  cudaEvent_t ev;
+  // ---- enqueue
+  if (!tiny.empty()) {
+    double flop = 0;
+    for (auto& t : tiny) flop += 2.0 * t.N * (double)t.N * t.N * matpow_gemm_count(t.n);
+    timed_begin(p, s, &ev);
+    CK(p, launch_tiny_group((const TinyDesc*)(dd + o_tiny), (int)tiny.size(), p->status, s));
+    timed_end(p, s, ev, MATPOW_KERNEL_TINY, flop);
+    p->launches++;
+  }
+  if (!prep.empty()) {
+    if (slots) CK(p, cudaMemsetAsync(p->batch.scales, 0, sizeof(Scale) * slots, s));
+    const PrepDesc* pd = (const PrepDesc*)(dd + o_prep);
+    CK(p, launch_prep_absmax_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, p->status, s));
+    CK(p, launch_prep_convert_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, s));
+    p->launches += 2;
+  }
+  for (int L = 0; L < max_levels; ++L) {
+    if (!lvl_count[L]) continue;
+    const GemmDesc* g = (const GemmDesc*)(dd + o_gd) + lvl_begin[L];
+    double flop = 0;
+    for (int k = 0; k < lvl_count[L]; ++k) {
+      const GemmDesc& d = gd[lvl_begin[L] + k];
+      flop += 2.0 * d.N * (double)d.N * d.N;
+    }
+    timed_begin(p, s, &ev);
+    if (tc) {
+      if ((st = tc_launch_group(p, g, lvl_count[L], lvl_tiles[L], p->batch.scales, s))) return st;
+      timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
+    } else {
+      CK(p, launch_simt_group(g, lvl_count[L], lvl_tiles[L], p->batch.scales, p->status, s));
+      timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
+    }
+    p->launches++;
+  }
+  return MATPOW_OK;
+}

@@ -1,0 +1,209 @@
+// Auxiliary kernels around the products: input absmax, conversion of A into
+// the stored format (with an exact power-of-two normalisation), identity and
+// copy for n = 0 and n = 1.
+//
+// These run once per power (arXiv 1204.3052 Sec. 4.3.8: A is moved once and
+// every partial product stays on the device), so they are plain grid-stride
+// HBM-bound kernels.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace mp {
+
+static int grid_for(size_t elems, int threads) {
+  size_t b = (elems + threads - 1) / threads;
+  int cap = 152 * 8;  // 152 SMs x 8 resident CTAs of 256 threads
+  return (int)(b < (size_t)cap ? (b == 0 ? 1 : b) : cap);
+}
+
+__global__ void absmax_f32_kernel(const float* __restrict__ A, size_t total, Scale* slot,
+                                  unsigned* status) {
+  float m = 0.0f;
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float v = A[i];
+    bad |= !isfinite(v);
+    m = fmaxf(m, fabsf(v));
+  }
+  m = warp_max(m);
+  __shared__ float red[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = m;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_BADINPUT);
+  if (w == 0) {
+    m = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+    m = warp_max(m);
+    if (lane == 0 && m > 0.0f) atomicMax(&slot->maxbits, __float_as_uint(m));
+  }
+}
+
+cudaError_t launch_absmax_f32(const float* A, int N, Scale* slot, unsigned* status,
+                              cudaStream_t s) {
+  size_t total = (size_t)N * N;
+  absmax_f32_kernel<<<grid_for(total, 256), 256, 0, s>>>(A, total, slot, status);
+  return cudaGetLastError();
+}
+
+// dst <- A * 2^-s in format `fmt`, s from raw->maxbits; stored->E = s and
+// stored->maxbits = max|A| * 2^-s.  Padding columns [N, ld) are zeroed.
+__global__ void convert_f32_kernel(const float* __restrict__ A, int N, int ld, const Scale* raw,
+                                   Scale* stored, int fmt, void* dst, long long plane) {
+  const int s = scale_exp_from_bits(raw->maxbits);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    stored->E = s;
+    stored->maxbits = raw->maxbits ? __float_as_uint(mul_pow2(__uint_as_float(raw->maxbits), -s)) : 0u;
+  }
+  size_t total = (size_t)N * ld;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    size_t r = i / ld;
+    int c = (int)(i - r * ld);
+    float v = c < N ? mul_pow2(A[r * N + c], -s) : 0.0f;
+    if (fmt == FMT_F32) {
+      ((float*)dst)[i] = v;
+    } else {
+      __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      ((__nv_bfloat16*)dst)[i] = hi;
+      if (fmt == FMT_PLANES) {
+        __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        ((__nv_bfloat16*)dst)[plane + i] = lo;
+      }
+    }
+  }
+}
+
+cudaError_t launch_convert_f32(const float* A, int N, const Scale* raw, Scale* stored, int fmt,
+                               void* dst, long long plane, cudaStream_t s) {
+  int ld = ld_for(N, fmt);
+  convert_f32_kernel<<<grid_for((size_t)N * ld, 256), 256, 0, s>>>(A, N, ld, raw, stored, fmt, dst,
+                                                                   plane);
+  return cudaGetLastError();
+}
+
+__global__ void identity_kernel(void* out, int N, int is_u32, unsigned one, long long* log2) {
+  size_t total = (size_t)N * N;
+  if (log2 && blockIdx.x == 0 && threadIdx.x == 0) *log2 = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    size_t r = i / N, c = i - r * N;
+    if (is_u32)
+      ((unsigned*)out)[i] = r == c ? one : 0u;
+    else
+      ((float*)out)[i] = r == c ? 1.0f : 0.0f;
+  }
+}
+
+cudaError_t launch_identity(void* out, int N, int is_u32, unsigned one, long long* log2,
+                            cudaStream_t s) {
+  identity_kernel<<<grid_for((size_t)N * N, 256), 256, 0, s>>>(out, N, is_u32, one, log2);
+  return cudaGetLastError();
+}
+
+// out <- A (4-byte elements).  Aliasing out == A is a no-op copy.
+__global__ void copy_kernel(const unsigned* __restrict__ A, unsigned* out, size_t total,
+                            long long* log2) {
+  if (log2 && blockIdx.x == 0 && threadIdx.x == 0) *log2 = 0;
+  if ((const void*)A == (const void*)out) return;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = A[i];
+}
+
+cudaError_t launch_copy(const void* A, void* out, int N, long long* log2, cudaStream_t s) {
+  size_t total = (size_t)N * N;
+  copy_kernel<<<grid_for(total, 256), 256, 0, s>>>((const unsigned*)A, (unsigned*)out, total, log2);
+  return cudaGetLastError();
+}
+
+}  // namespace mp
+
+namespace mp {
+
+__device__ __forceinline__ int find_desc(const PrepDesc* __restrict__ d, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (d[mid].block_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void prep_absmax_group_kernel(const PrepDesc* __restrict__ descs, int count,
+                                         Scale* scales, unsigned* status) {
+  const PrepDesc d = descs[find_desc(descs, count, blockIdx.x)];
+  if (d.kind != 0) return;
+  const int b = blockIdx.x - d.block_begin;
+  const size_t total = (size_t)d.N * d.N;
+  float m = 0.0f;
+  bool bad = false;
+  for (size_t i = b * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)d.blocks * blockDim.x) {
+    float v = d.A[i];
+    bad |= !isfinite(v);
+    m = fmaxf(m, fabsf(v));
+  }
+  m = warp_max(m);
+  __shared__ float red[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = m;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_BADINPUT);
+  if (w == 0) {
+    m = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+    m = warp_max(m);
+    if (lane == 0 && m > 0.0f) atomicMax(&scales[d.slot_raw].maxbits, __float_as_uint(m));
+  }
+}
+
+__global__ void prep_convert_group_kernel(const PrepDesc* __restrict__ descs, int count,
+                                          Scale* scales) {
+  const PrepDesc d = descs[find_desc(descs, count, blockIdx.x)];
+  const int b = blockIdx.x - d.block_begin;
+  const int N = d.N;
+  if (d.kind == 1 || d.kind == 2) {  // trivial powers straight into the user's output
+    if (d.log2 && b == 0 && threadIdx.x == 0) *d.log2 = 0;
+    const size_t total = (size_t)N * N;
+    float* out = (float*)d.dst;
+    for (size_t i = b * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)d.blocks * blockDim.x) {
+      size_t r = i / N, c = i - r * N;
+      out[i] = d.kind == 1 ? (r == c ? 1.0f : 0.0f) : d.A[i];
+    }
+    return;
+  }
+  const Scale* raw = &scales[d.slot_raw];
+  Scale* stored = &scales[d.slot_stored];
+  const int s = scale_exp_from_bits(raw->maxbits);
+  if (b == 0 && threadIdx.x == 0) {
+    stored->E = s;
+    stored->maxbits = raw->maxbits ? __float_as_uint(mul_pow2(__uint_as_float(raw->maxbits), -s)) : 0u;
+  }
+  const int ld = ld_for(N, d.fmt);
+  const size_t total = (size_t)N * ld;
+  for (size_t i = b * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)d.blocks * blockDim.x) {
+    size_t r = i / ld;
+    int c = (int)(i - r * ld);
+    float v = c < N ? mul_pow2(d.A[r * N + c], -s) : 0.0f;
+    if (d.fmt == FMT_F32) {
+      ((float*)d.dst)[i] = v;
+    } else {
+      __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      ((__nv_bfloat16*)d.dst)[i] = hi;
+      if (d.fmt == FMT_PLANES)
+        ((__nv_bfloat16*)d.dst)[d.plane + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+  }
+}
+
+cudaError_t launch_prep_absmax_group(const PrepDesc* d, int count, int blocks, Scale* scales,
+                                     unsigned* status, cudaStream_t s) {
+  prep_absmax_group_kernel<<<blocks, 256, 0, s>>>(d, count, scales, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_convert_group(const PrepDesc* d, int count, int blocks, Scale* scales,
+                                      cudaStream_t s) {
+  prep_convert_group_kernel<<<blocks, 256, 0, s>>>(d, count, scales);
+  return cudaGetLastError();
+}
+
+}  // namespace mp

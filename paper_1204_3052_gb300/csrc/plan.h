@@ -1,0 +1,121 @@
+// Host-side plan state of libmatpow (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mp {
+
+constexpr int kSingleSlots = 256;  // scale slots of one power: 2 + G(n) <= 2 + 126
+constexpr size_t kMaxGraphs = 16;
+
+// One product of the schedule: C(cb, sc) = X(xb, sx) * Y(yb, sy).
+struct Op {
+  int xb, yb, cb;
+  int sx, sy, sc;
+  bool square;
+};
+struct LevelOps {
+  std::vector<Op> ops;  // one or two products that read the same P
+};
+void build_schedule(uint64_t n, std::vector<LevelOps>* levels);
+
+struct GraphKey {
+  int kind;  // 0 float, 1 mod p
+  const void* A;
+  void* out;
+  void* log2;
+  int N;
+  uint64_t n;
+  uint32_t p;
+  bool operator==(const GraphKey& o) const {
+    return kind == o.kind && A == o.A && out == o.out && log2 == o.log2 && N == o.N && n == o.n &&
+           p == o.p;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+  uint64_t stamp = 0;
+};
+
+struct KernelTiming {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<double> pending_flop;
+  int64_t launches = 0;
+  double total_ms = 0.0;
+  double flop = 0.0;
+};
+
+// Device arrays of matpow_batched, grown on demand and kept by the plan.
+struct BatchState {
+  void* ws = nullptr;           // per-matrix partial products
+  size_t ws_bytes = 0;
+  Scale* scales = nullptr;      // per-matrix scale slots
+  size_t scale_cap = 0;
+  void* descs = nullptr;        // GemmDesc / TinyDesc tables (device)
+  size_t desc_bytes = 0;
+  void* h_descs = nullptr;      // pinned staging for the tables
+  size_t h_desc_bytes = 0;
+  cudaEvent_t staged = nullptr; // the last upload from h_descs has been consumed
+};
+
+}  // namespace mp
+
+struct matpow_plan_s {
+  int device = 0;
+  int max_n = 0;
+  matpow_precision prec = MATPOW_FP32_SIMT;
+  int num_sms = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  size_t buf_bytes = 0;
+  mp::Scale* scales = nullptr;
+  unsigned* status = nullptr;
+  unsigned* h_status = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::string err;
+  // options
+  bool use_graphs = true;
+  bool timing_on = false;
+  int tiny_max = 64;
+  int tile_override = 0;
+  // graphs
+  std::vector<mp::GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  // timing
+  mp::KernelTiming timing[MATPOW_KERNEL_KINDS];
+  std::vector<cudaEvent_t> event_pool;
+  int64_t launches = 0;
+  // batching
+  mp::BatchState batch;
+  // tensor-core path state (tensor maps etc.), owned by k_tc.cu
+  void* tc = nullptr;
+};
+
+namespace mp {
+matpow_status fail(matpow_plan_s* plan, matpow_status st, const char* fmt, ...);
+matpow_status cuda_fail(matpow_plan_s* plan, cudaError_t e, const char* what);
+size_t matrix_bytes(int N, int fmt);
+long long plane_offset_elems(int N, int fmt);
+int float_fmt(matpow_precision p);
+cudaEvent_t take_event(matpow_plan_s* p);
+void timed_begin(matpow_plan_s* p, cudaStream_t s, cudaEvent_t* ev);
+void timed_end(matpow_plan_s* p, cudaStream_t s, cudaEvent_t ev, int kind, double flop);
+void batch_free(matpow_plan_s* p);
+// tensor-core path (k_tc.cu)
+cudaError_t tc_init(matpow_plan_s* p);  // kernel attributes, driver entry points
+void tc_free(matpow_plan_s* p);
+// Fill the tensor-core fields of d (tiles_n, tile count in *ntiles).
+matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc* d, int* ntiles);
+matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s);
+matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
+                              Scale* scales, cudaStream_t s);
+}  // namespace mp

@@ -1,0 +1,215 @@
+"""Float path parity: libmatpow (GPU) against the float64 CPU oracle.
+
+Every case runs the same seeded input through both sides and compares the
+whole result (rel. Frobenius error in float64, after aligning exponents), or
+element by element where the answer is exact (integers, permutations).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import float_tol, gate, to_dev
+from paper_1204_3052_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp32"]
+
+
+@pytest.fixture(scope="module")
+def plans():
+    from paper_1204_3052_gb300 import matpow as mpw
+    out = {pr: mpw.Plan(1024, pr) for pr in PRECS}
+    yield out
+    for p in out.values():
+        p.close()
+
+
+def run(plan, A, n, mantissa=True):
+    import torch
+    dA = to_dev(A)
+    if mantissa:
+        out, lg = plan.f32(dA, n, mantissa=True)
+        plan.check()
+        return out.cpu().numpy().astype(np.float64), int(lg.item())
+    out = plan.f32(dA, n)
+    st = plan.sync()
+    return out.cpu().numpy().astype(np.float64), st
+
+
+def floor_rel(A, n, M, e):
+    Mf, ef = oracle.fp32_sqmul(A, n)
+    return oracle.rel_frobenius(Mf, ef, M, e)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_stochastic_64_n100(plans, prec):
+    A = wl.stochastic_exact(64, 0)
+    M, e, _ = oracle.matpow_f64(A, 100)
+    got, ge = run(plans[prec], A, 100)
+    err = oracle.rel_frobenius(got, ge, M, e)
+    assert err <= float_tol(100), err
+    rows = np.ldexp(got, ge).sum(axis=1)
+    assert np.max(np.abs(rows - 1.0)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [2, 16, 128, 1024])
+def test_config2_gaussian_512(plans, prec, n):
+    A = wl.gaussian(512, 0)
+    M, e, _ = oracle.matpow_f64(A, n)
+    got, ge = run(plans[prec], A, n)
+    err = oracle.rel_frobenius(got, ge, M, e)
+    bound = gate(n, floor_rel(A, n, M, e))
+    print("prec=%s n=%d rel_F=%.3e bound=%.3e" % (prec, n, err, bound))
+    assert err <= bound, (err, bound)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 16, 17, 31, 33, 63, 64, 65, 100, 127, 128, 129, 200, 257, 383])
+def test_sizes_span_tiles_and_ragged_tails(plans, prec, N):
+    A = wl.gaussian(N, N)
+    for n in (2, 3, 7, 64, 77):
+        M, e, _ = oracle.matpow_f64(A, n)
+        got, ge = run(plans[prec], A, n)
+        err = oracle.rel_frobenius(got, ge, M, e)
+        bound = gate(n, floor_rel(A, n, M, e))
+        assert err <= bound, (N, n, err, bound)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_n0_identity_and_n1_copy(plans, prec):
+    for N in (1, 7, 64, 100):
+        A = wl.gaussian(N, 3)
+        got, ge = run(plans[prec], A, 0)
+        assert np.array_equal(np.ldexp(got, ge), np.eye(N))
+        got, ge = run(plans[prec], A, 1)
+        assert np.array_equal(np.ldexp(got, ge), A.astype(np.float64))
+        got, st = run(plans[prec], A, 1, mantissa=False)
+        assert st == 0 and np.array_equal(got, A.astype(np.float64))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fibonacci_exact_on_gpu(plans, prec):
+    # F(n+1) < 2^24 for n <= 34: every partial product is an exact float32
+    # integer and the power-of-two rescaling is exact.
+    for N in (16, 64, 130):
+        A = wl.fibonacci_blocks(N)
+        for n in (2, 5, 10, 20, 33, 34):
+            got, ge = run(plans[prec], A, n)
+            want = oracle.matpow_value(A, n)
+            assert np.array_equal(np.ldexp(got, ge), want), (N, n)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_permutation_and_shift_exact(plans, prec):
+    for N in (13, 64, 150):
+        P, perm = wl.permutation(N, 5)
+        for n in (2, 3, 10, 1000, 123457):
+            got, ge = run(plans[prec], P, n)
+            assert np.array_equal(np.ldexp(got, ge), oracle.matpow_value(P, n)), (N, n)
+        S = wl.shift(N)
+        for n in (2, 5, N - 1, N, N + 3):
+            got, ge = run(plans[prec], S, n)
+            assert np.array_equal(np.ldexp(got, ge), oracle.matpow_value(S, n)), (N, n)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_value_mode_and_range(plans, prec):
+    A = wl.gaussian(100, 8)
+    for n in (2, 9, 100):
+        M, e, _ = oracle.matpow_f64(A, n)
+        got, st = run(plans[prec], A, n, mantissa=False)
+        assert st == 0
+        want = np.ldexp(M, e)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= gate(n, 0)
+    # 4I: (4I)^100 = 2^200 I overflows float32 -> inf and ERANGE, mantissa form exact
+    A = 4.0 * np.eye(80, dtype=np.float32)
+    got, st = run(plans[prec], A, 100, mantissa=False)
+    assert st == 7  # MATPOW_ERANGE
+    assert np.all(np.isinf(np.diag(got)))
+    got, ge = run(plans[prec], A, 100)
+    assert np.array_equal(np.ldexp(got, ge - 200), np.eye(80))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_huge_power_keeps_range(plans, prec):
+    # (2P)^n = 2^n P^n for a permutation P: every partial product is exact, and
+    # the exponent 2^30+12345 is far outside float32 (and float64) range.
+    for N in (40, 96):
+        P, perm = wl.permutation(N, 9)
+        n = 2 ** 30 + 12345
+        got, ge = run(plans[prec], 2.0 * P, n)
+        Pn = oracle.matpow_value(P, n)
+        nz = got != 0
+        assert np.array_equal(nz, Pn != 0)
+        # every nonzero is 2^k with k + ge = n
+        ks = np.log2(got[nz])
+        assert np.all(ks == np.round(ks)) and np.all(ks + ge == n)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_stochastic_long_chain_row_sums(plans, prec):
+    # error of the dominant eigenvalue doubles with each squaring (n*delta);
+    # report it and check it stays within the float32-class bound at n = 2^20
+    A = wl.stochastic_exact(96, 2)
+    n = 2 ** 20
+    M, e, _ = oracle.matpow_f64(A, n)
+    got, ge = run(plans[prec], A, n)
+    err = oracle.rel_frobenius(got, ge, M, e)
+    bound = gate(n, floor_rel(A, n, M, e))
+    rows = np.ldexp(got, ge).sum(axis=1)
+    print("prec=%s rel_F=%.3e bound=%.3e max|rowsum-1|=%.3e" % (prec, err, bound,
+                                                                  np.max(np.abs(rows - 1))))
+    assert err <= bound
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_aliasing_out_equals_in(plans, prec):
+    import torch
+    for N in (48, 150):
+        A = wl.gaussian(N, 11)
+        dA = to_dev(A)
+        lg = torch.zeros(1, dtype=torch.int64, device="cuda")
+        from paper_1204_3052_gb300 import matpow as mpw
+        st = mpw.matpow_f32(plans[prec].h, dA, N, 13, dA, lg)
+        assert st == 0
+        plans[prec].check()
+        M, e, _ = oracle.matpow_f64(A, 13)
+        err = oracle.rel_frobenius(dA.cpu().numpy(), int(lg.item()), M, e)
+        assert err <= gate(13, floor_rel(A, 13, M, e))
+
+
+def test_invalid_arguments():
+    from paper_1204_3052_gb300 import matpow as mpw
+    import torch
+    p = mpw.Plan(64, "fp32")
+    A = torch.zeros((64, 64), device="cuda")
+    assert mpw.matpow_f32(p.h, A, 65, 2, A) == mpw.EINVAL
+    assert mpw.matpow_f32(p.h, A, -1, 2, A) == mpw.EINVAL
+    assert mpw.matpow_f32(p.h, 0, 8, 2, A) == mpw.EINVAL
+    assert mpw.matpow_f32(p.h, A, 0, 2, A) == mpw.OK
+    B = torch.full((4, 4), float("nan"), device="cuda")
+    assert mpw.matpow_f32(p.h, B, 4, 3, B) == mpw.OK
+    assert p.sync() == mpw.EINVAL
+    assert p.sync() == mpw.OK  # cleared
+    p.close()
+
+
+def test_graph_replay_matches_direct():
+    from paper_1204_3052_gb300 import matpow as mpw
+    import torch
+    A = to_dev(wl.gaussian(300, 4))
+    pg = mpw.Plan(512, "fp32")
+    pd = mpw.Plan(512, "fp32")
+    pd.set_option(mpw.OPT_GRAPHS, 0)
+    outs = []
+    for _ in range(3):
+        o, lg = pg.f32(A, 77, mantissa=True)
+        outs.append((o.clone(), int(lg.item())))
+    od, lgd = pd.f32(A, 77, mantissa=True)
+    pg.check(); pd.check()
+    for o, l in outs:
+        assert torch.equal(o, od) and l == int(lgd.item())

@@ -1,0 +1,60 @@
+"""Mod-p parity: libmatpow (GPU) against the exact uint64 CPU oracle, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import to_dev
+from paper_1204_3052_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def plan():
+    from paper_1204_3052_gb300 import matpow as mpw
+    p = mpw.Plan(1024, "bf16x3")
+    yield p
+    p.close()
+
+
+def run(plan, A, n, p):
+    dA = to_dev(A.astype(np.uint32).view(np.int32))
+    out = plan.mod_p(dA, n, p)
+    st = plan.sync()
+    return out.cpu().numpy().view(np.uint32).astype(np.uint64), st
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 8, 17, 64, 65, 100, 129, 256, 300])
+def test_modp_random_bit_exact(plan, N):
+    p = 65521
+    A = wl.modp_uniform(N, p, N)
+    for n in (0, 1, 2, 3, 100, 2 ** 20, 2 ** 30 - 1):
+        got, st = run(plan, A, n, p)
+        want, _ = oracle.matpow_modp(A, n, p)
+        assert st == 0
+        assert np.array_equal(got, want), (N, n)
+
+
+@pytest.mark.parametrize("p", [2, 3, 251, 257, 65521, 65536])
+def test_modp_moduli(plan, p):
+    A = wl.modp_uniform(40, p, 3)
+    for n in (5, 999):
+        got, st = run(plan, A, n, p)
+        want, _ = oracle.matpow_modp(A, n, p)
+        assert st == 0 and np.array_equal(got, want), (p, n)
+
+
+def test_modp_fibonacci_huge(plan):
+    p = 65521
+    A = wl.fibonacci_blocks(64).astype(np.uint64)
+    n = 10 ** 18 + 7
+    got, st = run(plan, A, n, p)
+    want, _ = oracle.matpow_modp(A, n, p)
+    assert np.array_equal(got, want)
+
+
+def test_modp_rejects_unreduced(plan):
+    A = wl.modp_uniform(10, 7, 1)
+    A[3, 4] = 7
+    got, st = run(plan, A, 5, 7)
+    assert st == 1  # MATPOW_EINVAL from the device check
