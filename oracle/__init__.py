@@ -22,6 +22,15 @@ Functions and the passage each follows:
   rounded to float32 (numpy float32 matmul as the product step).  It is an
   error yardstick, not a parity target: parity unpinned (its output is only
   used to size the error a float32-class method attains).
+* ``round_bf16``, ``split_bf16``: round-to-nearest-even to bfloat16 (8
+  significant bits) and the two-part split x ~ hi + lo, hi = bf16(x),
+  lo = bf16(x - hi).
+* ``emu_sqmul(A, n, precision)``: the square-and-multiply chain with the
+  operand rounding of a tensor-core precision emulated on the CPU ("bf16":
+  one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi; products and sums in
+  float64, each result rounded to float32).  Like ``fp32_sqmul`` it is an
+  error yardstick for the lower-precision paths, not a parity target; the
+  rounding primitives it uses are pinned by the tests.
 
 Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): Fibonacci, rotation,
 diagonal, nilpotent shift, permutation and identity closed forms; A^(m+k) =
@@ -245,4 +254,71 @@ def fp32_sqmul(A, n: int):
         bits >>= 1
         if bits:
             P, ep = norm(np.matmul(P, P), 2 * ep)
+    return R, er
+
+
+def round_bf16(x) -> np.ndarray:
+    """float32 -> nearest bfloat16 (ties to even), returned as float32.
+
+    bfloat16 keeps the top 16 bits of a float32: add 0x7FFF plus the lowest
+    kept bit to the 32-bit pattern and clear the low 16 bits.  Inputs are
+    finite.
+    """
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    r = ((b + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def split_bf16(x):
+    """(hi, lo) with hi = bf16(x), lo = bf16(x - hi); x - hi is exact in float32."""
+    x = np.asarray(x, dtype=np.float32)
+    hi = round_bf16(x)
+    lo = round_bf16((x - hi).astype(np.float32))
+    return hi, lo
+
+
+def _emu_product(X, Y, precision: str) -> np.ndarray:
+    if precision == "bf16":
+        P = round_bf16(X).astype(np.float64) @ round_bf16(Y).astype(np.float64)
+    elif precision == "bf16x3":
+        xh, xl = split_bf16(X)
+        yh, yl = split_bf16(Y)
+        xh, xl, yh, yl = (a.astype(np.float64) for a in (xh, xl, yh, yl))
+        P = xh @ yh + xh @ yl + xl @ yh
+    else:
+        raise ValueError(precision)
+    return P.astype(np.float32)
+
+
+def emu_sqmul(A, n: int, precision: str):
+    """Square-and-multiply with emulated tensor-core operand rounding (yardstick).
+
+    Returns (M, e): A^n ~ M * 2**e.  The stored matrices keep float32 values,
+    as the products' accumulators do; each product re-rounds its operands.
+    """
+    A = np.asarray(A, dtype=np.float32)
+    N = _square(A)
+
+    def norm(X, e):
+        mx = float(np.max(np.abs(X))) if X.size else 0.0
+        if mx == 0.0 or not math.isfinite(mx):
+            return X, e
+        _, s = math.frexp(mx)
+        return np.ldexp(X, -s).astype(np.float32), e + s
+
+    if n == 0:
+        return np.eye(N, dtype=np.float32), 0
+    P, ep = norm(A.copy(), 0)
+    R, er = None, 0
+    bits = int(n)
+    while bits:
+        if bits & 1:
+            if R is None:
+                R, er = P.copy(), ep
+            else:
+                R, er = norm(_emu_product(R, P, precision), er + ep)
+        bits >>= 1
+        if bits:
+            P, ep = norm(_emu_product(P, P, precision), 2 * ep)
     return R, er

@@ -57,7 +57,7 @@ struct GemmDesc {
   int tile_begin;        // first linear tile of this product in the launch
   int tiles_n;           // tiles along a row of C
   unsigned p;            // modulus (mod-p paths)
-  int pad_;
+  int bn;                // tensor-core tile width (columns of C per CTA)
 };
 
 // Up to two products passed by value (one squaring level of one matrix:

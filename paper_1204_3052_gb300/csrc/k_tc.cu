@@ -1,18 +1,372 @@
-// Tensor-core products (tcgen05 / TMEM / TMA) -- placeholder until the
-// kernels land; the float plan rejects BF16 / BF16X3 products for now.
+// Tensor-core products C = X * Y on sm_103a: TMA -> shared memory ->
+// tcgen05.mma (kind::f16, bfloat16 operands) -> float32 accumulator in TMEM ->
+// epilogue warps (tcgen05.ld) that apply the lagged power-of-two scale and
+// write the stored result.
+//
+// The product is the matrix product of arXiv 1204.3052 Sec. 4.1, run inside
+// the square-and-multiply chain of Sec. 4.3.  The paper's tiling through
+// local memory (Sec. 4.3.2, 4.3.7) becomes TMA boxes in a multi-stage
+// shared-memory ring; its vector loads (Sec. 4.3.5) become 128-byte swizzled
+// TMA rows feeding the tensor cores; its barriers (Sec. 4.3.6) become
+// mbarriers between the TMA, MMA and epilogue warps.
+//
+// Precisions:
+//   PL = 1 (BF16):   one plane, one MMA per 16-deep k-step.
+//   PL = 2 (BF16X3): x = hi + lo planes; hi*hi + hi*lo + lo*hi MMAs into one
+//                    float32 accumulator (the lo*lo term, ~2^-16 relative,
+//                    is dropped).
+// Layout: X is the A operand (K-major rows, 64x128 boxes, 128-byte swizzle),
+// row-major Y is the B operand in MN-major form (64x64 boxes per 64-column
+// chunk, 128-byte swizzle), so no operand is ever transposed in memory.
+//
+// CTA: 256 threads.  Warp 0 issues TMA, warp 1 issues MMAs (one thread),
+// warp 2 owns the TMEM allocation, warps 4-7 run the epilogue (each reads the
+// 32 TMEM lanes = 32 rows of its quadrant).  Every wait is bounded in time; a
+// CTA that gives up drains its copies and MMAs, frees TMEM, and reports
+// MATPOW_ETIMEDOUT through the plan's status word.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.cuh"
 #include "plan.h"
+#include "tc_ptx.cuh"
 
 namespace mp {
-cudaError_t tc_init(matpow_plan_s*) { return cudaSuccess; }
+
+namespace tc {
+constexpr int BM = 128, BK = 64, THREADS = 256;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
+constexpr int SMEM_RING = 192 * 1024;
+template <int BN, int PL>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = PL * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = SMEM_RING / STAGE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+}  // namespace tc
+
+struct TcProblem {
+  CUtensorMap ax[2];  // X as the A operand: hi, lo planes (box 64 x 128)
+  CUtensorMap by[2];  // Y as the B operand: hi, lo planes (box 64 x 64)
+  GemmDesc d;
+};
+
+struct TcPairParams {
+  TcProblem p[2];
+  int count;
+  int tiles0;
+};
+
+template <int BN, int PL>
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
+  using namespace tc;
+  using C = Cfg<BN, PL>;
+  constexpr int STAGES = C::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const uint32_t full0 = ptx::smem_u32(bars);
+  const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
+  const uint32_t accb = ptx::smem_u32(bars + 2 * STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int t = blockIdx.x;
+  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
+  if (which) t -= P.tiles0;
+  const TcProblem& pr = P.p[which];
+  const GemmDesc& d = pr.d;
+  const int tm = t / d.tiles_n, tn = t - (t / d.tiles_n) * d.tiles_n;
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int N = d.N;
+  const int KB = (N + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(full0 + 8 * s, 1);
+      ptx::mbar_init(empty0 + 8 * s, 1);
+    }
+    ptx::mbar_init(accb, 1);
+    *abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), BN);
+    ptx::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    ptx::prefetch_tmap(&pr.ax[0]);
+    ptx::prefetch_tmap(&pr.by[0]);
+    if (PL == 2) {
+      ptx::prefetch_tmap(&pr.ax[1]);
+      ptx::prefetch_tmap(&pr.by[1]);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int issued = 0;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!ptx::mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, WAIT_NS)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t fb = full0 + 8 * s;
+        ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
+        const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
+        const int kx = kb * BK;
+        ptx::tma_load_2d(base, &pr.ax[0], kx, m0, fb);
+        if (PL == 2) ptx::tma_load_2d(base + C::A_BYTES, &pr.ax[1], kx, m0, fb);
+        const uint32_t bbase = base + PL * C::A_BYTES;
+#pragma unroll
+        for (int c = 0; c < BN / 64; ++c) {
+          ptx::tma_load_2d(bbase + c * 8192, &pr.by[0], n0 + 64 * c, kx, fb);
+          if (PL == 2) ptx::tma_load_2d(bbase + C::B_BYTES + c * 8192, &pr.by[1], n0 + 64 * c, kx, fb);
+        }
+        ++issued;
+      }
+      // drain: every issued stage's copies have landed before the CTA can exit
+      for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+        int dummy = 0;
+        ptx::mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, &dummy, WAIT_NS);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!ptx::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_NS)) {
+          *abort_flag = 1;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t a_hi = ptx::smem_u32(smem + s * C::STAGE_BYTES);
+        const uint32_t a_lo = a_hi + C::A_BYTES;
+        const uint32_t b_hi = a_hi + PL * C::A_BYTES;
+        const uint32_t b_lo = b_hi + C::B_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t ad = ptx::smem_desc(a_hi + 32 * k, 16, 1024);
+          const uint64_t bd = ptx::smem_desc(b_hi + 2048 * k, 8192, 1024);
+          ptx::mma_f16(tmem, ad, bd, idesc, (kb | k) != 0);
+          if (PL == 2) {
+            const uint64_t bdl = ptx::smem_desc(b_lo + 2048 * k, 8192, 1024);
+            const uint64_t adl = ptx::smem_desc(a_lo + 32 * k, 16, 1024);
+            ptx::mma_f16(tmem, ad, bdl, idesc, 1);
+            ptx::mma_f16(tmem, adl, bd, idesc, 1);
+          }
+        }
+        ptx::mma_commit(empty0 + 8 * s);  // frees the stage when these MMAs are done
+      }
+      ptx::mma_commit(accb);  // accumulator complete (or drained, after an abort)
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue
+    int dummy = 0;
+    const bool ok = ptx::mbar_wait(accb, 0, &dummy, 2 * WAIT_NS);
+    if (!ok) *abort_flag = 1;
+    ptx::tc_fence_after();
+    if (ok && !*abort_flag) {
+      const int q = warp - 4;
+      const int row = m0 + 32 * q + lane;
+      const int sx = scale_exp_from_bits(scales[d.sx].maxbits);
+      const int sy = scale_exp_from_bits(scales[d.sy].maxbits);
+      const int sh = -(sx + sy);
+      const long long Ec = scales[d.sx].E + scales[d.sy].E + sx + sy;
+      if (t == 0 && q == 0 && lane == 0) {
+        if (d.mode == OUT_INTERNAL) scales[d.sc].E = Ec;
+        if (d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
+      }
+      float mx = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        ptx::tmem_ld_32x32b_x32(tmem + ((uint32_t)(32 * q) << 16) + 32 * c, r);
+        ptx::tmem_ld_wait();
+        const int col0 = n0 + 32 * c;
+        if (row >= N || col0 >= N) continue;
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = mul_pow2(__uint_as_float(r[j]), sh);
+        if (d.mode == OUT_INTERNAL) {
+          __nv_bfloat16* C0 = (__nv_bfloat16*)d.C + (size_t)row * d.ld + col0;
+          __nv_bfloat16* C1 = C0 + d.plane;
+          if (col0 + 32 <= N) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const float a = v[8 * g + 2 * h], b = v[8 * g + 2 * h + 1];
+                __nv_bfloat162 hi = __floats2bfloat162_rn(a, b);
+                hw[h] = *reinterpret_cast<uint32_t*>(&hi);
+                if (PL == 2) {
+                  __nv_bfloat162 lo = __floats2bfloat162_rn(a - __low2float(hi), b - __high2float(hi));
+                  lw[h] = *reinterpret_cast<uint32_t*>(&lo);
+                }
+              }
+              *reinterpret_cast<uint4*>(C0 + 8 * g) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              if (PL == 2) *reinterpret_cast<uint4*>(C1 + 8 * g) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fabsf(v[j]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (col0 + j < N) {
+                __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
+                C0[j] = hi;
+                if (PL == 2) C1[j] = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                mx = fmaxf(mx, fabsf(v[j]));
+              }
+            }
+          }
+        } else {
+          float* O = (float*)d.out + (size_t)row * N + col0;
+          const bool mant = d.mode == OUT_USER_MANT;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (col0 + j < N) O[j] = mant ? v[j] : final_value(v[j], Ec, status);
+        }
+      }
+      if (d.mode == OUT_INTERNAL) {
+        mx = warp_max(mx);
+        if (lane == 0 && mx > 0.f) atomicMax(&scales[d.sc].maxbits, __float_as_uint(mx));
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, BN);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+template <int BN, int PL>
+static cudaError_t set_attr() {
+  return cudaFuncSetAttribute(tc_gemm_kernel<BN, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              tc::Cfg<BN, PL>::SMEM);
+}
+
+cudaError_t tc_init(matpow_plan_s*) {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!g_encode) return cudaErrorNotSupported;
+  cudaError_t e;
+  if ((e = set_attr<64, 1>()) != cudaSuccess) return e;
+  if ((e = set_attr<128, 1>()) != cudaSuccess) return e;
+  if ((e = set_attr<256, 1>()) != cudaSuccess) return e;
+  if ((e = set_attr<64, 2>()) != cudaSuccess) return e;
+  if ((e = set_attr<128, 2>()) != cudaSuccess) return e;
+  return set_attr<256, 2>();
+}
+
 void tc_free(matpow_plan_s*) {}
-matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc*, int*) {
-  return fail(p, MATPOW_EUNSUPPORTED, "tensor-core products are not built yet");
+
+static int pick_bn(matpow_plan_s* p, int N) {
+  if (p->tile_override == 64 || p->tile_override == 128 || p->tile_override == 256)
+    return p->tile_override;
+  if (N <= 1024) return 64;
+  if (N <= 3072) return 128;
+  return 256;
 }
-matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair&, cudaStream_t) {
-  return fail(p, MATPOW_EUNSUPPORTED, "tensor-core products are not built yet");
+
+matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc* d, int* ntiles) {
+  d->bn = pick_bn(p, d->N);
+  d->tiles_n = (d->N + d->bn - 1) / d->bn;
+  *ntiles = ((d->N + tc::BM - 1) / tc::BM) * d->tiles_n;
+  return MATPOW_OK;
 }
+
+static bool encode(CUtensorMap* m, const void* base, int N, int ld, int box_inner, int box_outer) {
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)N};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+static bool fill_problem(TcProblem* tp, const GemmDesc& d, int PL) {
+  tp->d = d;
+  const size_t lo = (size_t)d.plane * 2;
+  if (!encode(&tp->ax[0], d.X, d.N, d.ld, 64, tc::BM)) return false;
+  if (!encode(&tp->by[0], d.Y, d.N, d.ld, 64, 64)) return false;
+  if (PL == 2) {
+    if (!encode(&tp->ax[1], (const char*)d.X + lo, d.N, d.ld, 64, tc::BM)) return false;
+    if (!encode(&tp->by[1], (const char*)d.Y + lo, d.N, d.ld, 64, 64)) return false;
+  } else {
+    tp->ax[1] = tp->ax[0];
+    tp->by[1] = tp->by[0];
+  }
+  return true;
+}
+
+template <int BN, int PL>
+static cudaError_t launch(const TcPairParams& P, int grid, Scale* scales, unsigned* status,
+                          cudaStream_t s) {
+  tc_gemm_kernel<BN, PL><<<grid, tc::THREADS, tc::Cfg<BN, PL>::SMEM, s>>>(P, scales, status);
+  return cudaGetLastError();
+}
+
+matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s) {
+  const int PL = p->prec == MATPOW_BF16X3 ? 2 : 1;
+  TcPairParams P;
+  memset(&P, 0, sizeof P);
+  P.count = g.count;
+  for (int i = 0; i < g.count; ++i)
+    if (!fill_problem(&P.p[i], g.d[i], PL))
+      return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", g.d[i].N);
+  P.tiles0 = g.count > 1 ? g.d[1].tile_begin : g.tiles_total;
+  const int bn = g.d[0].bn;
+  cudaError_t e;
+  if (PL == 2)
+    e = bn == 64 ? launch<64, 2>(P, g.tiles_total, p->scales, p->status, s)
+        : bn == 128 ? launch<128, 2>(P, g.tiles_total, p->scales, p->status, s)
+                    : launch<256, 2>(P, g.tiles_total, p->scales, p->status, s);
+  else
+    e = bn == 64 ? launch<64, 1>(P, g.tiles_total, p->scales, p->status, s)
+        : bn == 128 ? launch<128, 1>(P, g.tiles_total, p->scales, p->status, s)
+                    : launch<256, 1>(P, g.tiles_total, p->scales, p->status, s);
+  if (e != cudaSuccess) return cuda_fail(p, e, "tc_gemm_kernel launch");
+  return MATPOW_OK;
+}
+
 matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc*, int, int, Scale*, cudaStream_t) {
-  return fail(p, MATPOW_EUNSUPPORTED, "tensor-core products are not built yet");
+  return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches are not built yet");
 }
+
 }  // namespace mp

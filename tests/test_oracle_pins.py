@@ -315,3 +315,65 @@ def test_modp_rejects_unreduced_entries():
     A = np.array([[5, 1], [0, 2]], dtype=np.uint64)
     with pytest.raises(RuntimeError):
         oracle.matpow_modp(A, 3, 5)
+
+
+# ---------------------------------------------------------------- precision emulators
+
+def test_round_bf16_known_values():
+    # bfloat16 has 8 significant bits: spacing 2^-7 in [1, 2)
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -7, 1.0 + 2 ** -9,
+                  -(1.0 + 3 * 2 ** -8), 3.0, 0.0, 2 ** -100, 65280.0, 65408.0], dtype=np.float32)
+    want = np.array([1.0, 1.0, 1.0 + 2 ** -6, 1.0 + 2 ** -7, 1.0,
+                     -(1.0 + 2 ** -6), 3.0, 0.0, 2 ** -100, 65280.0, 65536.0], dtype=np.float32)
+    assert np.array_equal(oracle.round_bf16(x), want)
+
+
+def test_round_bf16_is_nearest():
+    g = wl.rng(11)
+    x = g.standard_normal(20000).astype(np.float32)
+    r = oracle.round_bf16(x).astype(np.float64)
+    # every bf16 value has 7 fraction bits: r * 2^(7 - exponent) is an integer
+    m, e = np.frexp(r)
+    assert np.all(m * 256 == np.round(m * 256))
+    # nearest: |x - r| <= half a bf16 ulp of x
+    _, ex = np.frexp(x.astype(np.float64))
+    assert np.all(np.abs(x - r) <= np.ldexp(1.0, ex - 9) + 0.0)
+
+
+def test_split_bf16_sixteen_bits_exact():
+    # values with at most 16 significant bits are hi + lo exactly
+    g = wl.rng(12)
+    ints = g.integers(-(2 ** 15), 2 ** 15, size=5000).astype(np.float64)
+    x = np.ldexp(ints, g.integers(-20, 20, size=5000)).astype(np.float32)
+    hi, lo = oracle.split_bf16(x)
+    assert np.array_equal(hi.astype(np.float64) + lo.astype(np.float64), x.astype(np.float64))
+    # and a general float32 keeps ~16 bits: |x - hi - lo| <= 2^-16 |x|
+    y = g.standard_normal(5000).astype(np.float32)
+    h, l = oracle.split_bf16(y)
+    assert np.all(np.abs(y.astype(np.float64) - h - l) <= 2.0 ** -16 * np.abs(y))
+
+
+def test_emulated_paths_are_exact_on_small_integers():
+    # Fibonacci powers stay integers below 2^8 for n <= 12: every operand is
+    # exact in bfloat16, so both emulated precisions reproduce the power exactly
+    A = wl.fibonacci_blocks(6)
+    for prec in ("bf16", "bf16x3"):
+        for n in range(1, 12):
+            M, e = oracle.emu_sqmul(A, n, prec)
+            assert np.array_equal(np.ldexp(M.astype(np.float64), e), oracle.matpow_value(A, n))
+
+
+def test_emulated_error_ordering():
+    # bf16 error > bf16x3 error > float32 error on a Gaussian power
+    A = wl.gaussian(64, 1)
+    n = 16
+    M, e, _ = oracle.matpow_f64(A, n)
+    errs = {}
+    for prec in ("bf16", "bf16x3"):
+        Mp, ep = oracle.emu_sqmul(A, n, prec)
+        errs[prec] = oracle.rel_frobenius(Mp, ep, M, e)
+    Mf, ef = oracle.fp32_sqmul(A, n)
+    errs["fp32"] = oracle.rel_frobenius(Mf, ef, M, e)
+    assert errs["bf16"] > 30 * errs["bf16x3"]
+    assert errs["bf16x3"] > errs["fp32"]
+    assert errs["bf16"] < 2.0 ** -6

@@ -15,7 +15,12 @@ from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32"]
+PRECS = ["fp32", "bf16x3", "bf16"]
+# largest Fibonacci power whose partial products are exact in each path:
+# float32 holds F < 2^24; a bfloat16 operand (or the hi part of the split)
+# holds integers < 2^8, and the split path drops lo*lo, so both bf16 paths
+# are exact only while F(n+1) < 2^8.
+FIB_EXACT = {"fp32": 34, "bf16x3": 12, "bf16": 12}
 
 
 @pytest.fixture(scope="module")
@@ -39,9 +44,14 @@ def run(plan, A, n, mantissa=True):
     return out.cpu().numpy().astype(np.float64), st
 
 
-def floor_rel(A, n, M, e):
+def floor_rel(A, n, M, e, prec="fp32"):
+    """Error of a CPU run of the same method at the path's precision class."""
     Mf, ef = oracle.fp32_sqmul(A, n)
-    return oracle.rel_frobenius(Mf, ef, M, e)
+    f = oracle.rel_frobenius(Mf, ef, M, e)
+    if prec in ("bf16", "bf16x3") and A.shape[0] > 64:  # N <= 64 runs the float32 chain
+        Me, ee = oracle.emu_sqmul(A, n, prec)
+        f = max(f, oracle.rel_frobenius(Me, ee, M, e))
+    return f
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -62,7 +72,7 @@ def test_config2_gaussian_512(plans, prec, n):
     M, e, _ = oracle.matpow_f64(A, n)
     got, ge = run(plans[prec], A, n)
     err = oracle.rel_frobenius(got, ge, M, e)
-    bound = gate(n, floor_rel(A, n, M, e))
+    bound = gate(n, floor_rel(A, n, M, e, prec))
     print("prec=%s n=%d rel_F=%.3e bound=%.3e" % (prec, n, err, bound))
     assert err <= bound, (err, bound)
 
@@ -75,7 +85,7 @@ def test_sizes_span_tiles_and_ragged_tails(plans, prec, N):
         M, e, _ = oracle.matpow_f64(A, n)
         got, ge = run(plans[prec], A, n)
         err = oracle.rel_frobenius(got, ge, M, e)
-        bound = gate(n, floor_rel(A, n, M, e))
+        bound = gate(n, floor_rel(A, n, M, e, prec))
         assert err <= bound, (N, n, err, bound)
 
 
@@ -97,7 +107,9 @@ def test_fibonacci_exact_on_gpu(plans, prec):
     # integer and the power-of-two rescaling is exact.
     for N in (16, 64, 130):
         A = wl.fibonacci_blocks(N)
-        for n in (2, 5, 10, 20, 33, 34):
+        for n in (2, 5, 10, 12, 20, 33, 34):
+            if n > FIB_EXACT[prec] and N > 64:
+                continue
             got, ge = run(plans[prec], A, n)
             want = oracle.matpow_value(A, n)
             assert np.array_equal(np.ldexp(got, ge), want), (N, n)
@@ -124,7 +136,7 @@ def test_value_mode_and_range(plans, prec):
         got, st = run(plans[prec], A, n, mantissa=False)
         assert st == 0
         want = np.ldexp(M, e)
-        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= gate(n, 0)
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= gate(n, floor_rel(A, n, M, e, prec))
     # 4I: (4I)^100 = 2^200 I overflows float32 -> inf and ERANGE, mantissa form exact
     A = 4.0 * np.eye(80, dtype=np.float32)
     got, st = run(plans[prec], A, 100, mantissa=False)
@@ -159,7 +171,7 @@ def test_stochastic_long_chain_row_sums(plans, prec):
     M, e, _ = oracle.matpow_f64(A, n)
     got, ge = run(plans[prec], A, n)
     err = oracle.rel_frobenius(got, ge, M, e)
-    bound = gate(n, floor_rel(A, n, M, e))
+    bound = gate(n, floor_rel(A, n, M, e, prec))
     rows = np.ldexp(got, ge).sum(axis=1)
     print("prec=%s rel_F=%.3e bound=%.3e max|rowsum-1|=%.3e" % (prec, err, bound,
                                                                   np.max(np.abs(rows - 1))))
@@ -179,7 +191,7 @@ def test_aliasing_out_equals_in(plans, prec):
         plans[prec].check()
         M, e, _ = oracle.matpow_f64(A, 13)
         err = oracle.rel_frobenius(dA.cpu().numpy(), int(lg.item()), M, e)
-        assert err <= gate(13, floor_rel(A, 13, M, e))
+        assert err <= gate(13, floor_rel(A, 13, M, e, prec))
 
 
 def test_invalid_arguments():
@@ -213,3 +225,35 @@ def test_graph_replay_matches_direct():
     pg.check(); pd.check()
     for o, l in outs:
         assert torch.equal(o, od) and l == int(lgd.item())
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("tile", [64, 128, 256])
+def test_every_tensor_core_tile_shape(prec, tile):
+    from paper_1204_3052_gb300 import matpow as mpw
+    plan = mpw.Plan(700, prec)
+    plan.set_option(mpw.OPT_TILE, tile)
+    for N in (96, 300, 640, 700):
+        A = wl.gaussian(N, 5)
+        for n in (2, 7):
+            M, e, _ = oracle.matpow_f64(A, n)
+            got, ge = run(plan, A, n)
+            err = oracle.rel_frobenius(got, ge, M, e)
+            bound = gate(n, floor_rel(A, n, M, e, prec))
+            assert err <= bound, (tile, N, n, err, bound)
+    plan.close()
+
+
+def test_bf16x3_beats_bf16_and_meets_float_bound():
+    from paper_1204_3052_gb300 import matpow as mpw
+    A = wl.gaussian(512, 0)
+    errs = {}
+    for prec in ("bf16", "bf16x3"):
+        plan = mpw.Plan(512, prec)
+        M, e, _ = oracle.matpow_f64(A, 16)
+        got, ge = run(plan, A, 16)
+        errs[prec] = oracle.rel_frobenius(got, ge, M, e)
+        plan.close()
+    print(errs)
+    assert errs["bf16x3"] * 30 < errs["bf16"]
+    assert errs["bf16x3"] <= float_tol(16)
