@@ -94,10 +94,19 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       the caller's stream (read with matpow_kernel_time); 0 (default).
  *   MATPOW_OPT_TINY_MAX largest N handled by the single-kernel whole-chain path
  *                       (0 disables it; default 64).
- *   MATPOW_OPT_TILE     tensor-core tile override for matpow_f32 (0 = autotuned
- *                       table; otherwise one of the MATPOW_TILE_* codes).
+ *   MATPOW_OPT_TILE     tensor-core tile width override (columns of C per CTA:
+ *                       64, 128 or 256; 0 = the built-in choice by N).
+ *   MATPOW_OPT_SPLIT    MATPOW_BF16X3 operand split: 0 (default) exact
+ *                       fixed-point slices -- each matrix scaled by its
+ *                       power-of-two maximum and cut into two 8-bit integer
+ *                       slices, whose tensor-core partial sums are exact
+ *                       integers; 1: floating hi/lo bfloat16 parts summed in
+ *                       the tensor core's float32 accumulator (subject to the
+ *                       accumulator's rounding toward zero, whose bias the
+ *                       squaring chain amplifies).
  */
-enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4 };
+enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4,
+       MATPOW_OPT_SPLIT = 5 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
 /* ---- the power ------------------------------------------------------------ */

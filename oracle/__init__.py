@@ -25,10 +25,14 @@ Functions and the passage each follows:
 * ``round_bf16``, ``split_bf16``: round-to-nearest-even to bfloat16 (8
   significant bits) and the two-part split x ~ hi + lo, hi = bf16(x),
   lo = bf16(x - hi).
+* ``fixed_slices(X)``: the fixed-point split of a matrix scaled by its
+  power-of-two maximum 2^s: u = X 2^(8-s), a1 = rint(u), a2 = rint(256 (u - a1)),
+  so X ~ 2^(s-16) (256 a1 + a2) with integer slices |a1| <= 256, |a2| <= 128.
 * ``emu_sqmul(A, n, precision)``: the square-and-multiply chain with the
   operand rounding of a tensor-core precision emulated on the CPU ("bf16":
-  one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi; products and sums in
-  float64, each result rounded to float32).  Like ``fp32_sqmul`` it is an
+  one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi of floating
+  bfloat16 parts; "bf16x3fx": a1*b1 + a1*b2 + a2*b1 of the fixed-point
+  slices; products and sums in float64, each result rounded to float32).  Like ``fp32_sqmul`` it is an
   error yardstick for the lower-precision paths, not a parity target; the
   rounding primitives it uses are pinned by the tests.
 
@@ -278,7 +282,23 @@ def split_bf16(x):
     return hi, lo
 
 
+def fixed_slices(X):
+    """(a1, a2, s): X ~ 2^(s-16) (256 a1 + a2), s the frexp exponent of max|X|."""
+    X = np.asarray(X, dtype=np.float32)
+    mx = float(np.max(np.abs(X))) if X.size else 0.0
+    s = math.frexp(mx)[1] if mx > 0.0 else 0
+    u = np.ldexp(X.astype(np.float64), 8 - s)
+    a1 = np.rint(u)
+    a2 = np.rint((u - a1) * 256.0)
+    return a1, a2, s
+
+
 def _emu_product(X, Y, precision: str) -> np.ndarray:
+    if precision == "bf16x3fx":
+        a1, a2, sx = fixed_slices(X)
+        b1, b2, sy = fixed_slices(Y)
+        T = a1 @ b1 + (a1 @ b2 + a2 @ b1) / 256.0
+        return np.ldexp(T, sx + sy - 16).astype(np.float32)
     if precision == "bf16":
         P = round_bf16(X).astype(np.float64) @ round_bf16(Y).astype(np.float64)
     elif precision == "bf16x3":

@@ -75,9 +75,16 @@ size_t mp::matrix_bytes(int N, int fmt) {
       return align_up(e * 4, 1024);
     case FMT_BF16:
       return align_up(e * 2, 1024);
+    case FMT_FX2:  // two bfloat16 slices, then the float32 matrix
+      return 2 * align_up(e * 2, 1024) + align_up(e * 4, 1024);
     default:  // two bfloat16 planes
       return 2 * align_up(e * 2, 1024);
   }
+}
+
+size_t mp::fx2_f32_offset(int N) {
+  size_t ld = (size_t)ld_for(N, FMT_FX2);
+  return 2 * align_up((size_t)N * ld * 2, 1024);
 }
 
 long long mp::plane_offset_elems(int N, int fmt) {
@@ -90,10 +97,16 @@ int mp::float_fmt(matpow_precision p) {
     case MATPOW_BF16:
       return FMT_BF16;
     case MATPOW_BF16X3:
-      return FMT_PLANES;
+      return FMT_FX2;
     default:
       return FMT_F32;
   }
+}
+
+int mp::plan_float_fmt(const matpow_plan_s* p) {
+  int f = float_fmt(p->prec);
+  if (f == FMT_FX2 && p->split_mode == 1) return FMT_PLANES;
+  return f;
 }
 
 static size_t plan_bytes(int max_n, matpow_precision prec, size_t* buf_bytes) {
@@ -101,6 +114,7 @@ static size_t plan_bytes(int max_n, matpow_precision prec, size_t* buf_bytes) {
   // same buffers (uint32 or two bfloat16 planes take the same 4 bytes/entry)
   size_t bf = std::max(matrix_bytes(max_n, float_fmt(prec)), matrix_bytes(max_n, FMT_U32));
   bf = std::max(bf, matrix_bytes(max_n, FMT_MODP));
+  if (prec == MATPOW_BF16X3) bf = std::max(bf, matrix_bytes(max_n, FMT_PLANES));
   if (buf_bytes) *buf_bytes = bf;
   return 4 * bf + align_up(sizeof(Scale) * kSingleSlots, 1024) + 1024;
 }
@@ -224,8 +238,14 @@ extern "C" matpow_status matpow_plan_set_option(matpow_plan_t p, int key, int64_
       drop_graphs(p);
       return MATPOW_OK;
     case MATPOW_OPT_TILE:
-      if (value < 0 || value > 64) return fail(p, MATPOW_EINVAL, "unknown tile code");
+      if (value != 0 && value != 64 && value != 128 && value != 256)
+        return fail(p, MATPOW_EINVAL, "tile width must be 0, 64, 128 or 256");
       p->tile_override = (int)value;
+      drop_graphs(p);
+      return MATPOW_OK;
+    case MATPOW_OPT_SPLIT:
+      if (value != 0 && value != 1) return fail(p, MATPOW_EINVAL, "split mode must be 0 or 1");
+      p->split_mode = (int)value;
       drop_graphs(p);
       return MATPOW_OK;
     default:
@@ -368,15 +388,26 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
     p->launches++;
     return MATPOW_OK;
   }
-  const int fmt = float_fmt(p->prec);
+  const int fmt = plan_float_fmt(p);
   const long long plane = plane_offset_elems(N, fmt);
   const int ld = ld_for(N, fmt);
+  const bool fx2 = fmt == FMT_FX2;
+  const size_t f32off = fx2 ? fx2_f32_offset(N) : 0;
   std::vector<LevelOps> levels;
   build_schedule(n, &levels);
   int nslots = 2 + matpow_gemm_count(n);
   CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * nslots, s));
-  CK(p, launch_absmax_f32(dA, N, &p->scales[0], p->status, s));
-  CK(p, launch_convert_f32(dA, N, &p->scales[0], &p->scales[1], fmt, p->buf[0], plane, s));
+  if (fx2) {
+    // slot 1 describes A itself (exponent 0); the split normalises by max|A|
+    CK(p, launch_absmax_f32(dA, N, &p->scales[1], p->status, s));
+    SplitPair sp{};
+    sp.count = 1;
+    sp.j[0] = SplitJob{dA, p->buf[0], plane, N, N, ld, 1};
+    CK(p, launch_split_fx2(sp, p->scales, s));
+  } else {
+    CK(p, launch_absmax_f32(dA, N, &p->scales[0], p->status, s));
+    CK(p, launch_convert_f32(dA, N, &p->scales[0], &p->scales[1], fmt, p->buf[0], plane, s));
+  }
   p->launches += 2;
   const bool tc = p->prec != MATPOW_FP32_SIMT;
   for (size_t li = 0; li < levels.size(); ++li) {
@@ -390,7 +421,7 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       GemmDesc& d = g.d[i];
       d.X = p->buf[op.xb];
       d.Y = p->buf[op.yb];
-      d.C = last ? nullptr : p->buf[op.cb];
+      d.C = last ? nullptr : (char*)p->buf[op.cb] + f32off;
       d.out = last ? (void*)dOut : nullptr;
       d.out_log2 = last ? (long long*)dLog2 : nullptr;
       d.plane = plane;
@@ -423,6 +454,18 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
     }
     p->launches++;
+    if (fx2 && li + 1 < levels.size()) {  // slice the level's outputs for the next level
+      SplitPair sp{};
+      sp.count = g.count;
+      for (int i = 0; i < g.count; ++i) {
+        const Op& op = lv.ops[i];
+        sp.j[i] = SplitJob{(const float*)g.d[i].C, p->buf[op.cb], plane, ld, N, ld, op.sc};
+      }
+      timed_begin(p, s, &ev);
+      CK(p, launch_split_fx2(sp, p->scales, s));
+      timed_end(p, s, ev, MATPOW_KERNEL_AUX, 0.0);
+      p->launches++;
+    }
   }
   return MATPOW_OK;
 }

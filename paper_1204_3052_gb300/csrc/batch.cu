@@ -82,7 +82,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
     ~Restore() { cudaSetDevice(d); }
   } restore{prev};
   cudaStream_t s = (cudaStream_t)stream;
-  const int fmt = float_fmt(p->prec);
+  const int fmt = plan_float_fmt(p);
   const bool tc = p->prec != MATPOW_FP32_SIMT;
 
   // ---- classify
@@ -135,6 +135,9 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
     big.push_back(std::move(b));
   }
   matpow_status st;
+  if (tc && !big.empty())
+    return fail(p, MATPOW_EUNSUPPORTED,
+                "matpow_batched: tensor-core precisions need N <= %d in this build", p->tiny_max);
   if ((st = grow(p, &p->batch.ws, &p->batch.ws_bytes, std::max<size_t>(ws_need, 1), false))) return st;
   size_t sc_bytes = sizeof(Scale) * std::max(slots, 1);
   if ((st = grow(p, (void**)&p->batch.scales, &p->batch.scale_cap, sc_bytes, false))) return st;

@@ -87,6 +87,7 @@ struct matpow_plan_s {
   bool timing_on = false;
   int tiny_max = 64;
   int tile_override = 0;
+  int split_mode = 0;  // BF16X3: 0 exact fixed-point slices, 1 floating hi/lo planes
   // graphs
   std::vector<mp::GraphEntry> graphs;
   uint64_t graph_clock = 0;
@@ -106,6 +107,8 @@ matpow_status cuda_fail(matpow_plan_s* plan, cudaError_t e, const char* what);
 size_t matrix_bytes(int N, int fmt);
 long long plane_offset_elems(int N, int fmt);
 int float_fmt(matpow_precision p);
+int plan_float_fmt(const matpow_plan_s* p);  // float_fmt, with the split option applied
+size_t fx2_f32_offset(int N);                // byte offset of the float32 matrix in FMT_FX2
 cudaEvent_t take_event(matpow_plan_s* p);
 void timed_begin(matpow_plan_s* p, cudaStream_t s, cudaEvent_t* ev);
 void timed_end(matpow_plan_s* p, cudaStream_t s, cudaEvent_t ev, int kind, double flop);

@@ -377,3 +377,38 @@ def test_emulated_error_ordering():
     assert errs["bf16"] > 30 * errs["bf16x3"]
     assert errs["bf16x3"] > errs["fp32"]
     assert errs["bf16"] < 2.0 ** -6
+
+
+def test_fixed_slices_integers_and_reconstruction():
+    g = wl.rng(13)
+    X = (g.standard_normal((40, 40)) * 3.0).astype(np.float32)
+    a1, a2, s = oracle.fixed_slices(X)
+    assert np.all(a1 == np.rint(a1)) and np.all(a2 == np.rint(a2))
+    assert np.max(np.abs(a1)) <= 256 and np.max(np.abs(a2)) <= 128
+    # max|X| * 2^-s in [0.5, 1)
+    assert 0.5 <= np.max(np.abs(X)) * 2.0 ** -s < 1.0
+    rec = np.ldexp(256.0 * a1 + a2, s - 16)
+    assert np.max(np.abs(rec - X)) <= 2.0 ** (s - 17)
+    # values on the 2^(s-16) grid are reproduced exactly
+    Y = np.ldexp(np.rint(np.ldexp(X.astype(np.float64), 16 - s)), s - 16).astype(np.float32)
+    b1, b2, t = oracle.fixed_slices(Y)
+    assert t == s and np.array_equal(np.ldexp(256.0 * b1 + b2, t - 16), Y.astype(np.float64))
+
+
+def test_fixed_slice_products_stay_exact_in_float32():
+    # |a1 b1| <= 2^16 and |a1 b2 + a2 b1| <= 2^16, so 256-deep sums stay <= 2^24
+    assert 256 * 256 * 256 <= 2 ** 24
+    assert 256 * (256 * 128 + 128 * 256) <= 2 ** 24
+
+
+def test_emulated_fixed_split_close_to_float_split():
+    A = wl.gaussian(96, 2)
+    n = 16
+    M, e, _ = oracle.matpow_f64(A, n)
+    Mx, ex = oracle.emu_sqmul(A, n, "bf16x3fx")
+    Mh, eh = oracle.emu_sqmul(A, n, "bf16x3")
+    efx = oracle.rel_frobenius(Mx, ex, M, e)
+    efl = oracle.rel_frobenius(Mh, eh, M, e)
+    # 16-bit fixed point relative to the matrix maximum keeps fewer bits of
+    # the small entries than a per-entry 16-bit split: larger, but bounded
+    assert efl < efx < 30 * efl and efx < 1e-3

@@ -17,10 +17,11 @@ pytestmark = pytest.mark.gpu
 
 PRECS = ["fp32", "bf16x3", "bf16"]
 # largest Fibonacci power whose partial products are exact in each path:
-# float32 holds F < 2^24; a bfloat16 operand (or the hi part of the split)
-# holds integers < 2^8, and the split path drops lo*lo, so both bf16 paths
-# are exact only while F(n+1) < 2^8.
-FIB_EXACT = {"fp32": 34, "bf16x3": 12, "bf16": 12}
+# float32 holds F < 2^24; the exact split holds every integer below 2^16
+# (two 8-bit slices of a matrix whose maximum is below 2^16) and sums them
+# exactly; a bfloat16 operand holds integers < 2^8.
+FIB_EXACT = {"fp32": 34, "bf16x3": 23, "bf16": 12}
+EMU = {"bf16": "bf16", "bf16x3": "bf16x3fx"}
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +50,7 @@ def floor_rel(A, n, M, e, prec="fp32"):
     Mf, ef = oracle.fp32_sqmul(A, n)
     f = oracle.rel_frobenius(Mf, ef, M, e)
     if prec in ("bf16", "bf16x3") and A.shape[0] > 64:  # N <= 64 runs the float32 chain
-        Me, ee = oracle.emu_sqmul(A, n, prec)
+        Me, ee = oracle.emu_sqmul(A, n, EMU[prec])
         f = max(f, oracle.rel_frobenius(Me, ee, M, e))
     return f
 
@@ -107,7 +108,7 @@ def test_fibonacci_exact_on_gpu(plans, prec):
     # integer and the power-of-two rescaling is exact.
     for N in (16, 64, 130):
         A = wl.fibonacci_blocks(N)
-        for n in (2, 5, 10, 12, 20, 33, 34):
+        for n in (2, 5, 10, 12, 20, 23, 33, 34):
             if n > FIB_EXACT[prec] and N > 64:
                 continue
             got, ge = run(plans[prec], A, n)
@@ -255,5 +256,32 @@ def test_bf16x3_beats_bf16_and_meets_float_bound():
         errs[prec] = oracle.rel_frobenius(got, ge, M, e)
         plan.close()
     print(errs)
-    assert errs["bf16x3"] * 30 < errs["bf16"]
-    assert errs["bf16x3"] <= float_tol(16)
+    assert errs["bf16x3"] * 20 < errs["bf16"]
+
+
+def test_exact_split_accumulates_integers_exactly():
+    # small-integer matrices: the slices are exact and every 256-deep partial
+    # sum is an integer below 2^24, so A^2 must equal the integer product
+    from paper_1204_3052_gb300 import matpow as mpw
+    plan = mpw.Plan(1024, "bf16x3")
+    g = wl.rng(21)
+    for N in (96, 512, 1000):
+        A = g.integers(-15, 16, size=(N, N)).astype(np.float32)
+        got, ge = run(plan, A, 2)
+        want = oracle.gemm_f64(A, A)
+        assert np.array_equal(np.ldexp(got, ge), want), N
+    plan.close()
+
+
+@pytest.mark.parametrize("n", [2, 7, 16])
+def test_floating_split_option(n):
+    from paper_1204_3052_gb300 import matpow as mpw
+    plan = mpw.Plan(512, "bf16x3")
+    plan.set_option(mpw.OPT_SPLIT, 1)
+    A = wl.gaussian(300, 3)
+    M, e, _ = oracle.matpow_f64(A, n)
+    got, ge = run(plan, A, n)
+    err = oracle.rel_frobenius(got, ge, M, e)
+    Me, ee = oracle.emu_sqmul(A, n, "bf16x3")
+    assert err <= gate(n, oracle.rel_frobenius(Me, ee, M, e)), err
+    plan.close()
