@@ -132,6 +132,30 @@ matpow_status matpow_f32(matpow_plan_t plan, const float* dA, int N, uint64_t n,
                          int64_t* dLog2Scale, void* stream);
 
 /*
+ * A^n like matpow_f32 with MATPOW_FP32_SIMT products, for callers that may
+ * not allocate device memory: code that runs under an allocator which owns
+ * all of the device's memory (a framework's caching pool, a fixed budget set
+ * at start-up), or latency-critical code that cannot afford the implicit
+ * synchronisation of cudaMalloc/cudaFree.  It takes no plan and calls no
+ * allocating routine; its scratch (four 512 x 512 float32 buffers plus the
+ * per-power scale slots, about 4 MiB) is an array compiled into the library,
+ * present on every GPU that loads it until the process exits.  The paper has
+ * no counterpart to this entry point.
+ *   dA, N, n, dOut, dLog2Scale, stream: as in matpow_f32, on the calling
+ *               thread's current device; 0 <= N <= 512, larger N fails with
+ *               MATPOW_EINVAL (and a message naming the limit).
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same scratch, so calls whose work overlaps on the GPU
+ * (different streams, or threads without ordering) race and corrupt each
+ * other: order them on one stream.  Device-side conditions that matpow_sync
+ * reports for a plan (non-finite input, float32 range loss) are not reported
+ * here; the mantissa form (dLog2Scale != NULL) never loses range.
+ */
+matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, float* dOut,
+                                 int64_t* dLog2Scale, void* stream);
+
+/*
  * A^n mod p for integer A (exact; the same square-and-multiply over Z/pZ).
  *   dA     device, N*N uint32 with every entry in [0, p); read only.
  *   p      modulus, 2 <= p <= 65536.

@@ -36,6 +36,7 @@ EXPORTS = [
     "matpow_plan_set_option", "matpow_f32", "matpow_mod_p", "matpow_batched", "matpow_sync",
     "matpow_gemm_count", "matpow_kernel_time", "matpow_launch_count", "matpow_server_create",
     "matpow_submit", "matpow_poll", "matpow_server_latencies", "matpow_server_destroy",
+    "matpow_f32_noalloc",
 ]
 
 
@@ -97,6 +98,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "matpow_poll": (i32, [vp, u64, u32]),
             "matpow_server_latencies": (i64, [vp, ctypes.POINTER(ctypes.c_double), i64]),
             "matpow_server_destroy": (i32, [vp]),
+            "matpow_f32_noalloc": (i32, [vp, i32, u64, vp, vp, vp]),
         }
         for name, (res, args) in protos.items():
             fn = getattr(lib, name)
@@ -159,6 +161,11 @@ def matpow_plan_set_option(plan: int, key: int, value: int) -> None:
 def matpow_f32(plan: int, A, N: int, n: int, out, log2_scale=None, stream=None) -> int:
     return load().matpow_f32(plan, _ptr(A), int(N), int(n), _ptr(out), _ptr(log2_scale),
                              _stream(stream))
+
+
+def matpow_f32_noalloc(A, N: int, n: int, out, log2_scale=None, stream=None) -> int:
+    return load().matpow_f32_noalloc(_ptr(A), int(N), int(n), _ptr(out), _ptr(log2_scale),
+                                     _stream(stream))
 
 
 def matpow_mod_p(plan: int, A, N: int, n: int, p: int, out, stream=None) -> int:
