@@ -104,9 +104,13 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       the tensor core's float32 accumulator (subject to the
  *                       accumulator's rounding toward zero, whose bias the
  *                       squaring chain amplifies).
+ *   MATPOW_OPT_CHAIN    1 (default): for MATPOW_BF16X3 with the exact split and
+ *                       64 < N <= 1024, run the whole chain in one cooperative
+ *                       launch (grid barriers between levels); 0: one launch
+ *                       per level.
  */
 enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4,
-       MATPOW_OPT_SPLIT = 5 };
+       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
 /* ---- the power ------------------------------------------------------------ */

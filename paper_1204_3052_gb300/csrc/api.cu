@@ -176,9 +176,11 @@ extern "C" matpow_status matpow_plan(matpow_plan_t* out, int max_n, matpow_preci
   p->buf_bytes = bufb;
   p->scales = (Scale*)(base + 4 * bufb);
   p->status = (unsigned*)(base + 4 * bufb + align_up(sizeof(Scale) * kSingleSlots, 1024));
+  p->gbar = p->status + 32;  // own 128-byte line
   e = cudaMemset(p->ws, 0, need);
   if (e == cudaSuccess) e = tiny_attrs();
   if (e == cudaSuccess) e = tc_init(p);
+  if (e == cudaSuccess) e = tc_chain_init(p);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_status, sizeof(unsigned));
   cudaSetDevice(prev);
@@ -242,6 +244,9 @@ extern "C" matpow_status matpow_plan_set_option(matpow_plan_t p, int key, int64_
         return fail(p, MATPOW_EINVAL, "tile width must be 0, 64, 128 or 256");
       p->tile_override = (int)value;
       drop_graphs(p);
+      return MATPOW_OK;
+    case MATPOW_OPT_CHAIN:
+      p->use_chain = value != 0;
       return MATPOW_OK;
     case MATPOW_OPT_SPLIT:
       if (value != 0 && value != 1) return fail(p, MATPOW_EINVAL, "split mode must be 0 or 1");
@@ -595,6 +600,9 @@ extern "C" matpow_status matpow_f32(matpow_plan_t p, const float* dA, int N, uin
     return fail(p, MATPOW_EINVAL, "matpow_f32: misaligned pointer");
   DeviceGuard dg(p->device);
   cudaStream_t s = (cudaStream_t)stream;
+  bool used = false;
+  matpow_status cst = tc_chain_run(p, dA, N, n, dOut, dLog2Scale, s, &used);
+  if (cst != MATPOW_OK || used) return cst;
   GraphKey key{0, dA, dOut, dLog2Scale, N, n, 0};
   return run_maybe_graph(p, key, s, [&](cudaStream_t st) {
     return enqueue_f32(p, dA, N, n, dOut, dLog2Scale, st);

@@ -585,7 +585,7 @@ matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc* d, int* ntiles) {
   return MATPOW_OK;
 }
 
-static bool encode(CUtensorMap* m, const void* base, int N, int ld, int box_inner, int box_outer) {
+bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box_inner, int box_outer) {
   cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)N};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
@@ -599,11 +599,11 @@ static bool encode(CUtensorMap* m, const void* base, int N, int ld, int box_inne
 static bool fill_problem(TcProblem* tp, const GemmDesc& d, int PL) {
   tp->d = d;
   const size_t lo = (size_t)d.plane * 2;
-  if (!encode(&tp->ax[0], d.X, d.N, d.ld, 64, tc::BM)) return false;
-  if (!encode(&tp->by[0], d.Y, d.N, d.ld, 64, 64)) return false;
+  if (!tc_encode_bf16_map(&tp->ax[0], d.X, d.N, d.ld, 64, tc::BM)) return false;
+  if (!tc_encode_bf16_map(&tp->by[0], d.Y, d.N, d.ld, 64, 64)) return false;
   if (PL == 2) {
-    if (!encode(&tp->ax[1], (const char*)d.X + lo, d.N, d.ld, 64, tc::BM)) return false;
-    if (!encode(&tp->by[1], (const char*)d.Y + lo, d.N, d.ld, 64, 64)) return false;
+    if (!tc_encode_bf16_map(&tp->ax[1], (const char*)d.X + lo, d.N, d.ld, 64, tc::BM)) return false;
+    if (!tc_encode_bf16_map(&tp->by[1], (const char*)d.Y + lo, d.N, d.ld, 64, 64)) return false;
   } else {
     tp->ax[1] = tp->ax[0];
     tp->by[1] = tp->by[0];

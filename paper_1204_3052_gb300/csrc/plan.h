@@ -1,6 +1,7 @@
 // Host-side plan state of libmatpow (internal).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -88,6 +89,8 @@ struct matpow_plan_s {
   int tiny_max = 64;
   int tile_override = 0;
   int split_mode = 0;  // BF16X3: 0 exact fixed-point slices, 1 floating hi/lo planes
+  bool use_chain = true;  // whole-chain cooperative kernel where it applies
+  unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
   // graphs
   std::vector<mp::GraphEntry> graphs;
   uint64_t graph_clock = 0;
@@ -119,6 +122,14 @@ void tc_free(matpow_plan_s* p);
 // Fill the tensor-core fields of d (tiles_n, tile count in *ntiles).
 matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc* d, int* ntiles);
 matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s);
+// 2-D bfloat16 tensor map over an N x N matrix (row stride ld), 128-byte swizzle.
+bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box_inner,
+                        int box_outer);
+// Whole square-and-multiply chain in one cooperative tensor-core launch
+// (exact split; small and medium N).  *used = false when it does not apply.
+matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
+                           int64_t* dLog2, cudaStream_t s, bool* used);
+cudaError_t tc_chain_init(matpow_plan_s* p);
 matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                               Scale* scales, cudaStream_t s);
 }  // namespace mp

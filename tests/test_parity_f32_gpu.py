@@ -234,6 +234,7 @@ def test_every_tensor_core_tile_shape(prec, tile):
     from paper_1204_3052_gb300 import matpow as mpw
     plan = mpw.Plan(700, prec)
     plan.set_option(mpw.OPT_TILE, tile)
+    plan.set_option(mpw.OPT_CHAIN, 0)  # the level-by-level kernels
     for N in (96, 300, 640, 700):
         A = wl.gaussian(N, 5)
         for n in (2, 7):
@@ -285,3 +286,35 @@ def test_floating_split_option(n):
     Me, ee = oracle.emu_sqmul(A, n, "bf16x3")
     assert err <= gate(n, oracle.rel_frobenius(Me, ee, M, e)), err
     plan.close()
+
+
+@pytest.mark.parametrize("N", [65, 100, 200, 512, 700, 768, 769, 1000, 1024])
+def test_whole_chain_kernel_equals_level_path_bitwise(N):
+    # the cooperative whole-chain kernel and the level-by-level kernels do the
+    # same exact-split arithmetic on the same float32 values, so they agree bit
+    # for bit; both are also checked against the oracle
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    chain = mpw.Plan(1024, "bf16x3")
+    level = mpw.Plan(1024, "bf16x3")
+    level.set_option(mpw.OPT_CHAIN, 0)
+    A = wl.gaussian(N, N + 7)
+    dA = to_dev(A)
+    for n in (2, 3, 13, 1024):
+        oc, lc = chain.f32(dA, n, mantissa=True)
+        ol, ll = level.f32(dA, n, mantissa=True)
+        chain.check()
+        level.check()
+        assert int(lc.item()) == int(ll.item()), (N, n)
+        assert torch.equal(oc, ol), (N, n)
+        M, e, _ = oracle.matpow_f64(A, n)
+        err = oracle.rel_frobenius(oc.cpu().numpy(), int(lc.item()), M, e)
+        assert err <= gate(n, floor_rel(A, n, M, e, "bf16x3")), (N, n, err)
+    # value mode through the chain kernel
+    ov = chain.f32(dA, 5)
+    assert chain.sync() == 0
+    M, e, _ = oracle.matpow_f64(A, 5)
+    want = np.ldexp(M, e)
+    assert np.linalg.norm(ov.cpu().numpy() - want) / np.linalg.norm(want) <= gate(5, floor_rel(A, 5, M, e, "bf16x3"))
+    chain.close()
+    level.close()
