@@ -25,14 +25,18 @@ Functions and the passage each follows:
 * ``round_bf16``, ``split_bf16``: round-to-nearest-even to bfloat16 (8
   significant bits) and the two-part split x ~ hi + lo, hi = bf16(x),
   lo = bf16(x - hi).
-* ``fixed_slices(X)``: the fixed-point split of a matrix scaled by its
-  power-of-two maximum 2^s: u = X 2^(8-s), a1 = rint(u), a2 = rint(256 (u - a1)),
-  so X ~ 2^(s-16) (256 a1 + a2) with integer slices |a1| <= 256, |a2| <= 128.
+* ``fixed_slices(X, block)``: the fixed-point split of a matrix scaled by
+  the power-of-two maximum 2^s of each block x block tile (block=None: one
+  scale for the whole matrix): u = X 2^(8-s), a1 = rint(u),
+  a2 = rint(256 (u - a1)), so X ~ 2^(s-16) (256 a1 + a2) with integer slices
+  |a1| <= 256, |a2| <= 128.
 * ``emu_sqmul(A, n, precision)``: the square-and-multiply chain with the
   operand rounding of a tensor-core precision emulated on the CPU ("bf16":
   one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi of floating
   bfloat16 parts; "bf16x3fx": a1*b1 + a1*b2 + a2*b1 of the fixed-point
-  slices; products and sums in float64, each result rounded to float32).  Like ``fp32_sqmul`` it is an
+  slices with one scale per matrix; "bf16x3blk": the same with one scale per
+  64 x 64 block; products and sums in float64, each result rounded to
+  float32).  Like ``fp32_sqmul`` it is an
   error yardstick for the lower-precision paths, not a parity target; the
   rounding primitives it uses are pinned by the tests.
 
@@ -282,12 +286,21 @@ def split_bf16(x):
     return hi, lo
 
 
-def fixed_slices(X):
-    """(a1, a2, s): X ~ 2^(s-16) (256 a1 + a2), s the frexp exponent of max|X|."""
-    X = np.asarray(X, dtype=np.float32)
-    mx = float(np.max(np.abs(X))) if X.size else 0.0
-    s = math.frexp(mx)[1] if mx > 0.0 else 0
-    u = np.ldexp(X.astype(np.float64), 8 - s)
+def fixed_slices(X, block=None):
+    """(a1, a2, s): X ~ 2^(s-16) (256 a1 + a2), s the frexp exponent of max|X|
+    over the whole matrix (block=None) or over each block x block tile (s is
+    then an array of X's shape holding each entry's tile exponent)."""
+    X = np.asarray(X, dtype=np.float32).astype(np.float64)
+    if block is None:
+        mx = float(np.max(np.abs(X))) if X.size else 0.0
+        s = math.frexp(mx)[1] if mx > 0.0 else 0
+    else:
+        s = np.zeros(X.shape, dtype=np.int64)
+        for i in range(0, X.shape[0], block):
+            for j in range(0, X.shape[1], block):
+                mx = float(np.max(np.abs(X[i:i + block, j:j + block])))
+                s[i:i + block, j:j + block] = math.frexp(mx)[1] if mx > 0.0 else 0
+    u = np.ldexp(X, 8 - s)
     a1 = np.rint(u)
     a2 = np.rint((u - a1) * 256.0)
     return a1, a2, s
@@ -299,6 +312,12 @@ def _emu_product(X, Y, precision: str) -> np.ndarray:
         b1, b2, sy = fixed_slices(Y)
         T = a1 @ b1 + (a1 @ b2 + a2 @ b1) / 256.0
         return np.ldexp(T, sx + sy - 16).astype(np.float32)
+    if precision == "bf16x3blk":
+        a1, a2, sx = fixed_slices(X, 64)
+        b1, b2, sy = fixed_slices(Y, 64)
+        x1, x2 = np.ldexp(a1, sx - 8), np.ldexp(a2, sx - 16)
+        y1, y2 = np.ldexp(b1, sy - 8), np.ldexp(b2, sy - 16)
+        return (x1 @ y1 + x1 @ y2 + x2 @ y1).astype(np.float32)
     if precision == "bf16":
         P = round_bf16(X).astype(np.float64) @ round_bf16(Y).astype(np.float64)
     elif precision == "bf16x3":

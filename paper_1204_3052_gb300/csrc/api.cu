@@ -75,17 +75,16 @@ size_t mp::matrix_bytes(int N, int fmt) {
       return align_up(e * 4, 1024);
     case FMT_BF16:
       return align_up(e * 2, 1024);
-    case FMT_FX2:  // two bfloat16 slices, then the float32 matrix
-      return 2 * align_up(e * 2, 1024) + align_up(e * 4, 1024);
+    case FMT_FX2: {  // two bfloat16 slice planes, then the block exponents
+      size_t nb = ((size_t)N + 63) / 64;
+      return 2 * align_up(e * 2, 1024) + align_up(nb * nb * 4, 1024);
+    }
     default:  // two bfloat16 planes
       return 2 * align_up(e * 2, 1024);
   }
 }
 
-size_t mp::fx2_f32_offset(int N) {
-  size_t ld = (size_t)ld_for(N, FMT_FX2);
-  return 2 * align_up((size_t)N * ld * 2, 1024);
-}
+
 
 long long mp::plane_offset_elems(int N, int fmt) {
   size_t ld = (size_t)ld_for(N, fmt);
@@ -397,23 +396,19 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
   const long long plane = plane_offset_elems(N, fmt);
   const int ld = ld_for(N, fmt);
   const bool fx2 = fmt == FMT_FX2;
-  const size_t f32off = fx2 ? fx2_f32_offset(N) : 0;
   std::vector<LevelOps> levels;
   build_schedule(n, &levels);
   int nslots = 2 + matpow_gemm_count(n);
   CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * nslots, s));
   if (fx2) {
-    // slot 1 describes A itself (exponent 0); the split normalises by max|A|
-    CK(p, launch_absmax_f32(dA, N, &p->scales[1], p->status, s));
-    SplitPair sp{};
-    sp.count = 1;
-    sp.j[0] = SplitJob{dA, p->buf[0], plane, N, N, ld, 1};
-    CK(p, launch_split_fx2(sp, p->scales, s));
+    // slot 1 describes A itself (exponent 0): block slices, max|A|
+    CK(p, launch_prep_fxb(dA, N, p->buf[0], &p->scales[1], p->status, s));
+    p->launches += 1;
   } else {
     CK(p, launch_absmax_f32(dA, N, &p->scales[0], p->status, s));
     CK(p, launch_convert_f32(dA, N, &p->scales[0], &p->scales[1], fmt, p->buf[0], plane, s));
+    p->launches += 2;
   }
-  p->launches += 2;
   const bool tc = p->prec != MATPOW_FP32_SIMT;
   for (size_t li = 0; li < levels.size(); ++li) {
     const LevelOps& lv = levels[li];
@@ -426,7 +421,7 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       GemmDesc& d = g.d[i];
       d.X = p->buf[op.xb];
       d.Y = p->buf[op.yb];
-      d.C = last ? nullptr : (char*)p->buf[op.cb] + f32off;
+      d.C = last ? nullptr : p->buf[op.cb];
       d.out = last ? (void*)dOut : nullptr;
       d.out_log2 = last ? (long long*)dLog2 : nullptr;
       d.plane = plane;
@@ -459,18 +454,6 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
     }
     p->launches++;
-    if (fx2 && li + 1 < levels.size()) {  // slice the level's outputs for the next level
-      SplitPair sp{};
-      sp.count = g.count;
-      for (int i = 0; i < g.count; ++i) {
-        const Op& op = lv.ops[i];
-        sp.j[i] = SplitJob{(const float*)g.d[i].C, p->buf[op.cb], plane, ld, N, ld, op.sc};
-      }
-      timed_begin(p, s, &ev);
-      CK(p, launch_split_fx2(sp, p->scales, s));
-      timed_end(p, s, ev, MATPOW_KERNEL_AUX, 0.0);
-      p->launches++;
-    }
   }
   return MATPOW_OK;
 }

@@ -1,0 +1,232 @@
+// Exact block-scaled split (the default MATPOW_BF16X3 arithmetic).
+//
+// A stored matrix S is cut into 64 x 64 blocks.  Block (I, J) with maximum
+// |S| = m has exponent e = frexp exponent of m (m * 2^-e in [0.5, 1)) and its
+// entries are written as two integer slices
+//     u = s * 2^(8-e),  a1 = rint(u) in [-256, 256],  a2 = rint(256 (u - a1)) in [-128, 128],
+// so s = 2^(e-16) (256 a1 + a2) to within 2^(e-17).  Integers of at most 8
+// significant bits are exact in bfloat16, so the tensor core multiplies them
+// exactly.  For a 64-deep k-block the products sum to
+//     main  = sum a1 b1            (|main|  <= 64 * 2^16 = 2^22)
+//     cross = sum a1 b2 + a2 b1    (|cross| <= 64 * 2^16 = 2^22)
+// which the float32 TMEM accumulator holds exactly whatever its rounding.
+// Each finished k-block is folded into float32 registers with
+// round-to-nearest:
+//     T += (main + cross / 256) * 2^(eX(I,kb) + eY(kb,J) - 16 - sX - sY)
+// where eX, eY are the operands' block exponents and sX, sY their global
+// (frexp) exponents; T is then the product of the two normalised operands
+// (the lagged power-of-two scale of the chain).  The a2*b2 term (2^-16
+// relative) is dropped.  The epilogue re-splits T by 64 x 64 blocks, so no
+// global maximum is needed before the next product can start.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace mp {
+namespace fxb {
+
+constexpr int BLK = 64;
+constexpr int MAX_KB = 512;  // exponent table in shared memory: N <= 32768
+
+__host__ __device__ inline size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
+
+// Byte offset of the block-exponent table (int32, nb x nb) in a stored matrix.
+__host__ __device__ inline size_t bexp_offset(int N, int ld) {
+  return 2 * align1k((size_t)N * ld * 2);
+}
+__host__ __device__ inline int nblocks(int N) { return (N + BLK - 1) / BLK; }
+
+// 2^k as a float, exact for k in [-252, 254] (k below -252 gives 0).
+__device__ __forceinline__ float pow2f(int k) {
+  if (k >= -126 && k <= 127) return __int_as_float((127 + k) << 23);
+  if (k < -252) return 0.f;
+  return mul_pow2(1.0f, k);
+}
+
+__device__ __forceinline__ int frexp_exp(float m) { return scale_exp_from_bits(__float_as_uint(m)); }
+
+__device__ __forceinline__ void slice(float v, int e, float* h, float* l) {
+  const float u = mul_pow2(v, 8 - e);
+  *h = rintf(u);
+  *l = rintf((u - *h) * 256.f);
+}
+
+// Named barrier over the four epilogue warps (warps 4-7 of the CTA).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Epilogue warps 4..7 (q = warp - 4 owns rows 32q..32q+31 of the 128-row
+// tile; rows 64h..64h+63 form block row h = q / 2).  T holds this thread's
+// row `row` of the tile, columns n0..n0+BN-1.  Computes each 64 x 64 block's
+// maximum over the warp pair, writes the block exponents, the two slice
+// planes and folds the block maxima into the matrix maximum (*maxbits).
+// red: shared scratch of 4 * (BN / 64) floats.
+template <int BN>
+__device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int m0, int n0, int q,
+                                             int lane, int N, int ld, __nv_bfloat16* a1p,
+                                             long long plane, int* bexp, unsigned* maxbits,
+                                             float* red) {
+  constexpr int NG = BN / BLK;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < BLK; ++j) m = fmaxf(m, fabsf(T[BLK * g + j]));
+    m = warp_max(m);
+    if (lane == 0) red[q * NG + g] = m;
+  }
+  epi_bar();
+  const int nb = nblocks(N);
+  const int I = m0 / BLK + (q >> 1);
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const float bm = fmaxf(red[q * NG + g], red[(q ^ 1) * NG + g]);
+    const int e = frexp_exp(bm);
+    const int J = n0 / BLK + g;
+    if ((q & 1) == 0 && lane == 0 && I < nb && J < nb) {
+      bexp[I * nb + J] = e;
+      if (bm > 0.f) atomicMax(maxbits, __float_as_uint(bm));
+    }
+    if (row < N) {
+      const int c0 = n0 + BLK * g;
+      __nv_bfloat16* p1 = a1p + (size_t)row * ld + c0;
+      __nv_bfloat16* p2 = p1 + plane;
+      if (c0 + BLK <= N) {
+#pragma unroll
+        for (int g8 = 0; g8 < BLK / 8; ++g8) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            float h0, l0, h1, l1;
+            slice(T[BLK * g + 8 * g8 + 2 * h], e, &h0, &l0);
+            slice(T[BLK * g + 8 * g8 + 2 * h + 1], e, &h1, &l1);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
+            __nv_bfloat162 lo = __floats2bfloat162_rn(l0, l1);
+            hw[h] = *reinterpret_cast<uint32_t*>(&hi);
+            lw[h] = *reinterpret_cast<uint32_t*>(&lo);
+          }
+          *reinterpret_cast<uint4*>(p1 + 8 * g8) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(p2 + 8 * g8) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < BLK; ++j) {
+          if (c0 + j < N) {
+            float h, l;
+            slice(T[BLK * g + j], e, &h, &l);
+            p1[j] = __float2bfloat16_rn(h);
+            p2[j] = __float2bfloat16_rn(l);
+          }
+        }
+      }
+    }
+  }
+  epi_bar();  // red may be reused
+}
+
+// Fold one finished k-block (main at TMEM column tq, cross at tq + BN) into
+// T with the block factors fac[g] (one per 64 columns).
+template <int BN>
+__device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&fac)[BN / BLK]) {
+#pragma unroll
+  for (int c = 0; c < BN / 32; ++c) {
+    uint32_t rm[32], rc[32];
+    ptx::tmem_ld_32x32b_x32(tq + 32 * c, rm);
+    ptx::tmem_ld_32x32b_x32(tq + BN + 32 * c, rc);
+    ptx::tmem_ld_wait();
+    const float f = fac[c / 2];
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      T[32 * c + j] = fmaf(fmaf(__uint_as_float(rc[j]), 0.00390625f, __uint_as_float(rm[j])), f,
+                           T[32 * c + j]);
+  }
+}
+
+// One 64 x 64 block (I, J) of a float32 matrix A (leading dimension N) split
+// into the stored format by a CTA of 256 threads: block exponent, slices,
+// matrix maximum, non-finite check.  red: 8 floats of shared scratch.
+__device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, int ld, int I, int J,
+                                           __nv_bfloat16* a1p, long long plane, int* bexp,
+                                           unsigned* maxbits, unsigned* status, float* red) {
+  const int tid = threadIdx.x;
+  const int r = I * BLK + (tid >> 2);
+  const int c0 = J * BLK + (tid & 3) * 16;
+  float v[16];
+  float m = 0.f;
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    v[j] = (r < N && c0 + j < N) ? A[(size_t)r * N + c0 + j] : 0.f;
+    bad |= !isfinite(v[j]);
+    m = fmaxf(m, fabsf(v[j]));
+  }
+  m = warp_max(m);
+  if ((tid & 31) == 0) red[tid >> 5] = m;
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_BADINPUT);
+  float bm = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) bm = fmaxf(bm, red[w]);
+  const int e = frexp_exp(bm);
+  const int nb = nblocks(N);
+  if (tid == 0) {
+    bexp[I * nb + J] = e;
+    if (bm > 0.f) atomicMax(maxbits, __float_as_uint(bm));
+  }
+  if (r < N && c0 < ld) {
+    __nv_bfloat16* p1 = a1p + (size_t)r * ld + c0;
+    __nv_bfloat16* p2 = p1 + plane;
+    if (c0 + 16 <= ld) {
+#pragma unroll
+      for (int g8 = 0; g8 < 2; ++g8) {
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          float h0, l0, h1, l1;
+          slice(v[8 * g8 + 2 * h], e, &h0, &l0);
+          slice(v[8 * g8 + 2 * h + 1], e, &h1, &l1);
+          __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
+          __nv_bfloat162 lo = __floats2bfloat162_rn(l0, l1);
+          hw[h] = *reinterpret_cast<uint32_t*>(&hi);
+          lw[h] = *reinterpret_cast<uint32_t*>(&lo);
+        }
+        *reinterpret_cast<uint4*>(p1 + 8 * g8) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(p2 + 8 * g8) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (c0 + j < ld) {
+          float h, l;
+          slice(v[j], e, &h, &l);
+          p1[j] = __float2bfloat16_rn(h);
+          p2[j] = __float2bfloat16_rn(l);
+        }
+      }
+    }
+  }
+  __syncthreads();  // red may be reused
+}
+
+// Exponent table of one tile, staged in shared memory by warp 3:
+// eA[h * KB + kb] = eX(I0 + h, kb) for the tile's two block rows,
+// eB[kb * NG + g] = eY(kb, J0 + g) for its BN / 64 block columns.
+template <int BN>
+__device__ __forceinline__ void load_tile_exponents(const int* bexpX, const int* bexpY, int N, int m0,
+                                                    int n0, int KB, int* eA, int* eB, int lane) {
+  constexpr int NG = BN / BLK;
+  const int nb = nblocks(N);
+  const int I0 = m0 / BLK, J0 = n0 / BLK;
+  for (int i = lane; i < 2 * KB; i += 32) {
+    const int h = i / KB, kb = i - h * KB;
+    eA[i] = (I0 + h < nb) ? __ldcg(bexpX + (I0 + h) * nb + kb) : 0;
+  }
+  for (int i = lane; i < NG * KB; i += 32) {
+    const int kb = i / NG, g = i - kb * NG;
+    eB[i] = (J0 + g < nb) ? __ldcg(bexpY + kb * nb + J0 + g) : 0;
+  }
+}
+
+}  // namespace fxb
+}  // namespace mp

@@ -33,8 +33,8 @@ enum Fmt : int {
   FMT_MODP = 3,    // mod-p residues as two byte planes x = 256*x1 + x0 held in
                    // bfloat16 (exact integers 0..255): x1 plane then x0 plane
   FMT_U32 = 4,     // mod-p residues as uint32, leading dimension roundup(N, 4)
-  FMT_FX2 = 5,     // exact split: integer slices a1, a2 (two bfloat16 planes) of the
-                   // normalised matrix, then the float32 matrix itself; ld roundup(N, 8)
+  FMT_FX2 = 5,     // exact block-scaled split: integer slices a1, a2 (two bfloat16
+                   // planes) and an int32 exponent per 64 x 64 block; ld roundup(N, 8)
 };
 
 // Where a product's result goes.
@@ -168,21 +168,10 @@ struct PrepDesc {
   int kind;           // 0: absmax/convert, 1: identity (n = 0), 2: copy (n = 1)
   int pad_;
 };
-// Float32 -> two integer slices (FMT_FX2), up to two matrices per launch.
-struct SplitJob {
-  const float* src;   // float32 matrix, leading dimension src_ld
-  void* dst;          // slice planes (a1 at dst, a2 at dst + plane elements)
-  long long plane;
-  int src_ld;
-  int N;
-  int ld;             // leading dimension of the slices
-  int slot;           // scale slot holding max|src|
-};
-struct SplitPair {
-  SplitJob j[2];
-  int count;
-};
-cudaError_t launch_split_fx2(const SplitPair& sp, Scale* scales, cudaStream_t s);
+// Float32 A (leading dimension N) -> the block-scaled exact split (FMT_FX2)
+// at dst; max|A| folds into slot->maxbits.  One CTA per 64 x 64 block.
+cudaError_t launch_prep_fxb(const float* A, int N, void* dst, Scale* slot, unsigned* status,
+                            cudaStream_t s);
 cudaError_t launch_prep_absmax_group(const PrepDesc* d, int count, int blocks, Scale* scales,
                                      unsigned* status, cudaStream_t s);
 cudaError_t launch_prep_convert_group(const PrepDesc* d, int count, int blocks, Scale* scales,

@@ -8,18 +8,15 @@
 // its TMEM allocation and its mbarrier ring across levels, and the levels are
 // separated by grid-wide barriers:
 //
-//   prep:   max|A| -> barrier -> exact split of A into integer slices -> barrier
-//   level:  tile product (TMA -> tcgen05.mma exact slices -> TMEM chunks ->
-//           float32 registers) -> max|C| -> barrier -> re-split the tile from
-//           registers with the now-known power-of-two scale, store the slices
-//           -> barrier
+//   prep:   block-scaled exact split of A, max|A| -> barrier
+//   level:  tile product (TMA -> tcgen05.mma on integer slices -> exact
+//           64-deep TMEM partial sums -> float32 registers with the block
+//           factors) -> re-split by 64 x 64 blocks straight from registers,
+//           block exponents, max|C| -> barrier
 //   last:   the final product writes the user's float32 output directly.
 //
 // Compared with the level-by-level path this removes every kernel launch but
-// one, the float32 round trip of each partial product, and the split passes.
-// The arithmetic is identical to the exact-split level kernel: integer slices
-// a1, a2 of the normalised operands, exact 256-deep partial sums in TMEM,
-// round-to-nearest folding in float32 registers, lagged power-of-two scales.
+// one.  The arithmetic is that of fxb.cuh, identical to the level kernels'.
 //
 // Every wait is bounded: an mbarrier or grid barrier that gives up sets
 // MATPOW_ETIMEDOUT in the plan's status word, and all CTAs then leave the
@@ -33,6 +30,7 @@
 #include "internal.cuh"
 #include "plan.h"
 #include "tc_ptx.cuh"
+#include "fxb.cuh"
 
 namespace mp {
 
@@ -43,11 +41,13 @@ constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int SMEM_RING = 192 * 1024;
 template <int BN>
 struct Cfg {
+  static constexpr int NG = BN / fxb::BLK;
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
   static constexpr int STAGES = SMEM_RING / STAGE_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
+  static constexpr int KB_MAX = 16;  // N <= 1024
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256 + (2 + NG) * KB_MAX * 4 + 64;
   static constexpr int TMEM_COLS = 4 * BN;
 };
 struct Op {
@@ -60,6 +60,7 @@ struct ChainParams {
   CUtensorMap amap[4][2];  // buffer b as the A operand: slices a1, a2 (box 64 x 128)
   CUtensorMap bmap[4][2];  // buffer b as the B operand: slices a1, a2 (box 64 x 64)
   void* slices[4];         // slice a1 plane of buffer b (a2 at + plane elements)
+  int* bexp[4];            // block exponents of buffer b
   long long plane;
   const float* A;
   float* out;
@@ -121,7 +122,12 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   // full[S], empty[S], accfull[2], accempty[2], drain
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* epi_ok = (volatile int*)(tmem_slot + 2);
   float* red = (float*)(tmem_slot + 4);  // 8 floats
+  constexpr int NG = C::NG;
+  int* eA = (int*)(smem + STAGES * C::STAGE_BYTES + 256);
+  int* eB = eA + 2 * C::KB_MAX;
+  float* ered = (float*)(eB + NG * C::KB_MAX);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
   const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
@@ -131,7 +137,6 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = P.N, ld = P.ld;
   const int KB = (N + BK - 1) / BK;
-  const int NCH = (KB + CHUNK_KB - 1) / CHUNK_KB;
   const unsigned G = gridDim.x;
   unsigned bar_no = 0;
 
@@ -152,49 +157,31 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
     ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
     ptx::tmem_relinquish();
   }
+  if (warp == 0 && lane == 0) {
+    for (int b = 0; b < 4; ++b) {
+      ptx::prefetch_tmap(&P.amap[b][0]);
+      ptx::prefetch_tmap(&P.amap[b][1]);
+      ptx::prefetch_tmap(&P.bmap[b][0]);
+      ptx::prefetch_tmap(&P.bmap[b][1]);
+    }
+  }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // ---- prep: max|A|, then the exact split of A into buffer 0
+  // ---- prep: block-scaled exact split of A into buffer 0, max|A| into slot 1
   {
-    const size_t total = (size_t)N * N;
-    float m = 0.f;
-    bool bad = false;
-    for (size_t i = blockIdx.x * (size_t)THREADS + threadIdx.x; i < total; i += (size_t)G * THREADS) {
-      const float v = P.A[i];
-      bad |= !isfinite(v);
-      m = fmaxf(m, fabsf(v));
-    }
-    m = warp_max(m);
-    if (lane == 0) red[warp] = m;
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.status, ST_BADINPUT);
-    if (threadIdx.x == 0) {
-      float mm = red[0];
-      for (int w = 1; w < THREADS / 32; ++w) mm = fmaxf(mm, red[w]);
-      if (mm > 0.f) atomicMax(&P.scales[1].maxbits, __float_as_uint(mm));
-    }
-  }
-  grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag);
-  if (!*abort_flag) {
-    const int s = scale_exp_from_bits(__ldcg(&P.scales[1].maxbits));
-    __nv_bfloat16* a1 = (__nv_bfloat16*)P.slices[0];
-    __nv_bfloat16* a2 = a1 + P.plane;
-    const size_t total = (size_t)N * ld;
-    for (size_t i = blockIdx.x * (size_t)THREADS + threadIdx.x; i < total; i += (size_t)G * THREADS) {
-      const size_t r = i / ld;
-      const int c = (int)(i - r * ld);
-      const float u = c < N ? mul_pow2(P.A[r * N + c], 8 - s) : 0.f;
-      const float h = rintf(u);
-      a1[i] = __float2bfloat16_rn(h);
-      a2[i] = __float2bfloat16_rn(rintf((u - h) * 256.f));
-    }
+    const int nb = fxb::nblocks(N);
+    for (int b = blockIdx.x; b < nb * nb; b += G)
+      fxb::prep_block(P.A, N, ld, b / nb, b % nb, (__nv_bfloat16*)P.slices[0], P.plane, P.bexp[0],
+                      &P.scales[1].maxbits, P.status, red);
     fence_proxy_async_global();
   }
   grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag);
+  fence_proxy_async_global();
 
-  int kb_base = 0, ch_base = 0;  // ring and accumulator-buffer counters (per CTA)
+  int kb_base = 0;  // k-blocks done by this CTA: ring and accumulator-buffer phases
   float T[BN];
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
     const int nops = P.lvl_nops[L];
@@ -242,13 +229,10 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
           constexpr uint32_t idesc = idesc_bf16(BM, BN);
           for (int kb = 0; kb < KB; ++kb) {
             const int g = kb_base + kb;
-            const int ch = ch_base + kb / CHUNK_KB;
-            const int buf = ch & 1;
-            const bool first = (kb % CHUNK_KB) == 0;
-            const bool last = (kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1;
+            const int buf = g & 1;
             const uint32_t t_main = tmem + (uint32_t)(buf * 2 * BN);
             const uint32_t t_cross = t_main + BN;
-            if (first && !ptx::mbar_wait(accempty0 + 8 * buf, ((ch >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
+            if (!ptx::mbar_wait(accempty0 + 8 * buf, ((g >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
               *abort_flag = 1;
               break;
             }
@@ -268,116 +252,77 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
               const uint64_t ad2 = ptx::smem_desc(a2 + 32 * k, 16, 1024);
               const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
               const uint64_t bd2 = ptx::smem_desc(b2 + 2048 * k, 8192, 1024);
-              const uint32_t acc = (first && k == 0) ? 0u : 1u;
+              const uint32_t acc = k == 0 ? 0u : 1u;
               ptx::mma_f16(t_main, ad1, bd1, idesc, acc);
               ptx::mma_f16(t_cross, ad1, bd2, idesc, acc);
               ptx::mma_f16(t_cross, ad2, bd1, idesc, 1);
             }
             ptx::mma_commit(empty0 + 8 * s);
-            if (last) ptx::mma_commit(accfull0 + 8 * buf);
+            ptx::mma_commit(accfull0 + 8 * buf);
           }
         }
+      } else if (warp == 3) {
+        fxb::load_tile_exponents<BN>(P.bexp[op.xb], P.bexp[op.yb], N, m0, n0, KB, eA, eB, lane);
+        __syncwarp();
+        asm volatile("bar.arrive 2, 160;" ::: "memory");
       } else if (warp >= 4) {
-#pragma unroll
-        for (int j = 0; j < BN; ++j) T[j] = 0.f;
-        for (int cc = 0; cc < NCH; ++cc) {
-          const int ch = ch_base + cc;
-          const int buf = ch & 1;
-          int dummy = 0;
-          if (!ptx::mbar_wait(accfull0 + 8 * buf, (ch >> 1) & 1, &dummy, 2 * WAIT_NS)) {
-            *abort_flag = 1;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN);
-#pragma unroll
-          for (int c = 0; c < BN / 32; ++c) {
-            uint32_t rm[32], rc[32];
-            ptx::tmem_ld_32x32b_x32(tq + 32 * c, rm);
-            ptx::tmem_ld_32x32b_x32(tq + BN + 32 * c, rc);
-            ptx::tmem_ld_wait();
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              T[32 * c + j] += __uint_as_float(rm[j]) + __uint_as_float(rc[j]) * 0.00390625f;
-          }
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
-        }
-        // stored value of the normalised-operand product
-#pragma unroll
-        for (int j = 0; j < BN; ++j) T[j] *= 1.52587890625e-05f;  // 2^-16
+        const int h = q >> 1;
         // scale slots are written by other CTAs: read them from L2, not L1
         const int sx = scale_exp_from_bits(__ldcg(&P.scales[op.sx].maxbits));
         const int sy = scale_exp_from_bits(__ldcg(&P.scales[op.sy].maxbits));
         const long long Ec = __ldcg(&P.scales[op.sx].E) + __ldcg(&P.scales[op.sy].E) + sx + sy;
-        if (op.last) {
-          if (t == 0 && q == 0 && lane == 0 && P.out_log2) *P.out_log2 = Ec;
-          if (row < N) {
-            float* O = P.out + (size_t)row * N;
 #pragma unroll
-            for (int j = 0; j < BN; ++j) {
-              const int c = n0 + j;
-              if (c < N) O[c] = P.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+        for (int j = 0; j < BN; ++j) T[j] = 0.f;
+        asm volatile("bar.sync 2, 160;" ::: "memory");  // exponents staged
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb) {
+          const int g = kb_base + kb;
+          const int buf = g & 1;
+          int dummy = 0;
+          if (!ptx::mbar_wait(accfull0 + 8 * buf, (g >> 1) & 1, &dummy, 2 * WAIT_NS)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          float fac[NG];
+#pragma unroll
+          for (int gg = 0; gg < NG; ++gg)
+            fac[gg] = fxb::pow2f(eA[h * KB + kb] + eB[kb * NG + gg] - 16 - sx - sy);
+          fxb::fold<BN>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN), fac);
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
+        }
+        // one verdict for all four epilogue warps (they share named barriers below)
+        fxb::epi_bar();
+        if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
+        fxb::epi_bar();
+        ok = *epi_ok != 0;
+        if (op.last) {
+          if (ok) {
+            if (t == 0 && q == 0 && lane == 0 && P.out_log2) *P.out_log2 = Ec;
+            if (row < N) {
+              float* O = P.out + (size_t)row * N;
+#pragma unroll
+              for (int j = 0; j < BN; ++j) {
+                const int c = n0 + j;
+                if (c < N) O[c] = P.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+              }
             }
           }
         } else {
           if (t == 0 && q == 0 && lane == 0) P.scales[op.sc].E = Ec;
-          float mx = 0.f;
-          if (row < N) {
-#pragma unroll
-            for (int j = 0; j < BN; ++j)
-              if (n0 + j < N) mx = fmaxf(mx, fabsf(T[j]));
-          }
-          mx = warp_max(mx);
-          if (lane == 0 && mx > 0.f) atomicMax(&P.scales[op.sc].maxbits, __float_as_uint(mx));
+          if (ok)
+            fxb::store_slices<BN>(T, row, m0, n0, q, lane, N, ld, (__nv_bfloat16*)P.slices[op.cb],
+                                  P.plane, P.bexp[op.cb], &P.scales[op.sc].maxbits, ered);
+          fence_proxy_async_global();
         }
       }
-    }
-    if (has) {  // ring and accumulator counters advance only with work done
-      kb_base += KB;
-      ch_base += NCH;
+      kb_base += KB;  // ring and accumulator counters advance only with work done
     }
     if (P.ops[2 * L + nops - 1].last) break;  // the final product has been written
-    // all maxima of this level are in
-    if (!grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag)) break;
-    if (has && warp >= 4 && !op.last) {
-      const int s = scale_exp_from_bits(__ldcg(&P.scales[op.sc].maxbits));
-      if (row < N) {
-        __nv_bfloat16* a1 = (__nv_bfloat16*)P.slices[op.cb] + (size_t)row * ld + n0;
-        __nv_bfloat16* a2 = a1 + P.plane;
-        if (n0 + BN <= N) {
-#pragma unroll
-          for (int g8 = 0; g8 < BN / 8; ++g8) {
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const float u0 = mul_pow2(T[8 * g8 + 2 * h], 8 - s);
-              const float u1 = mul_pow2(T[8 * g8 + 2 * h + 1], 8 - s);
-              const float h0 = rintf(u0), h1 = rintf(u1);
-              __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
-              __nv_bfloat162 lo = __floats2bfloat162_rn(rintf((u0 - h0) * 256.f), rintf((u1 - h1) * 256.f));
-              hw[h] = *reinterpret_cast<uint32_t*>(&hi);
-              lw[h] = *reinterpret_cast<uint32_t*>(&lo);
-            }
-            *reinterpret_cast<uint4*>(a1 + 8 * g8) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4*>(a2 + 8 * g8) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < BN; ++j) {
-            if (n0 + j < N) {
-              const float u = mul_pow2(T[j], 8 - s);
-              const float h = rintf(u);
-              a1[j] = __float2bfloat16_rn(h);
-              a2[j] = __float2bfloat16_rn(rintf((u - h) * 256.f));
-            }
-          }
-        }
-      }
-      fence_proxy_async_global();
-    }
-    // the slices of this level are visible to every CTA's TMA
+    // this level's slices, exponents and maxima are visible to every CTA
     if (!grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag)) break;
     fence_proxy_async_global();
   }
@@ -438,6 +383,7 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
   for (int b = 0; b < 4; ++b) {
     const char* base = (const char*)p->buf[b];
     P.slices[b] = p->buf[b];
+    P.bexp[b] = (int*)((char*)p->buf[b] + fxb::bexp_offset(N, ld_for(N, FMT_FX2)));
     if (!tc_encode_bf16_map(&P.amap[b][0], base, N, ld, 64, chain::BM) ||
         !tc_encode_bf16_map(&P.amap[b][1], base + plane * 2, N, ld, 64, chain::BM) ||
         !tc_encode_bf16_map(&P.bmap[b][0], base, N, ld, 64, 64) ||

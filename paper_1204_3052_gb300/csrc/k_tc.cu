@@ -33,6 +33,7 @@
 #include "internal.cuh"
 #include "plan.h"
 #include "tc_ptx.cuh"
+#include "fxb.cuh"
 
 namespace mp {
 
@@ -262,44 +263,45 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Exact split products (BF16X3 default).  Each stored float32 matrix S with
-// max|S| = m, s = frexp exponent of m, is split into two integer slices
-//   u = S * 2^(8-s),  a1 = rint(u) in [-256, 256],  a2 = rint(256 (u - a1)) in [-128, 128],
-// so S = 2^(s-16) (256 a1 + a2) to within 2^(s-17).  Integers of at most 8
-// significant bits are exact in bfloat16, every product a*b is an exact
-// integer of at most 16 bits, and a 256-deep sum of them stays below 2^24,
-// so the float32 TMEM accumulator holds it exactly whatever rounding the
-// tensor core applies.  The three products a1*b1 (main) and a1*b2 + a2*b1
-// (cross) accumulate in two TMEM accumulators per 256-deep K chunk; the
-// epilogue warps fold each finished chunk into float32 registers with
-// round-to-nearest (T += main + cross/256) while the MMA fills the other
-// buffer.  The product of the two normalised operands is T * 2^-16.
+// Exact block-scaled split products (BF16X3 default; arithmetic in fxb.cuh).
+// Same warp roles as above, plus warp 3, which stages the tile's block
+// exponents in shared memory.  The MMA accumulates each 64-deep k-block into
+// one of two TMEM buffers (main, cross); the epilogue warps fold finished
+// k-blocks into float32 registers with the block factors while the MMA fills
+// the other buffer, then re-split the tile by 64 x 64 blocks straight into the
+// next product's operand planes.
 
 namespace fx {
-constexpr int CHUNK_KB = 4;  // 4 x 64 = 256-deep chunks
 template <int BN>
 struct Cfg {
+  static constexpr int NG = BN / fxb::BLK;
   static constexpr int A_BYTES = tc::BM * tc::BK * 2;
   static constexpr int B_BYTES = BN * tc::BK * 2;
   static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
   static constexpr int STAGES = tc::SMEM_RING / STAGE_BYTES;
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int EXP_BYTES = (2 + NG) * fxb::MAX_KB * 4;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256 + EXP_BYTES + 64;
   static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x (main, cross)
 };
 }  // namespace fx
 
 template <int BN>
 __global__ void __launch_bounds__(tc::THREADS, 1)
-    tc_fx2_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
+    tc_fxb_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
   using namespace tc;
   using C = fx::Cfg<BN>;
   constexpr int STAGES = C::STAGES;
+  constexpr int NG = C::NG;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
   // full[S], empty[S], accfull[2], accempty[2], drain
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* epi_ok = (volatile int*)(tmem_slot + 2);
+  int* eA = (int*)(smem + STAGES * C::STAGE_BYTES + 256);
+  int* eB = eA + 2 * fxb::MAX_KB;
+  float* red = (float*)(eB + NG * fxb::MAX_KB);
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
   const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
@@ -316,7 +318,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   const int m0 = tm * BM, n0 = tn * BN;
   const int N = d.N;
   const int KB = (N + BK - 1) / BK;
-  const int NCH = (KB + fx::CHUNK_KB - 1) / fx::CHUNK_KB;
+  const size_t boff = fxb::bexp_offset(N, d.ld);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -378,23 +380,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      bool ok = true;
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        const int ch = kb / fx::CHUNK_KB;
-        const int buf = ch & 1;
-        const bool first = (kb % fx::CHUNK_KB) == 0;
-        const bool last = (kb % fx::CHUNK_KB) == fx::CHUNK_KB - 1 || kb == KB - 1;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int buf = kb & 1;
         const uint32_t t_main = tmem + (uint32_t)(buf * 2 * BN);
         const uint32_t t_cross = t_main + BN;
-        if (first && !ptx::mbar_wait(accempty0 + 8 * buf, ((ch >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
+        if (!ptx::mbar_wait(accempty0 + 8 * buf, ((kb >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
           *abort_flag = 1;
           break;
         }
         const int s = kb % STAGES;
-        const uint32_t ph = (kb / STAGES) & 1;
-        if (!ptx::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_NS)) {
+        if (!ptx::mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, abort_flag, WAIT_NS)) {
           *abort_flag = 1;
-          ok = false;
           break;
         }
         ptx::tc_fence_after();
@@ -408,94 +404,72 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           const uint64_t ad2 = ptx::smem_desc(a2 + 32 * k, 16, 1024);
           const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
           const uint64_t bd2 = ptx::smem_desc(b2 + 2048 * k, 8192, 1024);
-          const uint32_t acc = (first && k == 0) ? 0u : 1u;
+          const uint32_t acc = k == 0 ? 0u : 1u;
           ptx::mma_f16(t_main, ad1, bd1, idesc, acc);
           ptx::mma_f16(t_cross, ad1, bd2, idesc, acc);
           ptx::mma_f16(t_cross, ad2, bd1, idesc, 1);
         }
         ptx::mma_commit(empty0 + 8 * s);
-        if (last) ptx::mma_commit(accfull0 + 8 * buf);
+        ptx::mma_commit(accfull0 + 8 * buf);
       }
-      // every MMA of this thread has finished before TMEM can be freed
       ptx::mma_commit(drainb);
       int dummy = 0;
       ptx::mbar_wait(drainb, 0, &dummy, WAIT_NS);
     }
+  } else if (warp == 3) {
+    fxb::load_tile_exponents<BN>((const int*)((const char*)d.X + boff),
+                                 (const int*)((const char*)d.Y + boff), N, m0, n0, KB, eA, eB, lane);
+    __syncwarp();
+    asm volatile("bar.arrive 2, 160;" ::: "memory");
   } else if (warp >= 4) {
     const int q = warp - 4;
+    const int h = q >> 1;
     const int row = m0 + 32 * q + lane;
+    const int sx = scale_exp_from_bits(scales[d.sx].maxbits);
+    const int sy = scale_exp_from_bits(scales[d.sy].maxbits);
     float T[BN];
 #pragma unroll
     for (int j = 0; j < BN; ++j) T[j] = 0.f;
+    asm volatile("bar.sync 2, 160;" ::: "memory");  // exponents staged
     bool ok = true;
-    for (int ch = 0; ch < NCH; ++ch) {
-      const int buf = ch & 1;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int buf = kb & 1;
       int dummy = 0;
-      if (!ptx::mbar_wait(accfull0 + 8 * buf, (ch >> 1) & 1, &dummy, 2 * WAIT_NS)) {
+      if (!ptx::mbar_wait(accfull0 + 8 * buf, (kb >> 1) & 1, &dummy, 2 * WAIT_NS)) {
         *abort_flag = 1;
         ok = false;
         break;
       }
       ptx::tc_fence_after();
-      const uint32_t t_main = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN);
+      float fac[NG];
 #pragma unroll
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t rm[32], rc[32];
-        ptx::tmem_ld_32x32b_x32(t_main + 32 * c, rm);
-        ptx::tmem_ld_32x32b_x32(t_main + BN + 32 * c, rc);
-        ptx::tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          T[32 * c + j] += __uint_as_float(rm[j]) + __uint_as_float(rc[j]) * 0.00390625f;
-      }
+      for (int g = 0; g < NG; ++g) fac[g] = fxb::pow2f(eA[h * KB + kb] + eB[kb * NG + g] - 16 - sx - sy);
+      fxb::fold<BN>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN), fac);
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
     }
-    if (ok && !*abort_flag) {
-      const int sx = scale_exp_from_bits(scales[d.sx].maxbits);
-      const int sy = scale_exp_from_bits(scales[d.sy].maxbits);
-      const long long Ec = scales[d.sx].E + scales[d.sy].E + sx + sy;
-      if (t == 0 && q == 0 && lane == 0) {
-        if (d.mode == OUT_INTERNAL) scales[d.sc].E = Ec;
-        if (d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
-      }
-      float mx = 0.f;
+    // one verdict for all four epilogue warps (they share named barriers below)
+    fxb::epi_bar();
+    if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
+    fxb::epi_bar();
+    ok = *epi_ok != 0;
+    const long long Ec = scales[d.sx].E + scales[d.sy].E + sx + sy;
+    if (d.mode == OUT_INTERNAL) {
+      if (t == 0 && q == 0 && lane == 0) scales[d.sc].E = Ec;
+      if (ok)  // every epilogue warp reaches the named barriers inside
+        fxb::store_slices<BN>(T, row, m0, n0, q, lane, N, d.ld, (__nv_bfloat16*)d.C, d.plane,
+                              (int*)((char*)d.C + boff), &scales[d.sc].maxbits, red);
+    } else if (ok) {
+      if (t == 0 && q == 0 && lane == 0 && d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
       if (row < N) {
-        if (d.mode == OUT_INTERNAL) {
-          float* Crow = (float*)d.C + (size_t)row * d.ld;
+        float* O = (float*)d.out + (size_t)row * N;
+        const bool mant = d.mode == OUT_USER_MANT;
 #pragma unroll
-          for (int j4 = 0; j4 < BN / 4; ++j4) {
-            const int c = n0 + 4 * j4;
-            float4 v = make_float4(T[4 * j4] * 1.52587890625e-05f, T[4 * j4 + 1] * 1.52587890625e-05f,
-                                   T[4 * j4 + 2] * 1.52587890625e-05f, T[4 * j4 + 3] * 1.52587890625e-05f);
-            if (c + 3 < N) {
-              *reinterpret_cast<float4*>(Crow + c) = v;
-              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-            } else {
-              const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                if (c + j < N) {
-                  Crow[c + j] = vv[j];
-                  mx = fmaxf(mx, fabsf(vv[j]));
-                }
-            }
-          }
-        } else {
-          float* O = (float*)d.out + (size_t)row * N;
-          const bool mant = d.mode == OUT_USER_MANT;
-#pragma unroll
-          for (int j = 0; j < BN; ++j) {
-            const int c = n0 + j;
-            const float v = T[j] * 1.52587890625e-05f;  // 2^-16
-            if (c < N) O[c] = mant ? v : final_value(v, Ec, status);
-          }
+        for (int j = 0; j < BN; ++j) {
+          const int c = n0 + j;
+          if (c < N) O[c] = mant ? T[j] : final_value(T[j], Ec, status);
         }
-      }
-      if (d.mode == OUT_INTERNAL) {
-        mx = warp_max(mx);
-        if (lane == 0 && mx > 0.f) atomicMax(&scales[d.sc].maxbits, __float_as_uint(mx));
       }
     }
   }
@@ -508,25 +482,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
 }
 
-// Split float32 matrices into the two integer slices above (grouped, <= 2).
-__global__ void split_fx2_kernel(const __grid_constant__ SplitPair sp, Scale* scales) {
-  const int which = (sp.count > 1 && blockIdx.y == 1) ? 1 : 0;
-  const SplitJob& j = sp.j[which];
-  const int s = scale_exp_from_bits(scales[j.slot].maxbits);
-  const int N = j.N, ld = j.ld;
-  __nv_bfloat16* a1 = (__nv_bfloat16*)j.dst;
-  __nv_bfloat16* a2 = a1 + j.plane;
-  const size_t total = (size_t)N * ld;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = i / ld;
-    const int c = (int)(i - r * ld);
-    float u = c < N ? mul_pow2(j.src[r * j.src_ld + c], 8 - s) : 0.f;
-    const float h = rintf(u);
-    const float l = rintf((u - h) * 256.f);
-    a1[i] = __float2bfloat16_rn(h);
-    a2[i] = __float2bfloat16_rn(l);
-  }
+// A (float32, leading dimension N) -> block-scaled stored format, one CTA per
+// 64 x 64 block.
+__global__ void __launch_bounds__(256) prep_fxb_kernel(const float* __restrict__ A, int N, int ld,
+                                                       __nv_bfloat16* dst, long long plane,
+                                                       int* bexp, unsigned* maxbits,
+                                                       unsigned* status) {
+  __shared__ float red[8];
+  const int nb = fxb::nblocks(N);
+  const int I = blockIdx.x / nb, J = blockIdx.x - (blockIdx.x / nb) * nb;
+  fxb::prep_block(A, N, ld, I, J, dst, plane, bexp, maxbits, status, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -558,10 +523,10 @@ cudaError_t tc_init(matpow_plan_s*) {
   if ((e = set_attr<64, 2>()) != cudaSuccess) return e;
   if ((e = set_attr<128, 2>()) != cudaSuccess) return e;
   if ((e = set_attr<256, 2>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(tc_fx2_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(tc_fxb_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 fx::Cfg<64>::SMEM)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(tc_fx2_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(tc_fxb_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               fx::Cfg<128>::SMEM);
 }
 
@@ -579,6 +544,8 @@ static int pick_bn(matpow_plan_s* p, int N) {
 }
 
 matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc* d, int* ntiles) {
+  if (plan_float_fmt(p) == FMT_FX2 && d->N > fxb::MAX_KB * fxb::BLK)
+    return fail(p, MATPOW_EUNSUPPORTED, "exact split: N=%d above %d", d->N, fxb::MAX_KB * fxb::BLK);
   d->bn = pick_bn(p, d->N);
   d->tiles_n = (d->N + d->bn - 1) / d->bn;
   *ntiles = ((d->N + tc::BM - 1) / tc::BM) * d->tiles_n;
@@ -632,9 +599,9 @@ matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s
   cudaError_t e;
   if (fmt == FMT_FX2) {
     if (bn == 64)
-      tc_fx2_kernel<64><<<g.tiles_total, tc::THREADS, fx::Cfg<64>::SMEM, s>>>(P, p->scales, p->status);
+      tc_fxb_kernel<64><<<g.tiles_total, tc::THREADS, fx::Cfg<64>::SMEM, s>>>(P, p->scales, p->status);
     else
-      tc_fx2_kernel<128><<<g.tiles_total, tc::THREADS, fx::Cfg<128>::SMEM, s>>>(P, p->scales, p->status);
+      tc_fxb_kernel<128><<<g.tiles_total, tc::THREADS, fx::Cfg<128>::SMEM, s>>>(P, p->scales, p->status);
     e = cudaGetLastError();
   } else if (PL == 2)
     e = bn == 64 ? launch<64, 2>(P, g.tiles_total, p->scales, p->status, s)
@@ -655,15 +622,14 @@ matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc*, int, int, Scale
 }  // namespace mp
 
 namespace mp {
-cudaError_t launch_split_fx2(const SplitPair& sp, Scale* scales, cudaStream_t s) {
-  size_t mx = 0;
-  for (int i = 0; i < sp.count; ++i) {
-    size_t e = (size_t)sp.j[i].N * sp.j[i].ld;
-    if (e > mx) mx = e;
-  }
-  size_t b = (mx + 255) / 256;
-  int gx = (int)(b < 1216 ? (b ? b : 1) : 1216);
-  split_fx2_kernel<<<dim3(gx, sp.count), 256, 0, s>>>(sp, scales);
+cudaError_t launch_prep_fxb(const float* A, int N, void* dst, Scale* slot, unsigned* status,
+                            cudaStream_t s) {
+  const int ld = ld_for(N, FMT_FX2);
+  const int nb = fxb::nblocks(N);
+  const long long plane = plane_offset_elems(N, FMT_FX2);
+  int* bexp = (int*)((char*)dst + fxb::bexp_offset(N, ld));
+  prep_fxb_kernel<<<nb * nb, 256, 0, s>>>(A, N, ld, (__nv_bfloat16*)dst, plane, bexp, &slot->maxbits,
+                                          status);
   return cudaGetLastError();
 }
 }  // namespace mp

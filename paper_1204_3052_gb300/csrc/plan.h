@@ -111,7 +111,6 @@ size_t matrix_bytes(int N, int fmt);
 long long plane_offset_elems(int N, int fmt);
 int float_fmt(matpow_precision p);
 int plan_float_fmt(const matpow_plan_s* p);  // float_fmt, with the split option applied
-size_t fx2_f32_offset(int N);                // byte offset of the float32 matrix in FMT_FX2
 cudaEvent_t take_event(matpow_plan_s* p);
 void timed_begin(matpow_plan_s* p, cudaStream_t s, cudaEvent_t* ev);
 void timed_end(matpow_plan_s* p, cudaStream_t s, cudaEvent_t ev, int kind, double flop);

@@ -412,3 +412,22 @@ def test_emulated_fixed_split_close_to_float_split():
     # 16-bit fixed point relative to the matrix maximum keeps fewer bits of
     # the small entries than a per-entry 16-bit split: larger, but bounded
     assert efl < efx < 30 * efl and efx < 1e-3
+
+
+def test_block_fixed_slices_reconstruct_per_block():
+    g = wl.rng(14)
+    X = (g.standard_normal((130, 130)) * np.exp(g.standard_normal((130, 130)))).astype(np.float32)
+    a1, a2, s = oracle.fixed_slices(X, 64)
+    assert np.all(np.abs(a1) <= 256) and np.all(np.abs(a2) <= 128)
+    rec = np.ldexp(256.0 * a1 + a2, s - 16)
+    assert np.all(np.abs(rec - X) <= np.ldexp(1.0, s - 17))
+    # each tile's own maximum sets its exponent
+    for i in range(0, 130, 64):
+        for j in range(0, 130, 64):
+            t = np.abs(X[i:i + 64, j:j + 64]).max()
+            assert 0.5 <= t * 2.0 ** -s[i, j] < 1.0
+    # the block emulator agrees with the global one when one block covers the matrix
+    A = wl.gaussian(60, 3)
+    Mb, eb = oracle.emu_sqmul(A, 9, "bf16x3blk")
+    Mg, eg = oracle.emu_sqmul(A, 9, "bf16x3fx")
+    assert oracle.rel_frobenius(Mb, eb, Mg, eg) < 1e-6

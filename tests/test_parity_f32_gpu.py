@@ -21,7 +21,7 @@ PRECS = ["fp32", "bf16x3", "bf16"]
 # (two 8-bit slices of a matrix whose maximum is below 2^16) and sums them
 # exactly; a bfloat16 operand holds integers < 2^8.
 FIB_EXACT = {"fp32": 34, "bf16x3": 23, "bf16": 12}
-EMU = {"bf16": "bf16", "bf16x3": "bf16x3fx"}
+EMU = {"bf16": "bf16", "bf16x3": "bf16x3blk"}
 
 
 @pytest.fixture(scope="module")
