@@ -54,8 +54,11 @@ __device__ __forceinline__ void slice(float v, int e, float* h, float* l) {
   *l = rintf((u - *h) * 256.f);
 }
 
-// Named barrier over the four epilogue warps (warps 4-7 of the CTA).
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier 1 over the NT epilogue threads (warps 4.. of the CTA).
+template <int NT = 128>
+__device__ __forceinline__ void epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
 
 // Epilogue warps 4..7 (q = warp - 4 owns rows 32q..32q+31 of the 128-row
 // tile; rows 64h..64h+63 form block row h = q / 2).  T holds this thread's
@@ -63,7 +66,9 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 // maximum over the warp pair, writes the block exponents, the two slice
 // planes and folds the block maxima into the matrix maximum (*maxbits).
 // red: shared scratch of 4 * (BN / 64) floats.
-template <int BN>
+// (WC columns per epilogue warp starting at n0; NT epilogue threads share
+// named barrier 1; red is this column slice's 4 x (WC / 64) scratch.)
+template <int BN, int NT = 128>
 __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int m0, int n0, int q,
                                              int lane, int N, int ld, __nv_bfloat16* a1p,
                                              long long plane, int* bexp, unsigned* maxbits,
@@ -77,7 +82,7 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
     m = warp_max(m);
     if (lane == 0) red[q * NG + g] = m;
   }
-  epi_bar();
+  epi_bar<NT>();
   const int nb = nblocks(N);
   const int I = m0 / BLK + (q >> 1);
 #pragma unroll
@@ -123,18 +128,19 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
       }
     }
   }
-  epi_bar();  // red may be reused
+  epi_bar<NT>();  // red may be reused
 }
 
-// Fold one finished k-block (main at TMEM column tq, cross at tq + BN) into
-// T with the block factors fac[g] (one per 64 columns).
+// Fold one finished k-block (main at TMEM column tq, cross at tq + cross_off)
+// into T with the block factors fac[g] (one per 64 columns).
 template <int BN>
-__device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&fac)[BN / BLK]) {
+__device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&fac)[BN / BLK],
+                                     uint32_t cross_off = BN) {
 #pragma unroll
   for (int c = 0; c < BN / 32; ++c) {
     uint32_t rm[32], rc[32];
     ptx::tmem_ld_32x32b_x32(tq + 32 * c, rm);
-    ptx::tmem_ld_32x32b_x32(tq + BN + 32 * c, rc);
+    ptx::tmem_ld_32x32b_x32(tq + cross_off + 32 * c, rc);
     ptx::tmem_ld_wait();
     const float f = fac[c / 2];
 #pragma unroll

@@ -274,6 +274,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 namespace fx {
 template <int BN>
 struct Cfg {
+  // epilogue warps: 4 lane quadrants x CS column slices of WC columns each
+  static constexpr int CS = BN / 64;
+  static constexpr int WC = BN / CS;
+  static constexpr int EW = 4 * CS;
+  static constexpr int THREADS = 128 + 32 * EW;
   static constexpr int NG = BN / fxb::BLK;
   static constexpr int A_BYTES = tc::BM * tc::BK * 2;
   static constexpr int B_BYTES = BN * tc::BK * 2;
@@ -286,10 +291,11 @@ struct Cfg {
 }  // namespace fx
 
 template <int BN>
-__global__ void __launch_bounds__(tc::THREADS, 1)
+__global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
     tc_fxb_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
   using namespace tc;
   using C = fx::Cfg<BN>;
+  constexpr int EW = C::EW, WC = C::WC;
   constexpr int STAGES = C::STAGES;
   constexpr int NG = C::NG;
   extern __shared__ uint8_t smem_raw[];
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(accfull0 + 8 * b, 1);
-      ptx::mbar_init(accempty0 + 8 * b, 4);  // one arrival per epilogue warp
+      ptx::mbar_init(accempty0 + 8 * b, EW);  // one arrival per epilogue warp
     }
     ptx::mbar_init(drainb, 1);
     *abort_flag = 0;
@@ -420,17 +426,22 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     fxb::load_tile_exponents<BN>((const int*)((const char*)d.X + boff),
                                  (const int*)((const char*)d.Y + boff), N, m0, n0, KB, eA, eB, lane);
     __syncwarp();
-    asm volatile("bar.arrive 2, 160;" ::: "memory");
+    asm volatile("bar.arrive 2, %0;" ::"n"(32 + 32 * EW) : "memory");
   } else if (warp >= 4) {
-    const int q = warp - 4;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows) and one slice
+    // of WC columns
+    const int e = warp - 4;
+    const int q = warp & 3;
+    const int cs = e >> 2;
     const int h = q >> 1;
     const int row = m0 + 32 * q + lane;
+    const int nw = n0 + cs * WC;
     const int sx = scale_exp_from_bits(scales[d.sx].maxbits);
     const int sy = scale_exp_from_bits(scales[d.sy].maxbits);
-    float T[BN];
+    float T[WC];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) T[j] = 0.f;
-    asm volatile("bar.sync 2, 160;" ::: "memory");  // exponents staged
+    for (int j = 0; j < WC; ++j) T[j] = 0.f;
+    asm volatile("bar.sync 2, %0;" ::"n"(32 + 32 * EW) : "memory");  // exponents staged
     bool ok = true;
     for (int kb = 0; kb < KB; ++kb) {
       const int buf = kb & 1;
@@ -441,33 +452,35 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         break;
       }
       ptx::tc_fence_after();
-      float fac[NG];
+      float fac[WC / 64];
 #pragma unroll
-      for (int g = 0; g < NG; ++g) fac[g] = fxb::pow2f(eA[h * KB + kb] + eB[kb * NG + g] - 16 - sx - sy);
-      fxb::fold<BN>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN), fac);
+      for (int g = 0; g < WC / 64; ++g)
+        fac[g] = fxb::pow2f(eA[h * KB + kb] + eB[kb * NG + cs * (WC / 64) + g] - 16 - sx - sy);
+      fxb::fold<WC>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN + cs * WC), fac, BN);
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
     }
-    // one verdict for all four epilogue warps (they share named barriers below)
-    fxb::epi_bar();
-    if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
-    fxb::epi_bar();
+    // one verdict for all epilogue warps (they share named barriers below)
+    fxb::epi_bar<32 * EW>();
+    if (e == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
+    fxb::epi_bar<32 * EW>();
     ok = *epi_ok != 0;
     const long long Ec = scales[d.sx].E + scales[d.sy].E + sx + sy;
     if (d.mode == OUT_INTERNAL) {
-      if (t == 0 && q == 0 && lane == 0) scales[d.sc].E = Ec;
+      if (t == 0 && e == 0 && lane == 0) scales[d.sc].E = Ec;
       if (ok)  // every epilogue warp reaches the named barriers inside
-        fxb::store_slices<BN>(T, row, m0, n0, q, lane, N, d.ld, (__nv_bfloat16*)d.C, d.plane,
-                              (int*)((char*)d.C + boff), &scales[d.sc].maxbits, red);
+        fxb::store_slices<WC, 32 * EW>(T, row, m0, nw, q, lane, N, d.ld, (__nv_bfloat16*)d.C,
+                                       d.plane, (int*)((char*)d.C + boff), &scales[d.sc].maxbits,
+                                       red + cs * 4 * (WC / 64));
     } else if (ok) {
-      if (t == 0 && q == 0 && lane == 0 && d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
+      if (t == 0 && e == 0 && lane == 0 && d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
       if (row < N) {
         float* O = (float*)d.out + (size_t)row * N;
         const bool mant = d.mode == OUT_USER_MANT;
 #pragma unroll
-        for (int j = 0; j < BN; ++j) {
-          const int c = n0 + j;
+        for (int j = 0; j < WC; ++j) {
+          const int c = nw + j;
           if (c < N) O[c] = mant ? T[j] : final_value(T[j], Ec, status);
         }
       }
@@ -599,9 +612,11 @@ matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s
   cudaError_t e;
   if (fmt == FMT_FX2) {
     if (bn == 64)
-      tc_fxb_kernel<64><<<g.tiles_total, tc::THREADS, fx::Cfg<64>::SMEM, s>>>(P, p->scales, p->status);
+      tc_fxb_kernel<64><<<g.tiles_total, fx::Cfg<64>::THREADS, fx::Cfg<64>::SMEM, s>>>(P, p->scales,
+                                                                                      p->status);
     else
-      tc_fxb_kernel<128><<<g.tiles_total, tc::THREADS, fx::Cfg<128>::SMEM, s>>>(P, p->scales, p->status);
+      tc_fxb_kernel<128><<<g.tiles_total, fx::Cfg<128>::THREADS, fx::Cfg<128>::SMEM, s>>>(
+          P, p->scales, p->status);
     e = cudaGetLastError();
   } else if (PL == 2)
     e = bn == 64 ? launch<64, 2>(P, g.tiles_total, p->scales, p->status, s)
