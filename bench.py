@@ -36,6 +36,9 @@ WORKLOADS = {
                     desc="single N=64 exact row-stochastic float32, n=100, seed 0"),
     "large8192": dict(N=8192, ns=[2 ** 20], gen="stochastic",
                       desc="single N=8192 exact row-stochastic float32, n=2^20, seed 0"),
+    # one product at N=4096 (operands 64 MB each, beyond L2): profiling case
+    "probe4096": dict(N=4096, ns=[2], gen="stochastic",
+                      desc="single N=4096 exact row-stochastic float32, n=2 (one product), seed 0"),
 }
 
 
@@ -148,34 +151,31 @@ def make_input(wk):
 # ---------------------------------------------------------------------------- oracle timing
 
 def cpu_sample(wk, budget_s: float = 15.0, threads: int = 0):
-    """Time the CPU oracle on a bounded sample of the workload (effective TFLOP/s)."""
+    """Time the CPU oracle on a bounded sample of the workload (effective TFLOP/s).
+
+    The sample is the workload's list of powers, repeated until about
+    ``budget_s`` seconds of oracle time; for large N (where one power takes
+    far longer) it is a single product (n = 2) of the same matrix.
+    """
     import oracle
     A = make_input(wk)
     N = wk["N"]
     cores = oracle.set_threads(threads)
-    done_flop, t_total, runs = 0.0, 0.0, []
-    for n in sorted(wk["ns"]):
-        g = gemm_count(n)
-        est = g * 2.0 * N ** 3 / 2e9  # ~2 GFLOP/s per core-ish guess, scaled below
-        if t_total > 0 and t_total + est / max(cores, 1) > budget_s:
+    per_power_est = max(gemm_count(n) for n in wk["ns"]) * 2.0 * N ** 3 / (1.5e9 * cores)
+    ns = sorted(wk["ns"]) if per_power_est < budget_s else [2]
+    done_flop, t_total, reps = 0.0, 0.0, 0
+    while True:
+        for n in ns:
+            t0 = time.perf_counter()
+            oracle.matpow_f64(A, n)
+            t_total += time.perf_counter() - t0
+            done_flop += gemm_count(n) * 2.0 * N ** 3
+        reps += 1
+        if t_total >= budget_s or t_total * (reps + 1) / reps > 2 * budget_s or reps >= 1000:
             break
-        t0 = time.perf_counter()
-        oracle.matpow_f64(A, n)
-        dt = time.perf_counter() - t0
-        t_total += dt
-        done_flop += g * 2.0 * N ** 3
-        runs.append(n)
-        if t_total > budget_s:
-            break
-    if not runs:  # the smallest power alone
-        n = min(wk["ns"])
-        t0 = time.perf_counter()
-        oracle.matpow_f64(A, n)
-        t_total = time.perf_counter() - t0
-        done_flop = gemm_count(n) * 2.0 * N ** 3
-        runs = [n]
     return {"value": done_flop / t_total / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-            "sample": "float64 triple-loop square-and-multiply, N=%d, n in %s (%.1f s)" % (N, runs, t_total)}
+            "sample": "float64 triple-loop square-and-multiply, N=%d, n in %s x %d (%.1f s)" % (
+                N, ns, reps, t_total)}
 
 
 def run_reference(args, wk, world, rank):
@@ -361,11 +361,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single512")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16x3")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--ref-budget", type=float, default=5.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
