@@ -297,3 +297,44 @@ class Plan:
 
     def launch_count(self) -> int:
         return matpow_launch_count(self.h)
+
+
+class Server:
+    """Owns one libmatpow request server (continuous batching)."""
+
+    def __init__(self, max_n: int, precision="fp32", device: int = 0,
+                 hbm_budget_bytes: int = 1 << 30, max_inflight: int = 64, max_queue: int = 1 << 16):
+        self.h = matpow_server_create(device, max_n, precision, hbm_budget_bytes, max_inflight,
+                                      max_queue)
+
+    def submit(self, A, n: int, out, kind: int = 0, p: int = 0, log2_scale=None) -> int:
+        """Queue A^n (kind 0, float32) or A^n mod p (kind 1, uint32); returns the ticket."""
+        st, t = matpow_submit(self.h, A.shape[0], n, kind, p, A, out, log2_scale)
+        if st != OK:
+            _check(st)
+        return t
+
+    def poll(self, ticket: int, timeout_us: int = 0) -> int:
+        return matpow_poll(self.h, ticket, timeout_us)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        import time
+        t_end = time.time() + timeout_s
+        while True:
+            st = self.poll(ticket, 100000)
+            if st not in (EAGAIN, ETIMEDOUT) or time.time() > t_end:
+                return st
+
+    def latencies_us(self, cap: int = 1 << 20):
+        return matpow_server_latencies(self.h, cap)
+
+    def close(self):
+        if self.h:
+            matpow_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
