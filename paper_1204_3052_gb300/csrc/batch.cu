@@ -135,9 +135,10 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
     big.push_back(std::move(b));
   }
   matpow_status st;
-  if (tc && !big.empty())
+  const bool fx2 = fmt == FMT_FX2;
+  if (tc && !fx2 && !big.empty())
     return fail(p, MATPOW_EUNSUPPORTED,
-                "matpow_batched: tensor-core precisions need N <= %d in this build", p->tiny_max);
+                "matpow_batched: grouped tensor-core launches use the exact split (MATPOW_BF16X3)");
   if ((st = grow(p, &p->batch.ws, &p->batch.ws_bytes, std::max<size_t>(ws_need, 1), false))) return st;
   size_t sc_bytes = sizeof(Scale) * std::max(slots, 1);
   if ((st = grow(p, (void**)&p->batch.scales, &p->batch.scale_cap, sc_bytes, false))) return st;
@@ -150,56 +151,89 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
         ++bi;
       }
   }
-  // ---- product descriptors per level
+  // ---- product descriptors per level; tensor-core levels get one launch per
+  // tile width (64 columns for N <= 1024, 128 above)
+  struct Launch {
+    int begin, count, tiles, bn;
+  };
   int max_levels = 0;
   for (auto& b : big) max_levels = std::max(max_levels, (int)b.levels.size());
   std::vector<GemmDesc> gd;
-  std::vector<int> lvl_begin, lvl_count, lvl_tiles;
+  std::vector<std::vector<Launch>> lvl_launches(max_levels);
+  const int passes[2] = {64, 128};
   for (int L = 0; L < max_levels; ++L) {
-    int begin = (int)gd.size(), tiles = 0;
-    for (auto& b : big) {
-      if (L >= (int)b.levels.size()) continue;
-      const int Ni = N[b.i];
-      const bool final_level = L + 1 == (int)b.levels.size();
-      const LevelOps& lv = b.levels[L];
-      for (size_t k = 0; k < lv.ops.size(); ++k) {
-        const Op& op = lv.ops[k];
-        const bool last = final_level && k + 1 == lv.ops.size();
-        char* base = (char*)p->batch.ws + b.off;
-        GemmDesc d{};
-        d.X = base + op.xb * b.mb;
-        d.Y = base + op.yb * b.mb;
-        d.C = last ? nullptr : base + op.cb * b.mb;
-        d.out = last ? (void*)dOut[b.i] : nullptr;
-        d.out_log2 = last && dLog2Scale ? (long long*)(dLog2Scale + b.i) : nullptr;
-        d.plane = plane_offset_elems(Ni, fmt);
-        d.N = Ni;
-        d.ld = ld_for(Ni, fmt);
-        d.sx = b.slot0 + op.sx;
-        d.sy = b.slot0 + op.sy;
-        d.sc = b.slot0 + op.sc;
-        d.mode = last ? (dLog2Scale ? OUT_USER_MANT : OUT_USER_VALUE) : OUT_INTERNAL;
-        d.tile_begin = tiles;
-        if (tc) {
-          int nt = 0;
-          if ((st = tc_fill_desc(p, &d, &nt))) return st;
-          tiles += nt;
-        } else {
-          d.tiles_n = (Ni + simt_tile_edge() - 1) / simt_tile_edge();
-          tiles += d.tiles_n * d.tiles_n;
+    for (int pi = 0; pi < (tc ? 2 : 1); ++pi) {
+      const int bn = tc ? passes[pi] : 0;
+      int begin = (int)gd.size(), tiles = 0;
+      for (size_t bi = 0; bi < big.size(); ++bi) {
+        const Big& b = big[bi];
+        if (L >= (int)b.levels.size()) continue;
+        const int Ni = N[b.i];
+        if (tc && tc_group_bn(Ni) != bn) continue;
+        const bool final_level = L + 1 == (int)b.levels.size();
+        const LevelOps& lv = b.levels[L];
+        for (size_t k = 0; k < lv.ops.size(); ++k) {
+          const Op& op = lv.ops[k];
+          const bool last = final_level && k + 1 == lv.ops.size();
+          char* base = (char*)p->batch.ws + b.off;
+          GemmDesc d{};
+          d.X = base + op.xb * b.mb;
+          d.Y = base + op.yb * b.mb;
+          d.C = last ? nullptr : base + op.cb * b.mb;
+          d.out = last ? (void*)dOut[b.i] : nullptr;
+          d.out_log2 = last && dLog2Scale ? (long long*)(dLog2Scale + b.i) : nullptr;
+          d.plane = plane_offset_elems(Ni, fmt);
+          d.N = Ni;
+          d.ld = ld_for(Ni, fmt);
+          d.sx = b.slot0 + op.sx;
+          d.sy = b.slot0 + op.sy;
+          d.sc = b.slot0 + op.sc;
+          d.mode = last ? (dLog2Scale ? OUT_USER_MANT : OUT_USER_VALUE) : OUT_INTERNAL;
+          d.tile_begin = tiles;
+          if (tc) {
+            d.bn = bn;
+            d.tiles_n = (Ni + bn - 1) / bn;
+            d.map_x = 16 * (int)bi + 4 * op.xb;
+            d.map_y = 16 * (int)bi + 4 * op.yb;
+            tiles += ((Ni + 127) / 128) * d.tiles_n;
+          } else {
+            d.tiles_n = (Ni + simt_tile_edge() - 1) / simt_tile_edge();
+            tiles += d.tiles_n * d.tiles_n;
+          }
+          gd.push_back(d);
         }
-        gd.push_back(d);
       }
+      if ((int)gd.size() > begin) lvl_launches[L].push_back({begin, (int)gd.size() - begin, tiles, bn});
     }
-    lvl_begin.push_back(begin);
-    lvl_count.push_back((int)gd.size() - begin);
-    lvl_tiles.push_back(tiles);
   }
-  // prep CTAs: about one CTA per 16K entries
+  // ---- TMA descriptors of every batch buffer (tensor-core levels), rebuilt
+  // only when the layout (buffer addresses, orders) changed since the last call
+  if (tc && !big.empty()) {
+    std::vector<std::pair<const void*, int>> keys;
+    keys.reserve(4 * big.size());
+    for (auto& b : big)
+      for (int k = 0; k < 4; ++k) keys.push_back({(char*)p->batch.ws + b.off + k * b.mb, N[b.i]});
+    if (keys != p->batch.map_keys) {
+      p->batch.h_maps.resize(4 * keys.size());
+      for (size_t k = 0; k < keys.size(); ++k)
+        if (!tc_encode_buffer_maps(&p->batch.h_maps[4 * k], keys[k].first, keys[k].second))
+          return fail(p, MATPOW_ECUDA, "matpow_batched: cuTensorMapEncodeTiled failed");
+      const size_t mbytes = p->batch.h_maps.size() * sizeof(CUtensorMap);
+      if ((st = grow(p, &p->batch.maps, &p->batch.maps_bytes, mbytes, false))) return st;
+      CK(p, cudaMemcpy(p->batch.maps, p->batch.h_maps.data(), mbytes, cudaMemcpyHostToDevice));
+      p->batch.map_keys = keys;
+    }
+  }
+  // prep CTAs: one per 64 x 64 block (exact split), else about one per 16K entries
   int prep_blocks = 0;
   for (auto& d : prep) {
     size_t e = (size_t)d.N * d.N;
-    d.blocks = (int)std::min<size_t>(std::max<size_t>((e + 16383) / 16384, 1), 1024);
+    if (fx2 && d.kind == 0) {
+      const size_t nb = ((size_t)d.N + 63) / 64;
+      d.blocks = (int)(nb * nb);
+    } else {
+      d.blocks = (int)std::min<size_t>(std::max<size_t>((e + 16383) / 16384, 1), 1024);
+    }
     d.block_begin = prep_blocks;
     prep_blocks += d.blocks;
   }
@@ -232,27 +266,35 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   if (!prep.empty()) {
     if (slots) CK(p, cudaMemsetAsync(p->batch.scales, 0, sizeof(Scale) * slots, s));
     const PrepDesc* pd = (const PrepDesc*)(dd + o_prep);
-    CK(p, launch_prep_absmax_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, p->status, s));
-    CK(p, launch_prep_convert_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, s));
-    p->launches += 2;
+    if (fx2) {
+      CK(p, launch_prep_fxb_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, p->status, s));
+      p->launches += 1;
+    } else {
+      CK(p, launch_prep_absmax_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, p->status, s));
+      CK(p, launch_prep_convert_group(pd, (int)prep.size(), prep_blocks, p->batch.scales, s));
+      p->launches += 2;
+    }
   }
   for (int L = 0; L < max_levels; ++L) {
-    if (!lvl_count[L]) continue;
-    const GemmDesc* g = (const GemmDesc*)(dd + o_gd) + lvl_begin[L];
-    double flop = 0;
-    for (int k = 0; k < lvl_count[L]; ++k) {
-      const GemmDesc& d = gd[lvl_begin[L] + k];
-      flop += 2.0 * d.N * (double)d.N * d.N;
+    for (const Launch& la : lvl_launches[L]) {
+      const GemmDesc* g = (const GemmDesc*)(dd + o_gd) + la.begin;
+      double flop = 0;
+      for (int k = 0; k < la.count; ++k) {
+        const GemmDesc& d = gd[la.begin + k];
+        flop += 2.0 * d.N * (double)d.N * d.N;
+      }
+      timed_begin(p, s, &ev);
+      if (tc) {
+        if ((st = tc_launch_group_bn(p, g, la.count, la.tiles, p->batch.maps, la.bn, p->batch.scales,
+                                     p->status, s)))
+          return st;
+        timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
+      } else {
+        CK(p, launch_simt_group(g, la.count, la.tiles, p->batch.scales, p->status, s));
+        timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
+      }
+      p->launches++;
     }
-    timed_begin(p, s, &ev);
-    if (tc) {
-      if ((st = tc_launch_group(p, g, lvl_count[L], lvl_tiles[L], p->batch.scales, s))) return st;
-      timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
-    } else {
-      CK(p, launch_simt_group(g, lvl_count[L], lvl_tiles[L], p->batch.scales, p->status, s));
-      timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
-    }
-    p->launches++;
   }
   return MATPOW_OK;
 }

@@ -60,6 +60,8 @@ struct GemmDesc {
   int tiles_n;           // tiles along a row of C
   unsigned p;            // modulus (mod-p paths)
   int bn;                // tensor-core tile width (columns of C per CTA)
+  int map_x, map_y;      // grouped tensor-core launches: TMA descriptors of X and Y
+                         // (4 per buffer: A-role a1, a2, B-role a1, a2)
 };
 
 // Up to two products passed by value (one squaring level of one matrix:
@@ -172,6 +174,10 @@ struct PrepDesc {
 // at dst; max|A| folds into slot->maxbits.  One CTA per 64 x 64 block.
 cudaError_t launch_prep_fxb(const float* A, int N, void* dst, Scale* slot, unsigned* status,
                             cudaStream_t s);
+// Block-scaled split of many matrices (PrepDesc kind 0: nb x nb CTAs each;
+// kinds 1, 2: identity / copy into the user's output).
+cudaError_t launch_prep_fxb_group(const PrepDesc* d, int count, int blocks, Scale* scales,
+                                  unsigned* status, cudaStream_t s);
 cudaError_t launch_prep_absmax_group(const PrepDesc* d, int count, int blocks, Scale* scales,
                                      unsigned* status, cudaStream_t s);
 cudaError_t launch_prep_convert_group(const PrepDesc* d, int count, int blocks, Scale* scales,

@@ -290,9 +290,13 @@ struct Cfg {
 };
 }  // namespace fx
 
+// One CTA = one output tile t of product d; ax0/ax1 (A operand, slices a1/a2
+// of X) and by0/by1 (B operand, slices of Y) are TMA descriptors in param or
+// global memory.
 template <int BN>
-__global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
-    tc_fxb_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
+__device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensorMap* ax0,
+                                        const CUtensorMap* ax1, const CUtensorMap* by0,
+                                        const CUtensorMap* by1, Scale* scales, unsigned* status) {
   using namespace tc;
   using C = fx::Cfg<BN>;
   constexpr int EW = C::EW, WC = C::WC;
@@ -315,11 +319,6 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int t = blockIdx.x;
-  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
-  if (which) t -= P.tiles0;
-  const TcProblem& pr = P.p[which];
-  const GemmDesc& d = pr.d;
   const int tm = t / d.tiles_n, tn = t - (t / d.tiles_n) * d.tiles_n;
   const int m0 = tm * BM, n0 = tn * BN;
   const int N = d.N;
@@ -344,10 +343,10 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
     ptx::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
-    ptx::prefetch_tmap(&pr.ax[0]);
-    ptx::prefetch_tmap(&pr.ax[1]);
-    ptx::prefetch_tmap(&pr.by[0]);
-    ptx::prefetch_tmap(&pr.by[1]);
+    ptx::prefetch_tmap(ax0);
+    ptx::prefetch_tmap(ax1);
+    ptx::prefetch_tmap(by0);
+    ptx::prefetch_tmap(by1);
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -368,13 +367,13 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
         ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
         const int kx = kb * BK;
-        ptx::tma_load_2d(base, &pr.ax[0], kx, m0, fb);
-        ptx::tma_load_2d(base + C::A_BYTES, &pr.ax[1], kx, m0, fb);
+        ptx::tma_load_2d(base, ax0, kx, m0, fb);
+        ptx::tma_load_2d(base + C::A_BYTES, ax1, kx, m0, fb);
         const uint32_t bbase = base + 2 * C::A_BYTES;
 #pragma unroll
         for (int c = 0; c < BN / 64; ++c) {
-          ptx::tma_load_2d(bbase + c * 8192, &pr.by[0], n0 + 64 * c, kx, fb);
-          ptx::tma_load_2d(bbase + C::B_BYTES + c * 8192, &pr.by[1], n0 + 64 * c, kx, fb);
+          ptx::tma_load_2d(bbase + c * 8192, by0, n0 + 64 * c, kx, fb);
+          ptx::tma_load_2d(bbase + C::B_BYTES + c * 8192, by1, n0 + 64 * c, kx, fb);
         }
         ++issued;
       }
@@ -495,6 +494,34 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
 }
 
+template <int BN>
+__global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
+    tc_fxb_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
+  int t = blockIdx.x;
+  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
+  if (which) t -= P.tiles0;
+  const TcProblem& pr = P.p[which];
+  fxb_cta<BN>(pr.d, t, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], scales, status);
+}
+
+// Grouped launch: products from a device table (any number of matrices),
+// TMA descriptors from a device table (4 per stored buffer: A-role a1, a2,
+// B-role a1, a2 at index map_x / map_y).
+template <int BN>
+__global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
+    tc_fxb_group_kernel(const GemmDesc* __restrict__ descs, int count,
+                        const CUtensorMap* __restrict__ maps, Scale* scales, unsigned* status) {
+  const int tb = blockIdx.x;
+  int lo = 0, hi = count - 1;  // last desc with tile_begin <= tb
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].tile_begin <= tb) lo = mid; else hi = mid - 1;
+  }
+  const GemmDesc d = descs[lo];
+  fxb_cta<BN>(d, tb - d.tile_begin, &maps[d.map_x], &maps[d.map_x + 1], &maps[d.map_y + 2],
+              &maps[d.map_y + 3], scales, status);
+}
+
 // A (float32, leading dimension N) -> block-scaled stored format, one CTA per
 // 64 x 64 block.
 __global__ void __launch_bounds__(256) prep_fxb_kernel(const float* __restrict__ A, int N, int ld,
@@ -539,7 +566,14 @@ cudaError_t tc_init(matpow_plan_s*) {
   if ((e = cudaFuncSetAttribute(tc_fxb_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 fx::Cfg<64>::SMEM)) != cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(tc_fxb_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(tc_fxb_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                fx::Cfg<128>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(tc_fxb_group_kernel<64>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, fx::Cfg<64>::SMEM)) !=
+      cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(tc_fxb_group_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               fx::Cfg<128>::SMEM);
 }
 
@@ -630,13 +664,82 @@ matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s
   return MATPOW_OK;
 }
 
-matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc*, int, int, Scale*, cudaStream_t) {
-  return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches are not built yet");
+matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
+                              Scale* scales, cudaStream_t s) {
+  return tc_launch_group_bn(p, d_descs, count, tiles, p->batch.maps, p->group_bn, scales, p->status, s);
+}
+
+matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
+                                 const void* d_maps, int bn, Scale* scales, unsigned* status,
+                                 cudaStream_t s) {
+  if (plan_float_fmt(p) != FMT_FX2)
+    return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches need the exact split");
+  const CUtensorMap* maps = (const CUtensorMap*)d_maps;
+  if (bn == 64)
+    tc_fxb_group_kernel<64><<<tiles, fx::Cfg<64>::THREADS, fx::Cfg<64>::SMEM, s>>>(d_descs, count, maps,
+                                                                                  scales, status);
+  else
+    tc_fxb_group_kernel<128><<<tiles, fx::Cfg<128>::THREADS, fx::Cfg<128>::SMEM, s>>>(
+        d_descs, count, maps, scales, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(p, e, "tc_fxb_group_kernel launch");
+  return MATPOW_OK;
+}
+
+int tc_group_bn(int N) { return N <= 1024 ? 64 : 128; }
+
+bool tc_encode_buffer_maps(CUtensorMap* m4, const void* base, int N) {
+  const int ld = ld_for(N, FMT_FX2);
+  const char* b = (const char*)base;
+  const size_t lo = (size_t)plane_offset_elems(N, FMT_FX2) * 2;
+  return tc_encode_bf16_map(&m4[0], b, N, ld, 64, tc::BM) &&
+         tc_encode_bf16_map(&m4[1], b + lo, N, ld, 64, tc::BM) &&
+         tc_encode_bf16_map(&m4[2], b, N, ld, 64, 64) &&
+         tc_encode_bf16_map(&m4[3], b + lo, N, ld, 64, 64);
 }
 
 }  // namespace mp
 
 namespace mp {
+
+// Grouped block-scaled split: PrepDesc kind 0 covers nb x nb CTAs of its
+// matrix; kinds 1 and 2 write the identity / a copy into the user's output.
+__global__ void __launch_bounds__(256) prep_fxb_group_kernel(const PrepDesc* __restrict__ descs,
+                                                             int count, Scale* scales,
+                                                             unsigned* status) {
+  __shared__ float red[8];
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].block_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const PrepDesc d = descs[lo];
+  const int b = blockIdx.x - d.block_begin;
+  const int N = d.N;
+  if (d.kind != 0) {
+    if (d.log2 && b == 0 && threadIdx.x == 0) *d.log2 = 0;
+    const size_t total = (size_t)N * N;
+    float* out = (float*)d.dst;
+    for (size_t i = b * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)d.blocks * blockDim.x) {
+      const size_t r = i / N, c = i - r * N;
+      out[i] = d.kind == 1 ? (r == c ? 1.0f : 0.0f) : d.A[i];
+    }
+    return;
+  }
+  const int ld = ld_for(N, FMT_FX2);
+  const int nb = fxb::nblocks(N);
+  __nv_bfloat16* a1p = (__nv_bfloat16*)d.dst;
+  int* bexp = (int*)((char*)d.dst + fxb::bexp_offset(N, ld));
+  fxb::prep_block(d.A, N, ld, b / nb, b % nb, a1p, d.plane, bexp, &scales[d.slot_stored].maxbits,
+                  status, red);
+}
+
+cudaError_t launch_prep_fxb_group(const PrepDesc* d, int count, int blocks, Scale* scales,
+                                  unsigned* status, cudaStream_t s) {
+  prep_fxb_group_kernel<<<blocks, 256, 0, s>>>(d, count, scales, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep_fxb(const float* A, int N, void* dst, Scale* slot, unsigned* status,
                             cudaStream_t s) {
   const int ld = ld_for(N, FMT_FX2);

@@ -64,6 +64,10 @@ struct BatchState {
   size_t desc_bytes = 0;
   void* h_descs = nullptr;      // pinned staging for the tables
   size_t h_desc_bytes = 0;
+  void* maps = nullptr;         // TMA descriptors of the batch buffers (device)
+  size_t maps_bytes = 0;
+  std::vector<CUtensorMap> h_maps;  // host copy; rebuilt when the layout changes
+  std::vector<std::pair<const void*, int>> map_keys;  // (buffer, N) per 4 descriptors
   cudaEvent_t staged = nullptr; // the last upload from h_descs has been consumed
 };
 
@@ -90,6 +94,7 @@ struct matpow_plan_s {
   int tile_override = 0;
   int split_mode = 0;  // BF16X3: 0 exact fixed-point slices, 1 floating hi/lo planes
   bool use_chain = true;  // whole-chain cooperative kernel where it applies
+  int group_bn = 64;      // tile width of the current grouped tensor-core launch
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
   // graphs
   std::vector<mp::GraphEntry> graphs;
@@ -131,4 +136,10 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
 cudaError_t tc_chain_init(matpow_plan_s* p);
 matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                               Scale* scales, cudaStream_t s);
+matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
+                                 const void* d_maps, int bn, Scale* scales, unsigned* status,
+                                 cudaStream_t s);
+int tc_group_bn(int N);  // tile width of grouped launches for order N
+// The four TMA descriptors of one block-scaled buffer (A-role a1, a2, B-role a1, a2).
+bool tc_encode_buffer_maps(CUtensorMap* m4, const void* base, int N);
 }  // namespace mp

@@ -1,4 +1,6 @@
-"""Batched parity: each matrix of an uneven batch against the oracle."""
+"""Batched parity: each matrix of an uneven batch against the oracle, and
+bit-for-bit against the same power computed alone (the grouped launches run
+the same product code on the same values)."""
 import numpy as np
 import pytest
 
@@ -8,9 +10,20 @@ from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
+EMU = {"bf16x3": "bf16x3blk"}
 
-@pytest.mark.parametrize("prec", ["fp32"])
-def test_uneven_batch_matches_single_calls(prec):
+
+def floor_for(prec, A, n, M, e):
+    Mf, ef = oracle.fp32_sqmul(A, n)
+    f = oracle.rel_frobenius(Mf, ef, M, e)
+    if prec in EMU and A.shape[0] > 64:
+        Me, ee = oracle.emu_sqmul(A, n, EMU[prec])
+        f = max(f, oracle.rel_frobenius(Me, ee, M, e))
+    return f
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_uneven_batch_matches_oracle_and_single_calls(prec):
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
     bd = wl.batched_draw(count=48, seed=1, n_max=300)
@@ -26,11 +39,36 @@ def test_uneven_batch_matches_single_calls(prec):
     for i, (A, n) in enumerate(zip(As, ns)):
         M, e, _ = oracle.matpow_f64(A, n)
         err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lgs[i]), M, e)
-        Mf, ef = oracle.fp32_sqmul(A, n)
-        assert err <= gate(n, oracle.rel_frobenius(Mf, ef, M, e)), (i, A.shape[0], n, err)
-    # a second call reuses the plan's batch tables
+        assert err <= gate(n, floor_for(prec, A, n, M, e)), (i, A.shape[0], n, err)
+        alone, alone_lg = plan.f32(dAs[i], n, mantissa=True)
+        plan.check()
+        assert torch.equal(alone, outs[i]) and int(alone_lg.item()) == int(lgs[i]), (i, A.shape[0], n)
+    # a second call reuses the plan's batch tables (and cached descriptors)
     outs2 = plan.batched(dAs, ns, log2=lg)
     plan.check()
     for a, b in zip(outs, outs2):
         assert torch.equal(a, b)
+    plan.close()
+
+
+def test_batch_with_wide_tiles():
+    # orders above 1024 run in the 128-column grouped launch, next to 64-column ones
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    Ns = [1100, 300, 1030, 96, 40]
+    ns = [13, 77, 2, 1000, 9]
+    As = [wl.gaussian(N, 7 + i) for i, N in enumerate(Ns)]
+    plan = mpw.Plan(1100, "bf16x3")
+    dAs = [to_dev(a) for a in As]
+    lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
+    outs = plan.batched(dAs, ns, log2=lg)
+    plan.check()
+    for i, (A, n) in enumerate(zip(As, ns)):
+        alone, alone_lg = plan.f32(dAs[i], n, mantissa=True)
+        plan.check()
+        assert torch.equal(alone, outs[i]), (Ns[i], n)
+        if Ns[i] <= 300:
+            M, e, _ = oracle.matpow_f64(A, n)
+            err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
+            assert err <= gate(n, floor_for("bf16x3", A, n, M, e))
     plan.close()
