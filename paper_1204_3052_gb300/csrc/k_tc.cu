@@ -669,11 +669,8 @@ matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int cou
   return tc_launch_group_bn(p, d_descs, count, tiles, p->batch.maps, p->group_bn, scales, p->status, s);
 }
 
-matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
-                                 const void* d_maps, int bn, Scale* scales, unsigned* status,
-                                 cudaStream_t s) {
-  if (plan_float_fmt(p) != FMT_FX2)
-    return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches need the exact split");
+cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
+                             int bn, Scale* scales, unsigned* status, cudaStream_t s) {
   const CUtensorMap* maps = (const CUtensorMap*)d_maps;
   if (bn == 64)
     tc_fxb_group_kernel<64><<<tiles, fx::Cfg<64>::THREADS, fx::Cfg<64>::SMEM, s>>>(d_descs, count, maps,
@@ -681,7 +678,15 @@ matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int 
   else
     tc_fxb_group_kernel<128><<<tiles, fx::Cfg<128>::THREADS, fx::Cfg<128>::SMEM, s>>>(
         d_descs, count, maps, scales, status);
-  cudaError_t e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
+                                 const void* d_maps, int bn, Scale* scales, unsigned* status,
+                                 cudaStream_t s) {
+  if (plan_float_fmt(p) != FMT_FX2)
+    return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches need the exact split");
+  cudaError_t e = launch_fxb_group(d_descs, count, tiles, d_maps, bn, scales, status, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "tc_fxb_group_kernel launch");
   return MATPOW_OK;
 }

@@ -102,7 +102,9 @@ struct Req {
 
 struct matpow_server_s {
   matpow_server_desc desc{};
-  int fmt = FMT_F32;
+  int fmt = FMT_F32;  // FMT_FX2: float levels on the tensor cores (exact split)
+  CUtensorMap* d_maps = nullptr;  // 16 TMA descriptors per slot chunk (4 buffers x 4)
+  CUtensorMap* h_maps = nullptr;  // pinned host copy
   cudaStream_t stream = nullptr;
   void* arena_mem = nullptr;
   Arena arena;
@@ -179,8 +181,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64_t step) {
   std::vector<TinyDesc> tiny;
   std::vector<PrepDesc> prep;
-  std::vector<GemmDesc> gf, gm;
-  int tiles_f = 0, tiles_m = 0;
+  std::vector<GemmDesc> gf, gw, gm;  // float (64-wide tiles), float (128-wide), mod p
+  int tiles_f = 0, tiles_w = 0, tiles_m = 0;
   std::vector<Req*> modp_prep;
   for (Req* q : act) {
     if (q->state != 1) continue;
@@ -258,11 +260,29 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
       if (r.kind == 0) {
         d.out_log2 = last ? (long long*)r.dLog2Scale : nullptr;
         d.ld = ld_for(r.N, s->fmt);
+        d.plane = plane_offset_elems(r.N, s->fmt);
         d.mode = last ? (r.dLog2Scale ? OUT_USER_MANT : OUT_USER_VALUE) : OUT_INTERNAL;
-        d.tiles_n = (r.N + simt_tile_edge() - 1) / simt_tile_edge();
-        d.tile_begin = tiles_f;
-        tiles_f += d.tiles_n * d.tiles_n;
-        gf.push_back(d);
+        if (s->fmt == FMT_FX2) {
+          d.bn = tc_group_bn(r.N);
+          d.tiles_n = (r.N + d.bn - 1) / d.bn;
+          d.map_x = 16 * q->chunk + 4 * op.xb;
+          d.map_y = 16 * q->chunk + 4 * op.yb;
+          const int nt = ((r.N + 127) / 128) * d.tiles_n;
+          if (d.bn == 64) {
+            d.tile_begin = tiles_f;
+            tiles_f += nt;
+            gf.push_back(d);
+          } else {
+            d.tile_begin = tiles_w;
+            tiles_w += nt;
+            gw.push_back(d);
+          }
+        } else {
+          d.tiles_n = (r.N + simt_tile_edge() - 1) / simt_tile_edge();
+          d.tile_begin = tiles_f;
+          tiles_f += d.tiles_n * d.tiles_n;
+          gf.push_back(d);
+        }
       } else {
         d.ld = ld_for(r.N, FMT_U32);
         d.mode = last ? OUT_USER_VALUE : OUT_INTERNAL;
@@ -283,7 +303,12 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   int prep_blocks = 0;
   for (auto& d : prep) {
     size_t e = (size_t)d.N * d.N;
-    d.blocks = (int)std::min<size_t>(std::max<size_t>((e + 16383) / 16384, 1), 1024);
+    if (s->fmt == FMT_FX2 && d.kind == 0) {
+      const size_t nb = ((size_t)d.N + 63) / 64;
+      d.blocks = (int)(nb * nb);
+    } else {
+      d.blocks = (int)std::min<size_t>(std::max<size_t>((e + 16383) / 16384, 1), 1024);
+    }
     d.block_begin = prep_blocks;
     prep_blocks += d.blocks;
   }
@@ -291,7 +316,8 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   const size_t o_t = 0;
   const size_t o_p = align256(o_t + tiny.size() * sizeof(TinyDesc));
   const size_t o_f = align256(o_p + prep.size() * sizeof(PrepDesc));
-  const size_t o_m = align256(o_f + gf.size() * sizeof(GemmDesc));
+  const size_t o_w = align256(o_f + gf.size() * sizeof(GemmDesc));
+  const size_t o_m = align256(o_w + gw.size() * sizeof(GemmDesc));
   const size_t total = std::max<size_t>(align256(o_m + gm.size() * sizeof(GemmDesc)), 256);
   if (!ensure_tab(s, total)) return fail(nullptr, MATPOW_ENOMEM, "server: descriptor table");
   const int ti = s->tab_i;
@@ -302,6 +328,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   if (!tiny.empty()) memcpy(h + o_t, tiny.data(), tiny.size() * sizeof(TinyDesc));
   if (!prep.empty()) memcpy(h + o_p, prep.data(), prep.size() * sizeof(PrepDesc));
   if (!gf.empty()) memcpy(h + o_f, gf.data(), gf.size() * sizeof(GemmDesc));
+  if (!gw.empty()) memcpy(h + o_w, gw.data(), gw.size() * sizeof(GemmDesc));
   if (!gm.empty()) memcpy(h + o_m, gm.data(), gm.size() * sizeof(GemmDesc));
   cudaError_t e = cudaMemcpyAsync(dd, h, total, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: upload");
@@ -314,9 +341,13 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   }
   if (!prep.empty()) {
     const PrepDesc* pd = (const PrepDesc*)(dd + o_p);
-    e = launch_prep_absmax_group(pd, (int)prep.size(), prep_blocks, s->scales, st0, s->stream);
-    if (e == cudaSuccess)
-      e = launch_prep_convert_group(pd, (int)prep.size(), prep_blocks, s->scales, s->stream);
+    if (s->fmt == FMT_FX2) {
+      e = launch_prep_fxb_group(pd, (int)prep.size(), prep_blocks, s->scales, st0, s->stream);
+    } else {
+      e = launch_prep_absmax_group(pd, (int)prep.size(), prep_blocks, s->scales, st0, s->stream);
+      if (e == cudaSuccess)
+        e = launch_prep_convert_group(pd, (int)prep.size(), prep_blocks, s->scales, s->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: prep");
   }
   for (Req* q : modp_prep) {
@@ -330,8 +361,17 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p prep");
   }
   if (!gf.empty()) {
-    e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->scales, st0,
-                          s->stream);
+    if (s->fmt == FMT_FX2)
+      e = launch_fxb_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->d_maps, 64,
+                           s->scales, st0, s->stream);
+    else
+      e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->scales, st0,
+                            s->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
+  }
+  if (!gw.empty()) {
+    e = launch_fxb_group((const GemmDesc*)(dd + o_w), (int)gw.size(), tiles_w, s->d_maps, 128,
+                         s->scales, st0, s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
   }
   if (!gm.empty()) {
@@ -366,6 +406,26 @@ static void scheduler(matpow_server_s* s) {
         q->state = 1;
         q->tiny = q->r.kind == 0 && q->r.N <= tiny_max_supported() && q->r.n >= 2;
         if (q->r.n >= 2) build_schedule(q->r.n, &q->levels);
+        if (s->fmt == FMT_FX2 && q->r.kind == 0 && !q->tiny && q->r.n >= 2) {
+          // TMA descriptors of the request's four buffers, uploaded in stream
+          // order before its first product
+          CUtensorMap* hm = s->h_maps + 16 * q->chunk;
+          const size_t mb = fp / 4;
+          bool okm = true;
+          for (int k = 0; k < 4 && okm; ++k)
+            okm = tc_encode_buffer_maps(hm + 4 * k, (char*)s->arena_mem + off + k * mb, q->r.N);
+          if (okm)
+            okm = cudaMemcpyAsync(s->d_maps + 16 * q->chunk, hm, 16 * sizeof(CUtensorMap),
+                                  cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
+          if (!okm) {
+            q->state = 3;
+            q->result = MATPOW_ECUDA;
+            s->arena.release(off, fp);
+            s->free_chunks.push_back(q->chunk);
+            s->cv_done.notify_all();
+            continue;
+          }
+        }
         s->active.push_back(q);
       }
       act = s->active;
@@ -463,8 +523,9 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   auto* s = new (std::nothrow) matpow_server_s();
   if (!s) return fail(nullptr, MATPOW_ENOMEM, "matpow_server_create: host allocation");
   s->desc = *d;
-  // grouped float levels run the float32 SIMT product kernels
-  s->fmt = FMT_F32;
+  // grouped float levels: the exact-split tensor-core kernels for MATPOW_BF16X3,
+  // the float32 SIMT kernels otherwise
+  s->fmt = d->precision == MATPOW_BF16X3 ? FMT_FX2 : FMT_F32;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(d->device);
@@ -475,6 +536,11 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(unsigned) * s->h_status.size());
   if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(unsigned) * s->h_status.size());
   if (e == cudaSuccess) e = tiny_attrs();
+  if (e == cudaSuccess && s->fmt == FMT_FX2) {
+    e = tc_init(nullptr);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_maps, sizeof(CUtensorMap) * 16 * d->max_inflight);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_maps, sizeof(CUtensorMap) * 16 * d->max_inflight);
+  }
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     matpow_server_destroy(s);
@@ -555,6 +621,8 @@ extern "C" matpow_status matpow_server_destroy(matpow_server_t s) {
     if (s->h_tab[i]) cudaFreeHost(s->h_tab[i]);
   }
   if (s->d_tab) cudaFree(s->d_tab);
+  if (s->d_maps) cudaFree(s->d_maps);
+  if (s->h_maps) cudaFreeHost(s->h_maps);
   if (s->scales) cudaFree(s->scales);
   if (s->status) cudaFree(s->status);
   if (s->arena_mem) cudaFree(s->arena_mem);
