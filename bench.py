@@ -36,6 +36,12 @@ WORKLOADS = {
                     desc="single N=64 exact row-stochastic float32, n=100, seed 0"),
     "large8192": dict(N=8192, ns=[2 ** 20], gen="stochastic",
                       desc="single N=8192 exact row-stochastic float32, n=2^20, seed 0"),
+    "batched4096": dict(kind="batched", count=4096, n_max=4096, N=256, ns=[],
+                        desc="batched: 4096 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
+                             "n log-uniform in [1,4096], seed 0; one grouped launch per level"),
+    "serving": dict(kind="serving", count=2000, N=2048, ns=[],
+                    desc="serving: 2000 Poisson-arrival requests, N log-uniform [8,2048], n log-uniform "
+                         "[1,2^30], 90% float / 10% mod 65521, seed 0"),
     # one product at N=4096 (operands 64 MB each, beyond L2): profiling case
     "probe4096": dict(N=4096, ns=[2], gen="stochastic",
                       desc="single N=4096 exact row-stochastic float32, n=2 (one product), seed 0"),
@@ -178,15 +184,47 @@ def cpu_sample(wk, budget_s: float = 15.0, threads: int = 0):
                 N, ns, reps, t_total)}
 
 
+def cpu_sample_list(items, budget_s):
+    """Oracle over (A, n, p) items in order until ~budget_s; effective TFLOP/s."""
+    import oracle
+    cores = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    done, k = 0.0, 0
+    for A, n, p in items:
+        if k and time.perf_counter() - t0 >= budget_s:
+            break
+        if p:
+            oracle.matpow_modp(A, n, p)
+        else:
+            oracle.matpow_f64(A, n)
+        done += gemm_count(n) * 2.0 * A.shape[0] ** 3
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle on the first %d items of the workload (%.1f s)" % (k, dt)}
+
+
+def reference_items(wk):
+    from paper_1204_3052_gb300 import workloads as wl
+    if wk.get("kind") == "batched":
+        bd = wl.batched_draw(count=wk["count"], seed=0, n_max=wk["n_max"])
+        for N, n, sd in zip(bd.Ns, bd.ns, bd.seeds):
+            yield wl.gaussian(int(N), int(sd)), int(n), 0
+    else:
+        for r in wl.serving_stream(count=wk["count"], seed=0):
+            yield wl.request_matrix(r), r.n, (r.p if r.kind else 0)
+
+
 def run_reference(args, wk, world, rank):
     if rank != 0:
         return
     res = []
-    for _ in range(args.warmup):
-        pass  # the oracle has nothing to warm up beyond loading
     cb = None
     for _ in range(max(args.steps, 1)):
-        cb = cpu_sample(wk, budget_s=args.ref_budget)
+        if wk.get("kind") in ("batched", "serving"):
+            cb = cpu_sample_list(reference_items(wk), args.ref_budget)
+        else:
+            cb = cpu_sample(wk, budget_s=args.ref_budget)
         res.append(cb["value"])
     value = statistics.median(res)
     cb["value"] = value
@@ -264,6 +302,15 @@ def run_ours(args, wk, world, rank, local):
         import oracle
         for i, n in enumerate(ns):
             if N > 1024:
+                if wk["gen"] == "stochastic" and n >= 2 ** 10:
+                    # closed form: A^n -> 1 pi^T; check 64 sampled rows and all row sums
+                    pi = oracle.stationary(A_host)
+                    Mg = outs[i].cpu().numpy().astype(np.float64)
+                    Vg = np.ldexp(Mg, int(lgs[i].item()))
+                    rows = np.random.default_rng(0).choice(N, 64, replace=False)
+                    want = np.tile(pi, (64, 1))
+                    errs[str(n)] = float(np.linalg.norm(Vg[rows] - want) / np.linalg.norm(want))
+                    errs["max_rowsum_dev"] = float(np.max(np.abs(Vg.sum(axis=1) - 1.0)))
                 continue
             M, e, _ = oracle.matpow_f64(A_host, n)
             errs[str(n)] = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lgs[i].item()), M, e)
@@ -311,9 +358,11 @@ def run_ours(args, wk, world, rank, local):
     if kind == mpw.KERNEL_TC:
         achieved = kflop * products / (kms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
+        kname = ("tc_chain_kernel" if prec == "bf16x3" and 64 < N <= 1024 else
+                 "tc_fxb_kernel" if prec == "bf16x3" else "tc_gemm_kernel")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "tc_gemm", "peak_source": peak_src + " bf16 burst",
+                "kernel": kname, "peak_source": peak_src + " bf16 burst",
                 "counted": "%d bfloat16 product(s) per term" % int(products)}
     else:
         # float32 FFMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
@@ -354,6 +403,230 @@ def run_ours(args, wk, world, rank, local):
     plan.close()
 
 
+def run_batched(args, wk, world, rank, local):
+    """Config 3: one matpow_batched call over an uneven batch per step."""
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    from paper_1204_3052_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_src = load_peaks()
+    bd = wl.batched_draw(count=wk["count"], seed=0, n_max=wk["n_max"])
+    Ns = [int(x) for x in bd.Ns]
+    ns = [int(x) for x in bd.ns]
+    hostA = [wl.gaussian(N, int(sd)) for N, sd in zip(Ns, bd.seeds)]
+    dA = [torch.from_numpy(a).to(dev) for a in hostA]
+    outs = [torch.empty_like(a) for a in dA]
+    lg = torch.zeros(len(dA), dtype=torch.int64, device=dev)
+    flop_step = sum(gemm_count(n) * 2.0 * N ** 3 for N, n in zip(Ns, ns))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = mpw.Plan(max(Ns), args.precision, device=local)
+
+    def step(s):
+        mpw._check(mpw.matpow_batched(plan.h, dA, Ns, ns, outs, lg, s), plan.h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(stream)
+        plan.check(stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        l0 = plan.launch_count()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step(stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        barrier(world)
+        clocks = sampler.stop()
+        launches = plan.launch_count() - l0
+        st = plan.sync(stream)
+    t_ms = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in evs), dev)
+    value = world * args.steps * flop_step / (t_ms * 1e-3) / 1e12
+    # accuracy on a sample of the batch
+    errs = {}
+    if rank == 0 and not args.no_check:
+        import oracle
+        for i in range(0, len(Ns), max(1, len(Ns) // 16)):
+            M, e, _ = oracle.matpow_f64(hostA[i], ns[i])
+            errs["N%d_n%d" % (Ns[i], ns[i])] = oracle.rel_frobenius(
+                outs[i].cpu().numpy(), int(lg[i].item()), M, e)
+    # end to end: inputs from pinned host memory, results back, inside the timed region
+    pinA = [torch.from_numpy(a).pin_memory() for a in hostA]
+    pinO = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in hostA]
+    pinL = torch.zeros(len(dA), dtype=torch.int64).pin_memory()
+    with torch.cuda.stream(stream):
+        def e2e_step():
+            for a, b in zip(dA, pinA):
+                a.copy_(b, non_blocking=True)
+            step(stream)
+            for a, b in zip(pinO, outs):
+                a.copy_(b, non_blocking=True)
+            pinL.copy_(lg, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(max(args.steps, 2)):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / max(args.steps, 2)
+    # dominant kernel timing
+    plan.set_option(mpw.OPT_TIMING, 1)
+    kind = mpw.KERNEL_TC if args.precision != "fp32" else mpw.KERNEL_SIMT
+    with torch.cuda.stream(stream):
+        plan.kernel_time(kind, reset=True)
+        for _ in range(2):
+            flush.zero_()
+            step(stream)
+        torch.cuda.synchronize()
+        kl, kms, kflop = plan.kernel_time(kind, reset=True)
+        tl, tms, tflop = plan.kernel_time(mpw.KERNEL_TINY, reset=True)
+    plan.set_option(mpw.OPT_TIMING, 0)
+    products = 3.0 if args.precision == "bf16x3" else 1.0
+    achieved = kflop * products / (kms * 1e-3) / 1e12 if kms else 0.0
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["bf16_tflops"], "traffic": None,
+            "kernel": "tc_fxb_group_kernel (grouped level launches, N > 64)",
+            "peak_source": peak_src + " bf16 burst", "launches_timed": kl,
+            "avg_launch_us": kms * 1e3 / max(kl, 1),
+            "tiny_chain_share_ms": tms / 2, "level_kernels_ms": kms / 2}
+    if rank != 0:
+        return
+    cb = None
+    if world == 1 and not args.no_cpu:
+        import oracle
+        cores = oracle.set_threads(0)
+        t0 = time.perf_counter()
+        done, i = 0.0, 0
+        while time.perf_counter() - t0 < args.cpu_budget and i < len(Ns):
+            oracle.matpow_f64(hostA[i], ns[i])
+            done += gemm_count(ns[i]) * 2.0 * Ns[i] ** 3
+            i += 1
+        dt = time.perf_counter() - t0
+        cb = {"value": done / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+              "sample": "float64 square-and-multiply of the first %d matrices of the batch (%.1f s)" % (i, dt)}
+    line = {"metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": wk["desc"], "precision": args.precision,
+                       "matrices": len(Ns), "gemms_per_step": sum(gemm_count(n) for n in ns),
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "rel_frobenius_vs_f64": errs, "status": st, "wall_s_timed": wall, "clocks": clocks,
+            "e2e": {"value": flop_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": int(sum(a.nbytes for a in hostA)),
+                    "d2h_bytes_per_step": int(sum(a.nbytes for a in hostA) + 8 * len(Ns))},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb}
+    print(json.dumps(line))
+    plan.close()
+
+
+def run_serving(args, wk, world, rank, local):
+    """Config 5 (scaled): Poisson arrivals through matpow_submit / matpow_poll."""
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    from paper_1204_3052_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count = wk["count"]
+    # offered load: requests per second (about the measured capacity by default)
+    rate = args.serving_rate
+    reqs = wl.serving_stream(count=count, seed=0, rate_per_s=rate)
+    host = [wl.request_matrix(r) for r in reqs]
+    dA, outs, lgs = [], [], []
+    for r, a in zip(reqs, host):
+        t = torch.from_numpy(a.view(np.int32) if r.kind else a).to(dev)
+        dA.append(t)
+        outs.append(torch.empty_like(t))
+        lgs.append(torch.zeros(1, dtype=torch.int64, device=dev) if r.kind == 0 else None)
+    flop = sum(gemm_count(r.n) * 2.0 * r.N ** 3 for r in reqs)
+    server = mpw.Server(2048, args.precision, device=local, hbm_budget_bytes=16 << 30,
+                        max_inflight=256, max_queue=count + 16)
+    # warm-up requests (not timed)
+    for i in range(min(8, count)):
+        r = reqs[i]
+        server.wait(server.submit(dA[i], r.n, outs[i], kind=r.kind, p=r.p, log2_scale=lgs[i]))
+    base_lat = len(server.latencies_us())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for i, r in enumerate(reqs):
+        delay = r.t_arrival - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(server.submit(dA[i], r.n, outs[i], kind=r.kind, p=r.p, log2_scale=lgs[i]))
+    bad = 0
+    for t in tickets:
+        if server.wait(t, timeout_s=600) != mpw.OK:
+            bad += 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lat = server.latencies_us()[base_lat:]
+    server.close()
+    # exact mod-p requests checked against the oracle (those with N <= 256)
+    checked = mism = 0
+    if not args.no_check:
+        import oracle
+        for r, a, o in zip(reqs, host, outs):
+            if r.kind == 1 and r.N <= 256:
+                want, _ = oracle.matpow_modp(a, r.n, r.p)
+                checked += 1
+                mism += int(not np.array_equal(o.cpu().numpy().view(np.uint32).astype(np.uint64), want))
+    # unbatched comparator: the same requests one at a time through plans
+    plan_f = mpw.Plan(2048, args.precision, device=local)
+    plan_m = mpw.Plan(2048, "fp32", device=local)
+    sample = list(range(0, count, max(1, count // 200)))
+    torch.cuda.synchronize()
+    u0 = time.perf_counter()
+    for i in sample:
+        r = reqs[i]
+        if r.kind:
+            mpw._check(mpw.matpow_mod_p(plan_m.h, dA[i], r.N, r.n, r.p, outs[i]), plan_m.h)
+        else:
+            mpw._check(mpw.matpow_f32(plan_f.h, dA[i], r.N, r.n, outs[i], lgs[i]), plan_f.h)
+    torch.cuda.synchronize()
+    unb = (time.perf_counter() - u0) / len(sample)
+    plan_f.close()
+    plan_m.close()
+    if rank != 0:
+        return
+    lat = np.asarray(lat)
+    line = {"metric": "matpow serving req/s", "value": count / wall, "unit": "req/s", "n_gpus": world,
+            "steps": 1, "warmup": 8, "ms_per_step": wall * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": wk["desc"], "precision": args.precision,
+                       "offered_req_per_s": rate, "requests": count},
+            "p50_ms": float(np.percentile(lat, 50) / 1e3) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99) / 1e3) if lat.size else None,
+            "effective_tflops": flop / wall / 1e12, "failed_requests": bad,
+            "modp_checked": checked, "modp_mismatches": mism,
+            "unbatched_ms_per_request_sampled": unb * 1e3,
+            "unbatched_req_per_s_estimate": 1.0 / unb if unb else None,
+            "e2e": {"value": count / wall, "unit": "req/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0,
+                    "note": "inputs resident; submit-to-completion through the public API"},
+            "gpu_launches": None, "roofline": None, "cpu_baseline": None}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,6 +639,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--ref-budget", type=float, default=5.0)
+    ap.add_argument("--serving-rate", type=float, default=400.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -373,6 +647,10 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, wk, world, rank)
+    elif wk.get("kind") == "batched":
+        run_batched(args, wk, world, rank, local)
+    elif wk.get("kind") == "serving":
+        run_serving(args, wk, world, rank, local)
     else:
         run_ours(args, wk, world, rank, local)
     if world > 1:
