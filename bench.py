@@ -29,6 +29,15 @@ import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) from one ncu capture, keyed by (workload, precision);
+# the summaries under profiles/ give the command.  Reset to None whenever the
+# kernel changes.
+TRAFFIC = {
+    ("single512", "bf16x3"): (1152512 + 0, "profiles/tc_chain_kernel_single512.md (n=1024 launch)"),
+    ("probe4096", "bf16x3"): (278682624 + 56859136, "profiles/tc_fxb_kernel_probe4096.md"),
+}
+
 WORKLOADS = {
     "single512": dict(N=512, ns=[2, 16, 128, 1024], gen="gaussian",
                       desc="single N=512 N(0,1/N) float32, n in {2,16,128,1024}, seed 0"),
@@ -375,6 +384,10 @@ def run_ours(args, wk, world, rank, local):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
     roof["launches_timed"] = kl
     roof["avg_launch_us"] = kms * 1e3 / max(kl, 1)
+    tr = TRAFFIC.get((args.workload, prec))
+    if tr:
+        roof["traffic"] = tr[0]
+        roof["traffic_source"] = tr[1]
 
     if rank != 0:
         return
