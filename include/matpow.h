@@ -108,9 +108,12 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       64 < N <= 1024, run the whole chain in one cooperative
  *                       launch (grid barriers between levels); 0: one launch
  *                       per level.
+ *   MATPOW_OPT_MODP_TC  1 (default): matpow_mod_p with 64 < N <= 16384 runs on the
+ *                       tensor cores (byte slices of the residues, exact partial
+ *                       sums); 0: 64-bit integer products on the CUDA cores.
  */
 enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4,
-       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6 };
+       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6, MATPOW_OPT_MODP_TC = 7 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
 /* ---- the power ------------------------------------------------------------ */

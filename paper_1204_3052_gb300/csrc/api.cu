@@ -180,6 +180,7 @@ extern "C" matpow_status matpow_plan(matpow_plan_t* out, int max_n, matpow_preci
   if (e == cudaSuccess) e = tiny_attrs();
   if (e == cudaSuccess) e = tc_init(p);
   if (e == cudaSuccess) e = tc_chain_init(p);
+  if (e == cudaSuccess) e = tc_modp_init();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_status, sizeof(unsigned));
   cudaSetDevice(prev);
@@ -246,6 +247,10 @@ extern "C" matpow_status matpow_plan_set_option(matpow_plan_t p, int key, int64_
       return MATPOW_OK;
     case MATPOW_OPT_CHAIN:
       p->use_chain = value != 0;
+      return MATPOW_OK;
+    case MATPOW_OPT_MODP_TC:
+      p->modp_tc = value != 0;
+      drop_graphs(p);
       return MATPOW_OK;
     case MATPOW_OPT_SPLIT:
       if (value != 0 && value != 1) return fail(p, MATPOW_EINVAL, "split mode must be 0 or 1");
@@ -464,6 +469,47 @@ static matpow_status enqueue_modp(matpow_plan_s* p, const uint32_t* dA, int N, u
   if (n == 0) {
     CK(p, launch_identity(dOut, N, 1, 1u % pmod, nullptr, s));
     p->launches++;
+    return MATPOW_OK;
+  }
+  if (n >= 2 && p->modp_tc && N > 64 && N <= 16384) {
+    // tensor cores: byte slices, exact chunk sums, Barrett reduction
+    const int ldm = ld_for(N, FMT_MODP);
+    const long long plane = plane_offset_elems(N, FMT_MODP);
+    CK(p, launch_prep_modp_slices(dA, N, pmod, p->buf[0], p->status, s));
+    p->launches++;
+    std::vector<LevelOps> levels;
+    build_schedule(n, &levels);
+    const int tn = (N + tc_modp_tile_n() - 1) / tc_modp_tile_n();
+    const int tm = (N + 127) / 128;
+    for (size_t li = 0; li < levels.size(); ++li) {
+      const LevelOps& lv = levels[li];
+      GemmPair g{};
+      g.count = (int)lv.ops.size();
+      int t = 0;
+      for (int i = 0; i < g.count; ++i) {
+        const Op& op = lv.ops[i];
+        const bool last = (li + 1 == levels.size()) && (i + 1 == g.count);
+        GemmDesc& d = g.d[i];
+        d.X = p->buf[op.xb];
+        d.Y = p->buf[op.yb];
+        d.C = last ? nullptr : p->buf[op.cb];
+        d.out = last ? (void*)dOut : nullptr;
+        d.N = N;
+        d.ld = ldm;
+        d.plane = plane;
+        d.mode = last ? OUT_USER_VALUE : OUT_INTERNAL;
+        d.p = pmod;
+        d.tile_begin = t;
+        d.tiles_n = tn;
+        t += tm * tn;
+      }
+      g.tiles_total = t;
+      timed_begin(p, s, &ev);
+      matpow_status st = tc_modp_launch_pair(p, g, s);
+      if (st != MATPOW_OK) return st;
+      timed_end(p, s, ev, MATPOW_KERNEL_MODP, 2.0 * N * (double)N * N * g.count);
+      p->launches++;
+    }
     return MATPOW_OK;
   }
   // check entries (and copy into the stored format) for every n >= 1

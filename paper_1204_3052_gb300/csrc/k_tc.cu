@@ -33,6 +33,7 @@
 #include "internal.cuh"
 #include "plan.h"
 #include "tc_ptx.cuh"
+#include "tc_common.cuh"
 #include "fxb.cuh"
 
 namespace mp {
@@ -51,17 +52,6 @@ struct Cfg {
 };
 }  // namespace tc
 
-struct TcProblem {
-  CUtensorMap ax[2];  // X as the A operand: hi, lo planes (box 64 x 128)
-  CUtensorMap by[2];  // Y as the B operand: hi, lo planes (box 64 x 64)
-  GemmDesc d;
-};
-
-struct TcPairParams {
-  TcProblem p[2];
-  int count;
-  int tiles0;
-};
 
 template <int BN, int PL>
 __global__ void __launch_bounds__(tc::THREADS, 1)

@@ -1,0 +1,305 @@
+// Exact products over the integers mod p on the tensor cores.
+//
+// A residue x in [0, p), p <= 65536, is stored as two byte slices
+// x = 256 x1 + x0 (x1, x0 in [0, 255], exact in bfloat16).  For C = X Y mod p
+// (arXiv 1204.3052 Sec. 4.1's product, inside Sec. 4.3's chain) the tensor
+// cores form, per 256-deep chunk of k,
+//     H  = sum x1 y1,   M1 = sum x1 y0,   M2 = sum x0 y1,   L = sum x0 y0,
+// each a sum of at most 256 products <= 255^2, i.e. below 2^24: the float32
+// TMEM accumulators hold them exactly.  The epilogue warps add the chunk sums
+// into 32-bit integer totals (exact for N <= 32768), and at the end
+//     c = (H * 2^16 + (M1 + M2) * 2^8 + L) mod p
+// with Barrett reductions; a non-final product writes c's byte slices straight
+// into the next product's operand planes.
+//
+// CTA: 384 threads.  Warp 0 TMA, warp 1 MMA (4 MMAs per 16-deep step), warp 2
+// TMEM (2 buffers x 4 accumulators x 64 columns = 512), warps 4-11 epilogue
+// (lane quadrant w % 4, column half (w - 4) / 4).  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "plan.h"
+#include "tc_common.cuh"
+#include "tc_ptx.cuh"
+
+namespace mp {
+
+namespace tcm {
+constexpr int BM = 128, BN = 64, BK = 64, CHUNK_KB = 4;
+constexpr int EW = 8, THREADS = 128 + 32 * EW, WC = 32;
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
+constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 512;
+}  // namespace tcm
+
+// x mod p for x < 2^32 with m = floor(2^32 / p): one correction step.
+__device__ __forceinline__ unsigned barrett(unsigned x, unsigned p, unsigned m) {
+  unsigned q = __umulhi(x, m);
+  unsigned r = x - q * p;
+  return r >= p ? r - p : r;
+}
+
+__global__ void __launch_bounds__(tcm::THREADS, 1)
+    tc_modp_kernel(const __grid_constant__ TcPairParams P, unsigned* status) {
+  using namespace tcm;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  // full[S], empty[S], accfull[2], accempty[2], drain
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const uint32_t full0 = ptx::smem_u32(bars);
+  const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
+  const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
+  const uint32_t accempty0 = ptx::smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int t = blockIdx.x;
+  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
+  if (which) t -= P.tiles0;
+  const TcProblem& pr = P.p[which];
+  const GemmDesc& d = pr.d;
+  const int tm = t / d.tiles_n, tn = t - (t / d.tiles_n) * d.tiles_n;
+  const int m0 = tm * BM, n0 = tn * BN;
+  const int N = d.N;
+  const int KB = (N + BK - 1) / BK;
+  const int NCH = (KB + CHUNK_KB - 1) / CHUNK_KB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(full0 + 8 * s, 1);
+      ptx::mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(accfull0 + 8 * b, 1);
+      ptx::mbar_init(accempty0 + 8 * b, EW);
+    }
+    ptx::mbar_init(drainb, 1);
+    *abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  if (warp == 0 && lane == 0) {
+    ptx::prefetch_tmap(&pr.ax[0]);
+    ptx::prefetch_tmap(&pr.ax[1]);
+    ptx::prefetch_tmap(&pr.by[0]);
+    ptx::prefetch_tmap(&pr.by[1]);
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        if (!ptx::mbar_wait(empty0 + 8 * s, ((kb / STAGES) & 1) ^ 1, abort_flag, WAIT_NS)) {
+          *abort_flag = 1;
+          break;
+        }
+        const uint32_t fb = full0 + 8 * s;
+        ptx::mbar_expect_tx(fb, STAGE_BYTES);
+        const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
+        const int kx = kb * BK;
+        ptx::tma_load_2d(base, &pr.ax[0], kx, m0, fb);            // x1
+        ptx::tma_load_2d(base + A_BYTES, &pr.ax[1], kx, m0, fb);  // x0
+        ptx::tma_load_2d(base + 2 * A_BYTES, &pr.by[0], n0, kx, fb);            // y1
+        ptx::tma_load_2d(base + 2 * A_BYTES + B_BYTES, &pr.by[1], n0, kx, fb);  // y0
+        ++issued;
+      }
+      for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+        int dummy = 0;
+        ptx::mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, &dummy, WAIT_NS);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      for (int kb = 0; kb < KB; ++kb) {
+        const int ch = kb / CHUNK_KB;
+        const int buf = ch & 1;
+        const bool first = (kb % CHUNK_KB) == 0;
+        const bool last = (kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1;
+        const uint32_t tH = tmem + (uint32_t)(buf * 4 * BN);
+        if (first && !ptx::mbar_wait(accempty0 + 8 * buf, ((ch >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int s = kb % STAGES;
+        if (!ptx::mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, abort_flag, WAIT_NS)) {
+          *abort_flag = 1;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t a1 = ptx::smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t a0 = a1 + A_BYTES;
+        const uint32_t b1 = a1 + 2 * A_BYTES;
+        const uint32_t b0 = b1 + B_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t ad1 = ptx::smem_desc(a1 + 32 * k, 16, 1024);
+          const uint64_t ad0 = ptx::smem_desc(a0 + 32 * k, 16, 1024);
+          const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
+          const uint64_t bd0 = ptx::smem_desc(b0 + 2048 * k, 8192, 1024);
+          const uint32_t acc = (first && k == 0) ? 0u : 1u;
+          ptx::mma_f16(tH, ad1, bd1, idesc, acc);               // H  = x1 y1
+          ptx::mma_f16(tH + BN, ad1, bd0, idesc, acc);          // M1 = x1 y0
+          ptx::mma_f16(tH + 2 * BN, ad0, bd1, idesc, acc);      // M2 = x0 y1
+          ptx::mma_f16(tH + 3 * BN, ad0, bd0, idesc, acc);      // L  = x0 y0
+        }
+        ptx::mma_commit(empty0 + 8 * s);
+        if (last) ptx::mma_commit(accfull0 + 8 * buf);
+      }
+      ptx::mma_commit(drainb);
+      int dummy = 0;
+      ptx::mbar_wait(drainb, 0, &dummy, WAIT_NS);
+    }
+  } else if (warp >= 4) {
+    const int q = warp & 3;
+    const int cs = (warp - 4) >> 2;
+    const int row = m0 + 32 * q + lane;
+    const int nw = n0 + cs * WC;
+    unsigned Ht[WC], Mt[WC], Lt[WC];
+#pragma unroll
+    for (int j = 0; j < WC; ++j) Ht[j] = Mt[j] = Lt[j] = 0u;
+    bool ok = true;
+    for (int ch = 0; ch < NCH; ++ch) {
+      const int buf = ch & 1;
+      int dummy = 0;
+      if (!ptx::mbar_wait(accfull0 + 8 * buf, (ch >> 1) & 1, &dummy, 2 * WAIT_NS)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      ptx::tc_fence_after();
+      const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 4 * BN + cs * WC);
+      uint32_t r[32];
+      ptx::tmem_ld_32x32b_x32(tq, r);
+      ptx::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < WC; ++j) Ht[j] += (unsigned)__uint_as_float(r[j]);
+      ptx::tmem_ld_32x32b_x32(tq + BN, r);
+      ptx::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
+      ptx::tmem_ld_32x32b_x32(tq + 2 * BN, r);
+      ptx::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
+      ptx::tmem_ld_32x32b_x32(tq + 3 * BN, r);
+      ptx::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < WC; ++j) Lt[j] += (unsigned)__uint_as_float(r[j]);
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
+    }
+    if (ok && !*abort_flag && row < N) {
+      const unsigned pm = d.p;
+      const unsigned bm = (unsigned)(0x100000000ull / pm);
+      const unsigned c16 = (unsigned)((1ull << 16) % pm), c8 = 256u % pm;
+      unsigned res[WC];
+#pragma unroll
+      for (int j = 0; j < WC; ++j) {
+        const unsigned h = barrett(Ht[j], pm, bm), m = barrett(Mt[j], pm, bm), l = barrett(Lt[j], pm, bm);
+        const unsigned v = barrett(h * c16, pm, bm) + barrett(m * c8, pm, bm) + l;  // < 3p
+        res[j] = barrett(v, pm, bm);
+      }
+      if (d.mode == OUT_INTERNAL) {
+        __nv_bfloat16* p1 = (__nv_bfloat16*)d.C + (size_t)row * d.ld + nw;
+        __nv_bfloat16* p0 = p1 + d.plane;
+#pragma unroll
+        for (int j = 0; j < WC; ++j) {
+          if (nw + j < N) {
+            p1[j] = __float2bfloat16_rn((float)(res[j] >> 8));
+            p0[j] = __float2bfloat16_rn((float)(res[j] & 255u));
+          }
+        }
+      } else {
+        unsigned* O = (unsigned*)d.out + (size_t)row * N;
+#pragma unroll
+        for (int j = 0; j < WC; ++j)
+          if (nw + j < N) O[nw + j] = res[j];
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+}
+
+// A (uint32, leading dimension N) -> byte slices (x >> 8, x & 255) as bfloat16
+// planes with leading dimension ld; entries >= p flag ST_BADINPUT.
+__global__ void prep_modp_slices_kernel(const unsigned* __restrict__ A, int N, int ld, unsigned p,
+                                        __nv_bfloat16* dst, long long plane, unsigned* status) {
+  const size_t total = (size_t)N * ld;
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / ld;
+    const int c = (int)(i - r * ld);
+    const unsigned v = c < N ? A[r * N + c] : 0u;
+    bad |= v >= p;
+    dst[i] = __float2bfloat16_rn((float)(v >> 8));
+    dst[plane + i] = __float2bfloat16_rn((float)(v & 255u));
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_BADINPUT);
+}
+
+// ---------------------------------------------------------------------------
+
+cudaError_t tc_modp_init() {
+  return cudaFuncSetAttribute(tc_modp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcm::SMEM);
+}
+
+int tc_modp_tile_n() { return tcm::BN; }
+
+cudaError_t launch_prep_modp_slices(const unsigned* A, int N, unsigned p, void* dst,
+                                    unsigned* status, cudaStream_t s) {
+  const int ld = ld_for(N, FMT_MODP);
+  const long long plane = plane_offset_elems(N, FMT_MODP);
+  const size_t total = (size_t)N * ld;
+  size_t b = (total + 255) / 256;
+  const int grid = (int)(b < 1216 ? (b ? b : 1) : 1216);
+  prep_modp_slices_kernel<<<grid, 256, 0, s>>>(A, N, ld, p, (__nv_bfloat16*)dst, plane, status);
+  return cudaGetLastError();
+}
+
+matpow_status tc_modp_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s) {
+  TcPairParams P;
+  memset(&P, 0, sizeof P);
+  P.count = g.count;
+  for (int i = 0; i < g.count; ++i) {
+    const GemmDesc& d = g.d[i];
+    TcProblem& tp = P.p[i];
+    tp.d = d;
+    const size_t lo = (size_t)d.plane * 2;
+    if (!tc_encode_bf16_map(&tp.ax[0], d.X, d.N, d.ld, 64, tcm::BM) ||
+        !tc_encode_bf16_map(&tp.ax[1], (const char*)d.X + lo, d.N, d.ld, 64, tcm::BM) ||
+        !tc_encode_bf16_map(&tp.by[0], d.Y, d.N, d.ld, 64, 64) ||
+        !tc_encode_bf16_map(&tp.by[1], (const char*)d.Y + lo, d.N, d.ld, 64, 64))
+      return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", d.N);
+  }
+  P.tiles0 = g.count > 1 ? g.d[1].tile_begin : g.tiles_total;
+  tc_modp_kernel<<<g.tiles_total, tcm::THREADS, tcm::SMEM, s>>>(P, p->status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(p, e, "tc_modp_kernel launch");
+  return MATPOW_OK;
+}
+
+}  // namespace mp

@@ -94,6 +94,7 @@ struct matpow_plan_s {
   int tile_override = 0;
   int split_mode = 0;  // BF16X3: 0 exact fixed-point slices, 1 floating hi/lo planes
   bool use_chain = true;  // whole-chain cooperative kernel where it applies
+  bool modp_tc = true;    // mod-p products on the tensor cores (64 < N <= 16384)
   int group_bn = 64;      // tile width of the current grouped tensor-core launch
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
   // graphs
@@ -134,6 +135,12 @@ bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box
 matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
                            int64_t* dLog2, cudaStream_t s, bool* used);
 cudaError_t tc_chain_init(matpow_plan_s* p);
+// tensor-core mod-p products (k_tcmodp.cu)
+cudaError_t tc_modp_init();
+int tc_modp_tile_n();
+cudaError_t launch_prep_modp_slices(const unsigned* A, int N, unsigned p, void* dst,
+                                    unsigned* status, cudaStream_t s);
+matpow_status tc_modp_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s);
 matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                               Scale* scales, cudaStream_t s);
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,

@@ -28,7 +28,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EAGAIN", "EBUSY", "ETIMEDOUT
                 "EUNSUPPORTED"]
 FP32_SIMT, BF16, BF16X3 = 0, 1, 2
 PRECISIONS = {"fp32": FP32_SIMT, "fp32_simt": FP32_SIMT, "bf16": BF16, "bf16x3": BF16X3}
-OPT_GRAPHS, OPT_TIMING, OPT_TINY_MAX, OPT_TILE, OPT_SPLIT, OPT_CHAIN = 1, 2, 3, 4, 5, 6
+OPT_GRAPHS, OPT_TIMING, OPT_TINY_MAX, OPT_TILE, OPT_SPLIT, OPT_CHAIN, OPT_MODP_TC = 1, 2, 3, 4, 5, 6, 7
 KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_MODP, KERNEL_AUX = range(5)
 
 EXPORTS = [

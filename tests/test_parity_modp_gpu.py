@@ -9,10 +9,11 @@ from paper_1204_3052_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def plan():
+@pytest.fixture(scope="module", params=["tensor", "simt"])
+def plan(request):
     from paper_1204_3052_gb300 import matpow as mpw
     p = mpw.Plan(1024, "bf16x3")
+    p.set_option(mpw.OPT_MODP_TC, 1 if request.param == "tensor" else 0)
     yield p
     p.close()
 
@@ -58,3 +59,20 @@ def test_modp_rejects_unreduced(plan):
     A[3, 4] = 7
     got, st = run(plan, A, 5, 7)
     assert st == 1  # MATPOW_EINVAL from the device check
+
+
+def test_modp_tensor_and_simt_agree_on_large_orders():
+    from paper_1204_3052_gb300 import matpow as mpw
+    import torch
+    tc = mpw.Plan(2100, "fp32")
+    sm = mpw.Plan(2100, "fp32")
+    sm.set_option(mpw.OPT_MODP_TC, 0)
+    for N, n, p in ((1000, 77, 65521), (2100, 5, 65536), (513, 2 ** 40 + 3, 251)):
+        A = wl.modp_uniform(N, p, N)
+        dA = to_dev(A.view(np.int32))
+        a = tc.mod_p(dA, n, p)
+        b = sm.mod_p(dA, n, p)
+        assert tc.sync() == 0 and sm.sync() == 0
+        assert torch.equal(a, b), (N, n, p)
+    tc.close()
+    sm.close()
