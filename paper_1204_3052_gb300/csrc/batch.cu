@@ -195,6 +195,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
             d.tiles_n = (Ni + bn - 1) / bn;
             d.map_x = 16 * (int)bi + 4 * op.xb;
             d.map_y = 16 * (int)bi + 4 * op.yb;
+            d.map_c = 16 * (int)bi + 4 * (last ? op.xb : op.cb);
             tiles += ((Ni + 127) / 128) * d.tiles_n;
           } else {
             d.tiles_n = (Ni + simt_tile_edge() - 1) / simt_tile_edge();

@@ -131,6 +131,80 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
   epi_bar<NT>();  // red may be reused
 }
 
+// Like store_slices, but the slice planes leave through TMA: each epilogue
+// thread writes its row of every 64-column box into shared memory in the
+// 128-byte-swizzled layout the tensor map expects (16-byte chunk c of row r at
+// chunk position c ^ (r % 8)), then one thread stores each 128 x 64 box with
+// one bulk-tensor instruction and waits for the writes to complete (they are
+// read by TMA loads of the next product, after a barrier).
+//   T: this thread's WC columns starting at nw (a multiple of 64); r: row in
+//   the 128-row tile (32 q + lane); stage: 1024-aligned shared memory with
+//   room for 2 planes x (number of boxes) x 16 KB; box0: index of this
+//   warp's first box; c1, c2: the destination planes' tensor maps (box 64 x
+//   128); leader: the one thread that issues the stores; NT epilogue threads.
+template <int WC, int NT>
+__device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, int m0, int nw, int q,
+                                                 int lane, int N, int box0, int nbox, uint8_t* stage,
+                                                 const CUtensorMap* c1, const CUtensorMap* c2,
+                                                 int* bexp, unsigned* maxbits, float* red,
+                                                 bool leader, int n0) {
+  constexpr int NG = WC / BLK;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < BLK; ++j) m = fmaxf(m, fabsf(T[BLK * g + j]));
+    m = warp_max(m);
+    if (lane == 0) red[(box0 + g) * 4 + q] = m;
+  }
+  epi_bar<NT>();
+  const int nb = nblocks(N);
+  const int I = m0 / BLK + (q >> 1);
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const int b = box0 + g;
+    const float bm = fmaxf(red[b * 4 + q], red[b * 4 + (q ^ 1)]);
+    const int e = frexp_exp(bm);
+    const int J = (nw + BLK * g) / BLK;
+    if ((q & 1) == 0 && lane == 0 && I < nb && J < nb) {
+      bexp[I * nb + J] = e;
+      if (bm > 0.f) atomicMax(maxbits, __float_as_uint(bm));
+    }
+    uint8_t* p1 = stage + (size_t)b * 32768 + r * 128;
+    uint8_t* p2 = p1 + 16384;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float h0, l0, h1, l1;
+        slice(T[BLK * g + 8 * c + 2 * h], e, &h0, &l0);
+        slice(T[BLK * g + 8 * c + 2 * h + 1], e, &h1, &l1);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
+        __nv_bfloat162 lo = __floats2bfloat162_rn(l0, l1);
+        hw[h] = *reinterpret_cast<uint32_t*>(&hi);
+        lw[h] = *reinterpret_cast<uint32_t*>(&lo);
+      }
+      const int pos = (c ^ (r & 7)) * 16;
+      *reinterpret_cast<uint4*>(p1 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(p2 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+  ptx::fence_proxy_async_smem();  // generic smem writes -> visible to the TMA engine
+  epi_bar<NT>();
+  if (leader) {
+    for (int b = 0; b < nbox; ++b) {
+      const uint32_t src = ptx::smem_u32(stage + (size_t)b * 32768);
+      ptx::tma_store_2d(c1, n0 + BLK * b, m0, src);
+      ptx::tma_store_2d(c2, n0 + BLK * b, m0, src + 16384);
+    }
+    ptx::bulk_commit();
+    ptx::bulk_wait_all();
+    ptx::fence_proxy_async_global();
+  }
+  epi_bar<NT>();  // the stage and red may be reused
+}
+
 // Fold one finished k-block (main at TMEM column tq, cross at tq + cross_off)
 // into T with the block factors fac[g] (one per 64 columns).
 template <int BN>

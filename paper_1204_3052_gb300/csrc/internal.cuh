@@ -60,8 +60,8 @@ struct GemmDesc {
   int tiles_n;           // tiles along a row of C
   unsigned p;            // modulus (mod-p paths)
   int bn;                // tensor-core tile width (columns of C per CTA)
-  int map_x, map_y;      // grouped tensor-core launches: TMA descriptors of X and Y
-                         // (4 per buffer: A-role a1, a2, B-role a1, a2)
+  int map_x, map_y;      // grouped tensor-core launches: TMA descriptors of X, Y and C
+  int map_c, pad2_;      // (4 per buffer: A-role a1, a2, B-role a1, a2)
 };
 
 // Up to two products passed by value (one squaring level of one matrix:

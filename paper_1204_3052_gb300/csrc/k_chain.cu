@@ -313,9 +313,10 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
           }
         } else {
           if (t == 0 && q == 0 && lane == 0) P.scales[op.sc].E = Ec;
-          if (ok)
-            fxb::store_slices<BN>(T, row, m0, n0, q, lane, N, ld, (__nv_bfloat16*)P.slices[op.cb],
-                                  P.plane, P.bexp[op.cb], &P.scales[op.sc].maxbits, ered);
+          if (ok)  // the ring is idle here: all k-blocks of this tile were consumed
+            fxb::store_slices_tma<BN, 128>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
+                                           &P.amap[op.cb][0], &P.amap[op.cb][1], P.bexp[op.cb],
+                                           &P.scales[op.sc].maxbits, ered, q == 0 && lane == 0, n0);
           fence_proxy_async_global();
         }
       }

@@ -286,7 +286,8 @@ struct Cfg {
 template <int BN>
 __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensorMap* ax0,
                                         const CUtensorMap* ax1, const CUtensorMap* by0,
-                                        const CUtensorMap* by1, Scale* scales, unsigned* status) {
+                                        const CUtensorMap* by1, const CUtensorMap* cx0,
+                                        const CUtensorMap* cx1, Scale* scales, unsigned* status) {
   using namespace tc;
   using C = fx::Cfg<BN>;
   constexpr int EW = C::EW, WC = C::WC;
@@ -458,10 +459,10 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
     const long long Ec = scales[d.sx].E + scales[d.sy].E + sx + sy;
     if (d.mode == OUT_INTERNAL) {
       if (t == 0 && e == 0 && lane == 0) scales[d.sc].E = Ec;
-      if (ok)  // every epilogue warp reaches the named barriers inside
-        fxb::store_slices<WC, 32 * EW>(T, row, m0, nw, q, lane, N, d.ld, (__nv_bfloat16*)d.C,
-                                       d.plane, (int*)((char*)d.C + boff), &scales[d.sc].maxbits,
-                                       red + cs * 4 * (WC / 64));
+      if (ok)  // every epilogue warp reaches the named barriers inside; the ring is idle
+        fxb::store_slices_tma<WC, 32 * EW>(T, 32 * q + lane, m0, nw, q, lane, N, cs * (WC / 64),
+                                           BN / 64, smem, cx0, cx1, (int*)((char*)d.C + boff),
+                                           &scales[d.sc].maxbits, red, e == 0 && lane == 0, n0);
     } else if (ok) {
       if (t == 0 && e == 0 && lane == 0 && d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
       if (row < N) {
@@ -491,7 +492,8 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
   const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
   if (which) t -= P.tiles0;
   const TcProblem& pr = P.p[which];
-  fxb_cta<BN>(pr.d, t, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], scales, status);
+  fxb_cta<BN>(pr.d, t, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], &pr.cx[0], &pr.cx[1], scales,
+              status);
 }
 
 // Grouped launch: products from a device table (any number of matrices),
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
   }
   const GemmDesc d = descs[lo];
   fxb_cta<BN>(d, tb - d.tile_begin, &maps[d.map_x], &maps[d.map_x + 1], &maps[d.map_y + 2],
-              &maps[d.map_y + 3], scales, status);
+              &maps[d.map_y + 3], &maps[d.map_c], &maps[d.map_c + 1], scales, status);
 }
 
 // A (float32, leading dimension N) -> block-scaled stored format, one CTA per
@@ -611,6 +613,13 @@ static bool fill_problem(TcProblem* tp, const GemmDesc& d, int PL) {
   } else {
     tp->ax[1] = tp->ax[0];
     tp->by[1] = tp->by[0];
+  }
+  if (d.C) {  // TMA store targets of the output planes
+    if (!tc_encode_bf16_map(&tp->cx[0], d.C, d.N, d.ld, 64, tc::BM)) return false;
+    if (!tc_encode_bf16_map(&tp->cx[1], (const char*)d.C + lo, d.N, d.ld, 64, tc::BM)) return false;
+  } else {
+    tp->cx[0] = tp->ax[0];
+    tp->cx[1] = tp->ax[1];
   }
   return true;
 }

@@ -267,6 +267,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
           d.tiles_n = (r.N + d.bn - 1) / d.bn;
           d.map_x = 16 * q->chunk + 4 * op.xb;
           d.map_y = 16 * q->chunk + 4 * op.yb;
+          d.map_c = 16 * q->chunk + 4 * (last ? op.xb : op.cb);
           const int nt = ((r.N + 127) / 128) * d.tiles_n;
           if (d.bn == 64) {
             d.tile_begin = tiles_f;
