@@ -46,6 +46,14 @@ __device__ __forceinline__ float pow2f(int k) {
   return mul_pow2(1.0f, k);
 }
 
+// The i-th k-block a tile visits: tiles start at different k-blocks (tm + tn)
+// so that CTAs sharing an operand band do not read the same lines at the same
+// time.  The fold order follows it, identically in every kernel.
+__device__ __forceinline__ int rot_kb(int i, int KB, int rot) {
+  int k = i + rot % KB;
+  return k >= KB ? k - KB : k;
+}
+
 __device__ __forceinline__ int frexp_exp(float m) { return scale_exp_from_bits(__float_as_uint(m)); }
 
 __device__ __forceinline__ void slice(float v, int e, float* h, float* l) {

@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
             const uint32_t fb = full0 + 8 * s;
             ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
             const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-            const int kx = kb * BK;
+            const int kx = fxb::rot_kb(kb, KB, tm + tn) * BK;
             ptx::tma_load_2d(base, am1, kx, m0, fb);
             ptx::tma_load_2d(base + C::A_BYTES, am2, kx, m0, fb);
             const uint32_t bbase = base + 2 * C::A_BYTES;
@@ -285,10 +285,11 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
             break;
           }
           ptx::tc_fence_after();
+          const int kr = fxb::rot_kb(kb, KB, tm + tn);
           float fac[NG];
 #pragma unroll
           for (int gg = 0; gg < NG; ++gg)
-            fac[gg] = fxb::pow2f(eA[h * KB + kb] + eB[kb * NG + gg] - 16 - sx - sy);
+            fac[gg] = fxb::pow2f(eA[h * KB + kr] + eB[kr * NG + gg] - 16 - sx - sy);
           fxb::fold<BN>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN), fac);
           ptx::tc_fence_before();
           __syncwarp();

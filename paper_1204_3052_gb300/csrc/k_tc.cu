@@ -357,7 +357,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         const uint32_t fb = full0 + 8 * s;
         ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-        const int kx = kb * BK;
+        const int kx = fxb::rot_kb(kb, KB, tm + tn) * BK;
         ptx::tma_load_2d(base, ax0, kx, m0, fb);
         ptx::tma_load_2d(base + C::A_BYTES, ax1, kx, m0, fb);
         const uint32_t bbase = base + 2 * C::A_BYTES;
@@ -442,10 +442,11 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         break;
       }
       ptx::tc_fence_after();
+      const int kr = fxb::rot_kb(kb, KB, tm + tn);
       float fac[WC / 64];
 #pragma unroll
       for (int g = 0; g < WC / 64; ++g)
-        fac[g] = fxb::pow2f(eA[h * KB + kb] + eB[kb * NG + cs * (WC / 64) + g] - 16 - sx - sy);
+        fac[g] = fxb::pow2f(eA[h * KB + kr] + eB[kr * NG + cs * (WC / 64) + g] - 16 - sx - sy);
       fxb::fold<WC>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN + cs * WC), fac, BN);
       ptx::tc_fence_before();
       __syncwarp();
