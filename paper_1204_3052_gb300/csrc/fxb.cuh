@@ -46,7 +46,8 @@ __device__ __forceinline__ float pow2f(int k) {
   return mul_pow2(1.0f, k);
 }
 
-// The i-th k-block a tile visits: tiles start at different k-blocks (tm + tn)
+// The i-th k-block a tile visits: tiles start at different k-blocks ((m0 + n0) / 128,
+// the same for 64- and 128-wide tiles covering an element)
 // so that CTAs sharing an operand band do not read the same lines at the same
 // time.  The fold order follows it, identically in every kernel.
 __device__ __forceinline__ int rot_kb(int i, int KB, int rot) {

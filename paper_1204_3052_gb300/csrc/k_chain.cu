@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
             const uint32_t fb = full0 + 8 * s;
             ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
             const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-            const int kx = fxb::rot_kb(kb, KB, tm + tn) * BK;
+            const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
             ptx::tma_load_2d(base, am1, kx, m0, fb);
             ptx::tma_load_2d(base + C::A_BYTES, am2, kx, m0, fb);
             const uint32_t bbase = base + 2 * C::A_BYTES;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
             break;
           }
           ptx::tc_fence_after();
-          const int kr = fxb::rot_kb(kb, KB, tm + tn);
+          const int kr = fxb::rot_kb(kb, KB, (m0 + n0) / 128);
           float fac[NG];
 #pragma unroll
           for (int gg = 0; gg < NG; ++gg)

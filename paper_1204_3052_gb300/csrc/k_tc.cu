@@ -357,7 +357,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         const uint32_t fb = full0 + 8 * s;
         ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-        const int kx = fxb::rot_kb(kb, KB, tm + tn) * BK;
+        const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
         ptx::tma_load_2d(base, ax0, kx, m0, fb);
         ptx::tma_load_2d(base + C::A_BYTES, ax1, kx, m0, fb);
         const uint32_t bbase = base + 2 * C::A_BYTES;
@@ -442,7 +442,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         break;
       }
       ptx::tc_fence_after();
-      const int kr = fxb::rot_kb(kb, KB, tm + tn);
+      const int kr = fxb::rot_kb(kb, KB, (m0 + n0) / 128);
       float fac[WC / 64];
 #pragma unroll
       for (int g = 0; g < WC / 64; ++g)
