@@ -34,8 +34,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 # the summaries under profiles/ give the command.  Reset to None whenever the
 # kernel changes.
 TRAFFIC = {
-    ("single512", "bf16x3"): (1152512 + 0, "profiles/tc_chain_kernel_single512.md (n=1024 launch)"),
-    ("probe4096", "bf16x3"): (278682624 + 56859136, "profiles/tc_fxb_kernel_probe4096.md"),
+    # re-captured whenever the kernels change; empty until then
 }
 
 WORKLOADS = {
