@@ -29,14 +29,17 @@ Functions and the passage each follows:
   the power-of-two maximum 2^s of each block x block tile (block=None: one
   scale for the whole matrix): u = X 2^(8-s), a1 = rint(u),
   a2 = rint(256 (u - a1)), so X ~ 2^(s-16) (256 a1 + a2) with integer slices
-  |a1| <= 256, |a2| <= 128.
+  |a1| <= 256, |a2| <= 128.  ``fixed_slices_n(X, block, k)`` continues the
+  same recurrence to k slices (a_(j+1) = rint(256 * remainder)), so
+  X ~ 2^(s-8k) sum_j 256^(k-1-j) a_j.
 * ``emu_sqmul(A, n, precision)``: the square-and-multiply chain with the
   operand rounding of a tensor-core precision emulated on the CPU ("bf16":
   one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi of floating
   bfloat16 parts; "bf16x3fx": a1*b1 + a1*b2 + a2*b1 of the fixed-point
   slices with one scale per matrix; "bf16x3blk": the same with one scale per
-  64 x 64 block; products and sums in float64, each result rounded to
-  float32).  Like ``fp32_sqmul`` it is an
+  64 x 64 block; "bf16x6blk": three block-scaled slices and the six products
+  a_i b_j with i + j <= 2; products and sums in float64, each result rounded
+  to float32).  Like ``fp32_sqmul`` it is an
   error yardstick for the lower-precision paths, not a parity target; the
   rounding primitives it uses are pinned by the tests.
 
@@ -306,7 +309,32 @@ def fixed_slices(X, block=None):
     return a1, a2, s
 
 
+def fixed_slices_n(X, block, k: int):
+    """([a_0, ..., a_(k-1)], s): the k-slice fixed-point split of X with one
+    frexp exponent per block x block tile (s has X's shape):
+    u = X 2^(8-s), a_0 = rint(u), a_(j+1) = rint(256 (u_j - a_j)) with
+    u_(j+1) = 256 (u_j - a_j); X ~ 2^(s-8k) sum_j 256^(k-1-j) a_j."""
+    a1, _, s = fixed_slices(X, block)
+    u = np.ldexp(np.asarray(X, dtype=np.float32).astype(np.float64), 8 - s)
+    out = []
+    for _ in range(k):
+        a = np.rint(u)
+        out.append(a)
+        u = (u - a) * 256.0
+    return out, s
+
+
 def _emu_product(X, Y, precision: str) -> np.ndarray:
+    if precision == "bf16x6blk":
+        a, sx = fixed_slices_n(X, 64, 3)
+        b, sy = fixed_slices_n(Y, 64, 3)
+        x = [np.ldexp(a[j], sx - 8 * (j + 1)) for j in range(3)]
+        y = [np.ldexp(b[j], sy - 8 * (j + 1)) for j in range(3)]
+        P = np.zeros((x[0].shape[0], y[0].shape[1]))
+        for i in range(3):
+            for j in range(3 - i):
+                P += x[i] @ y[j]
+        return P.astype(np.float32)
     if precision == "bf16x3fx":
         a1, a2, sx = fixed_slices(X)
         b1, b2, sy = fixed_slices(Y)

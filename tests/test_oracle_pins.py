@@ -431,3 +431,50 @@ def test_block_fixed_slices_reconstruct_per_block():
     Mb, eb = oracle.emu_sqmul(A, 9, "bf16x3blk")
     Mg, eg = oracle.emu_sqmul(A, 9, "bf16x3fx")
     assert oracle.rel_frobenius(Mb, eb, Mg, eg) < 1e-6
+
+
+def test_three_slices_integers_and_top_binade_exact():
+    g = wl.rng(15)
+    X = (g.standard_normal((130, 130)) * np.exp(g.standard_normal((130, 130)))).astype(np.float32)
+    a, s = oracle.fixed_slices_n(X, 64, 3)
+    assert len(a) == 3
+    assert all(np.all(aj == np.rint(aj)) for aj in a)
+    assert np.all(np.abs(a[0]) <= 256) and np.all(np.abs(a[1]) <= 128) and np.all(np.abs(a[2]) <= 128)
+    # the first two slices are the two-slice split
+    b1, b2, t = oracle.fixed_slices(X, 64)
+    assert np.array_equal(a[0], b1) and np.array_equal(a[1], b2) and np.array_equal(s, t)
+    rec = np.ldexp(65536.0 * a[0] + 256.0 * a[1] + a[2], s - 24)
+    assert np.all(np.abs(rec - X) <= np.ldexp(1.0, s - 25))
+    # float32 entries in their block's top binade sit on the 2^(s-24) grid: exact
+    top = np.abs(X) >= np.ldexp(1.0, s - 1)
+    assert top.sum() >= 4 and np.array_equal(rec[top], X[top].astype(np.float64))
+
+
+def test_six_products_exact_on_sixteen_bit_grid():
+    # Entries on each block's 2^(s-16) grid have a third slice of zero, so the
+    # six products a_i b_j (i + j <= 2) cover every nonzero term: the emulated
+    # product is the exact product rounded once to float32 (a dropped a1 b1,
+    # a wrong slice weight or a transposed operand all break this).
+    g = wl.rng(16)
+    def grid16(X):
+        _, _, s = oracle.fixed_slices(X, 64)
+        return np.ldexp(np.rint(np.ldexp(X.astype(np.float64), 16 - s)), s - 16).astype(np.float32)
+    X = grid16((g.standard_normal((100, 100)) * np.exp(g.standard_normal((100, 100)))).astype(np.float32))
+    Y = grid16((g.standard_normal((100, 100)) * np.exp(g.standard_normal((100, 100)))).astype(np.float32))
+    a, _ = oracle.fixed_slices_n(X, 64, 3)
+    assert not np.any(a[2])
+    exact = (X.astype(np.float64) @ Y.astype(np.float64)).astype(np.float32)
+    assert np.array_equal(oracle._emu_product(X, Y, "bf16x6blk"), exact)
+    # the two-slice emulator drops a1 b1 there and differs
+    assert not np.array_equal(oracle._emu_product(X, Y, "bf16x3blk"), exact)
+
+
+def test_six_product_chain_at_float32_accuracy():
+    A = wl.gaussian(96, 2)
+    for n in (16, 1000):
+        M, e, _ = oracle.matpow_f64(A, n)
+        e6 = oracle.rel_frobenius(*oracle.emu_sqmul(A, n, "bf16x6blk"), M, e)
+        e3 = oracle.rel_frobenius(*oracle.emu_sqmul(A, n, "bf16x3blk"), M, e)
+        ef = oracle.rel_frobenius(*oracle.fp32_sqmul(A, n), M, e)
+        # 24-bit fixed point per block: float32-class, far below two slices
+        assert e6 < 3 * ef and e6 * 50 < e3
