@@ -4,8 +4,8 @@ Default workload (one "step"): a single N=512 float32 matrix with entries
 N(0, 1/N), seed 0, raised to every power n in {2, 16, 128, 1024} by binary
 square-and-multiply -- G(n) = {1, 4, 7, 10} products, 22 in all.  The metric
 is effective TFLOP/s = sum over the step of G(n) * 2 N^3 / time (the
-algorithmic count: the three bfloat16 products of the split path and the
-n-1 products of the naive method are not counted).
+algorithmic count: the three (bf16x3) or six (bf16x6) bfloat16 products of
+the split paths and the n-1 products of the naive method are not counted).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -36,6 +36,11 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 TRAFFIC = {
     # re-captured whenever the kernels change; empty until then
 }
+
+# bfloat16 tensor-core products per algorithmic product (roofline counting)
+# and the arithmetic each precision computes in
+PRODUCTS = {"fp32": 1.0, "bf16": 1.0, "bf16x3": 3.0, "bf16x6": 6.0}
+DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}
 
 WORKLOADS = {
     "single512": dict(N=512, ns=[2, 16, 128, 1024], gen="gaussian",
@@ -351,7 +356,7 @@ def run_ours(args, wk, world, rank, local):
 
     # ---- dominant kernel: per-launch CUDA-event timing on the launching stream
     plan.set_option(mpw.OPT_TIMING, 1)
-    kind = {"fp32": mpw.KERNEL_SIMT, "bf16": mpw.KERNEL_TC, "bf16x3": mpw.KERNEL_TC}[prec]
+    kind = mpw.KERNEL_SIMT if prec == "fp32" else mpw.KERNEL_TC
     if N <= 64:
         kind = mpw.KERNEL_TINY
     with torch.cuda.stream(stream):
@@ -362,12 +367,14 @@ def run_ours(args, wk, world, rank, local):
         torch.cuda.synchronize()
         kl, kms, kflop = plan.kernel_time(kind, reset=True)
     plan.set_option(mpw.OPT_TIMING, 0)
-    products = 3.0 if prec == "bf16x3" else 1.0
+    products = PRODUCTS[prec]
     if kind == mpw.KERNEL_TC:
         achieved = kflop * products / (kms * 1e-3) / 1e12
         peak = peaks["bf16_tflops"]
-        kname = ("tc_chain_kernel" if prec == "bf16x3" and 64 < N <= 1024 else
-                 "tc_fxb_kernel" if prec == "bf16x3" else "tc_gemm_kernel")
+        exact = prec in ("bf16x3", "bf16x6")
+        chain_max = 768 if prec == "bf16x6" else 1024
+        kname = ("tc_chain_kernel" if exact and 64 < N <= chain_max else
+                 "tc_fxb_kernel" if exact else "tc_gemm_kernel")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": kname, "peak_source": peak_src + " bf16 burst",
@@ -395,7 +402,7 @@ def run_ours(args, wk, world, rank, local):
         "metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[prec],
+        "vs_baseline": None, "dtype": DTYPE[prec],
         "data": "synthetic",
         "config": {"workload": wk["desc"], "precision": prec, "gemms_per_step":
                    sum(gemm_count(n) for n in ns), "l2": "flushed between timed steps (256 MB write)",
@@ -508,7 +515,7 @@ def run_batched(args, wk, world, rank, local):
         kl, kms, kflop = plan.kernel_time(kind, reset=True)
         tl, tms, tflop = plan.kernel_time(mpw.KERNEL_TINY, reset=True)
     plan.set_option(mpw.OPT_TIMING, 0)
-    products = 3.0 if args.precision == "bf16x3" else 1.0
+    products = PRODUCTS[args.precision]
     achieved = kflop * products / (kms * 1e-3) / 1e12 if kms else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
             "frac": achieved / peaks["bf16_tflops"], "traffic": None,
@@ -534,7 +541,7 @@ def run_batched(args, wk, world, rank, local):
     line = {"metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": wk["desc"], "precision": args.precision,
                        "matrices": len(Ns), "gemms_per_step": sum(gemm_count(n) for n in ns),
@@ -622,7 +629,7 @@ def run_serving(args, wk, world, rank, local):
     line = {"metric": "matpow serving req/s", "value": count / wall, "unit": "req/s", "n_gpus": world,
             "steps": 1, "warmup": 8, "ms_per_step": wall * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3"}[args.precision],
+            "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": wk["desc"], "precision": args.precision,
                        "offered_req_per_s": rate, "requests": count},
@@ -646,7 +653,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single512")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "bf16x3"], default="bf16x3")
+    ap.add_argument("--precision", choices=sorted(DTYPE), default="bf16x3")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

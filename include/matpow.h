@@ -54,8 +54,13 @@ typedef enum matpow_status {
 typedef enum matpow_precision {
   MATPOW_FP32_SIMT = 0, /* float32 fused multiply-add products on the CUDA cores */
   MATPOW_BF16 = 1,      /* one bfloat16 tensor-core product per term, float32 accumulation */
-  MATPOW_BF16X3 = 2     /* each operand split x = hi + lo into two bfloat16 parts;
-                           hi*hi + hi*lo + lo*hi tensor-core products, float32 accumulation */
+  MATPOW_BF16X3 = 2,    /* each operand split into two bfloat16 parts, three tensor-core
+                           products (hi*hi + hi*lo + lo*hi) with float32 accumulation; by
+                           default the parts are exact 8-bit integer slices of each 64 x 64
+                           block scaled by its power-of-two maximum (16-bit fixed point per
+                           block), see MATPOW_OPT_SPLIT */
+  MATPOW_BF16X6 = 3     /* three exact 8-bit slices per block (24-bit fixed point), six
+                           tensor-core products a_i * b_j (i + j <= 2): float32-class results */
 } matpow_precision;
 
 typedef struct matpow_plan_s* matpow_plan_t;

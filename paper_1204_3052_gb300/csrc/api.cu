@@ -75,9 +75,10 @@ size_t mp::matrix_bytes(int N, int fmt) {
       return align_up(e * 4, 1024);
     case FMT_BF16:
       return align_up(e * 2, 1024);
-    case FMT_FX2: {  // two bfloat16 slice planes, then the block exponents
+    case FMT_FX2:
+    case FMT_FX3: {  // two or three bfloat16 slice planes, then the block exponents
       size_t nb = ((size_t)N + 63) / 64;
-      return 2 * align_up(e * 2, 1024) + align_up(nb * nb * 4, 1024);
+      return fmt_slices(fmt) * align_up(e * 2, 1024) + align_up(nb * nb * 4, 1024);
     }
     default:  // two bfloat16 planes
       return 2 * align_up(e * 2, 1024);
@@ -97,6 +98,8 @@ int mp::float_fmt(matpow_precision p) {
       return FMT_BF16;
     case MATPOW_BF16X3:
       return FMT_FX2;
+    case MATPOW_BF16X6:
+      return FMT_FX3;
     default:
       return FMT_F32;
   }
@@ -131,7 +134,8 @@ extern "C" matpow_status matpow_plan(matpow_plan_t* out, int max_n, matpow_preci
   if (!out) return fail(nullptr, MATPOW_EINVAL, "matpow_plan: out is NULL");
   *out = nullptr;
   if (max_n < 1) return fail(nullptr, MATPOW_EINVAL, "matpow_plan: max_n must be >= 1");
-  if (precision != MATPOW_FP32_SIMT && precision != MATPOW_BF16 && precision != MATPOW_BF16X3)
+  if (precision != MATPOW_FP32_SIMT && precision != MATPOW_BF16 && precision != MATPOW_BF16X3 &&
+      precision != MATPOW_BF16X6)
     return fail(nullptr, MATPOW_EINVAL, "matpow_plan: unknown precision %d", (int)precision);
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -400,14 +404,14 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
   const int fmt = plan_float_fmt(p);
   const long long plane = plane_offset_elems(N, fmt);
   const int ld = ld_for(N, fmt);
-  const bool fx2 = fmt == FMT_FX2;
+  const bool fx2 = fmt_exact(fmt);
   std::vector<LevelOps> levels;
   build_schedule(n, &levels);
   int nslots = 2 + matpow_gemm_count(n);
   CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * nslots, s));
   if (fx2) {
     // slot 1 describes A itself (exponent 0): block slices, max|A|
-    CK(p, launch_prep_fxb(dA, N, p->buf[0], &p->scales[1], p->status, s));
+    CK(p, launch_prep_fxb(dA, N, fmt, p->buf[0], &p->scales[1], p->status, s));
     p->launches += 1;
   } else {
     CK(p, launch_absmax_f32(dA, N, &p->scales[0], p->status, s));

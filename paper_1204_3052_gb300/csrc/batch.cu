@@ -135,10 +135,12 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
     big.push_back(std::move(b));
   }
   matpow_status st;
-  const bool fx2 = fmt == FMT_FX2;
+  const bool fx2 = fmt_exact(fmt);
+  const int nsl = fmt_slices(fmt);
+  const int mpb = 2 * nsl;  // TMA descriptors per buffer
   if (tc && !fx2 && !big.empty())
     return fail(p, MATPOW_EUNSUPPORTED,
-                "matpow_batched: grouped tensor-core launches use the exact split (MATPOW_BF16X3)");
+                "matpow_batched: grouped tensor-core launches use the exact split (MATPOW_BF16X3 or MATPOW_BF16X6)");
   if ((st = grow(p, &p->batch.ws, &p->batch.ws_bytes, std::max<size_t>(ws_need, 1), false))) return st;
   size_t sc_bytes = sizeof(Scale) * std::max(slots, 1);
   if ((st = grow(p, (void**)&p->batch.scales, &p->batch.scale_cap, sc_bytes, false))) return st;
@@ -169,7 +171,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
         const Big& b = big[bi];
         if (L >= (int)b.levels.size()) continue;
         const int Ni = N[b.i];
-        if (tc && tc_group_bn(Ni) != bn) continue;
+        if (tc && tc_group_bn(Ni, nsl) != bn) continue;
         const bool final_level = L + 1 == (int)b.levels.size();
         const LevelOps& lv = b.levels[L];
         for (size_t k = 0; k < lv.ops.size(); ++k) {
@@ -193,9 +195,9 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
           if (tc) {
             d.bn = bn;
             d.tiles_n = (Ni + bn - 1) / bn;
-            d.map_x = 16 * (int)bi + 4 * op.xb;
-            d.map_y = 16 * (int)bi + 4 * op.yb;
-            d.map_c = 16 * (int)bi + 4 * (last ? op.xb : op.cb);
+            d.map_x = mpb * (4 * (int)bi + op.xb);
+            d.map_y = mpb * (4 * (int)bi + op.yb);
+            d.map_c = mpb * (4 * (int)bi + (last ? op.xb : op.cb));
             tiles += ((Ni + 127) / 128) * d.tiles_n;
           } else {
             d.tiles_n = (Ni + simt_tile_edge() - 1) / simt_tile_edge();
@@ -214,10 +216,10 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
     keys.reserve(4 * big.size());
     for (auto& b : big)
       for (int k = 0; k < 4; ++k) keys.push_back({(char*)p->batch.ws + b.off + k * b.mb, N[b.i]});
-    if (keys != p->batch.map_keys) {
-      p->batch.h_maps.resize(4 * keys.size());
+    if (keys != p->batch.map_keys || p->batch.h_maps.size() != mpb * keys.size()) {
+      p->batch.h_maps.resize(mpb * keys.size());
       for (size_t k = 0; k < keys.size(); ++k)
-        if (!tc_encode_buffer_maps(&p->batch.h_maps[4 * k], keys[k].first, keys[k].second))
+        if (!tc_encode_buffer_maps(&p->batch.h_maps[mpb * k], keys[k].first, keys[k].second, nsl))
           return fail(p, MATPOW_ECUDA, "matpow_batched: cuTensorMapEncodeTiled failed");
       const size_t mbytes = p->batch.h_maps.size() * sizeof(CUtensorMap);
       if ((st = grow(p, &p->batch.maps, &p->batch.maps_bytes, mbytes, false))) return st;

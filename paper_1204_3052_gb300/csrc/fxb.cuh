@@ -18,6 +18,12 @@
 // (the lagged power-of-two scale of the chain).  The a2*b2 term (2^-16
 // relative) is dropped.  The epilogue re-splits T by 64 x 64 blocks, so no
 // global maximum is needed before the next product can start.
+//
+// With three slices (MATPOW_BF16X6) a third one a3 = rint(256 * remainder)
+// extends the fixed point to 24 bits; six products a1b1 | a1b2 + a2b1 |
+// a1b3 + a2b2 + a3b1 fill three accumulators (the third sums to below
+// 64 * 81920 < 2^23 per k-block, still exact), and the dropped terms are
+// 2^-24 relative: float32-class results.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -33,9 +39,10 @@ constexpr int MAX_KB = 512;  // exponent table in shared memory: N <= 32768
 
 __host__ __device__ inline size_t align1k(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
-// Byte offset of the block-exponent table (int32, nb x nb) in a stored matrix.
-__host__ __device__ inline size_t bexp_offset(int N, int ld) {
-  return 2 * align1k((size_t)N * ld * 2);
+// Byte offset of the block-exponent table (int32, nb x nb) in a stored matrix
+// of NSL slice planes.
+__host__ __device__ inline size_t bexp_offset(int N, int ld, int NSL = 2) {
+  return (size_t)NSL * align1k((size_t)N * ld * 2);
 }
 __host__ __device__ inline int nblocks(int N) { return (N + BLK - 1) / BLK; }
 
@@ -61,6 +68,18 @@ __device__ __forceinline__ void slice(float v, int e, float* h, float* l) {
   const float u = mul_pow2(v, 8 - e);
   *h = rintf(u);
   *l = rintf((u - *h) * 256.f);
+}
+
+// NSL integer slices of v relative to block exponent e:
+//   u = v 2^(8-e); a0 = rint(u); a_k = rint(256 (previous remainder)).
+template <int NSL>
+__device__ __forceinline__ void slice_n(float v, int e, float (&a)[NSL]) {
+  float u = mul_pow2(v, 8 - e);
+#pragma unroll
+  for (int k = 0; k < NSL; ++k) {
+    a[k] = rintf(u);
+    u = (u - a[k]) * 256.f;
+  }
 }
 
 // Named barrier 1 over the NT epilogue threads (warps 4.. of the CTA).
@@ -151,13 +170,13 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
 //   room for 2 planes x (number of boxes) x 16 KB; box0: index of this
 //   warp's first box; c1, c2: the destination planes' tensor maps (box 64 x
 //   128); leader: the one thread that issues the stores; NT epilogue threads.
-template <int WC, int NT>
+template <int WC, int NT, int NSL = 2>
 __device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, int m0, int nw, int q,
                                                  int lane, int N, int box0, int nbox, uint8_t* stage,
-                                                 const CUtensorMap* c1, const CUtensorMap* c2,
-                                                 int* bexp, unsigned* maxbits, float* red,
-                                                 bool leader, int n0) {
+                                                 const CUtensorMap* const (&cmap)[NSL], int* bexp,
+                                                 unsigned* maxbits, float* red, bool leader, int n0) {
   constexpr int NG = WC / BLK;
+  constexpr int BOX = NSL * 16384;  // bytes of one 128 x 64 box in all planes
 #pragma unroll
   for (int g = 0; g < NG; ++g) {
     float m = 0.f;
@@ -179,33 +198,34 @@ __device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, in
       bexp[I * nb + J] = e;
       if (bm > 0.f) atomicMax(maxbits, __float_as_uint(bm));
     }
-    uint8_t* p1 = stage + (size_t)b * 32768 + r * 128;
-    uint8_t* p2 = p1 + 16384;
+    uint8_t* p0 = stage + (size_t)b * BOX + r * 128;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      uint32_t hw[4], lw[4];
+      uint32_t w[NSL][4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) {
-        float h0, l0, h1, l1;
-        slice(T[BLK * g + 8 * c + 2 * h], e, &h0, &l0);
-        slice(T[BLK * g + 8 * c + 2 * h + 1], e, &h1, &l1);
-        __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
-        __nv_bfloat162 lo = __floats2bfloat162_rn(l0, l1);
-        hw[h] = *reinterpret_cast<uint32_t*>(&hi);
-        lw[h] = *reinterpret_cast<uint32_t*>(&lo);
+        float x0[NSL], x1[NSL];
+        slice_n<NSL>(T[BLK * g + 8 * c + 2 * h], e, x0);
+        slice_n<NSL>(T[BLK * g + 8 * c + 2 * h + 1], e, x1);
+#pragma unroll
+        for (int k = 0; k < NSL; ++k) {
+          __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
+          w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+        }
       }
       const int pos = (c ^ (r & 7)) * 16;
-      *reinterpret_cast<uint4*>(p1 + pos) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-      *reinterpret_cast<uint4*>(p2 + pos) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+      for (int k = 0; k < NSL; ++k)
+        *reinterpret_cast<uint4*>(p0 + 16384 * k + pos) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
     }
   }
   ptx::fence_proxy_async_smem();  // generic smem writes -> visible to the TMA engine
   epi_bar<NT>();
   if (leader) {
     for (int b = 0; b < nbox; ++b) {
-      const uint32_t src = ptx::smem_u32(stage + (size_t)b * 32768);
-      ptx::tma_store_2d(c1, n0 + BLK * b, m0, src);
-      ptx::tma_store_2d(c2, n0 + BLK * b, m0, src + 16384);
+      const uint32_t src = ptx::smem_u32(stage + (size_t)b * BOX);
+#pragma unroll
+      for (int k = 0; k < NSL; ++k) ptx::tma_store_2d(cmap[k], n0 + BLK * b, m0, src + 16384 * k);
     }
     ptx::bulk_commit();
     ptx::bulk_wait_all();
@@ -214,17 +234,27 @@ __device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, in
   epi_bar<NT>();  // the stage and red may be reused
 }
 
-// Fold one finished k-block (main at TMEM column tq, cross at tq + cross_off)
-// into T with the block factors fac[g] (one per 64 columns).
-template <int BN>
+// Fold one finished k-block into T with the block factors fac[g] (one per 64
+// columns).  Accumulator k (0: main, 1: weight 2^-8, 2: weight 2^-16) sits at
+// TMEM column tq + k * acc_stride.
+template <int BN, int NSL = 2>
 __device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&fac)[BN / BLK],
-                                     uint32_t cross_off = BN) {
+                                     uint32_t acc_stride = BN) {
 #pragma unroll
   for (int c = 0; c < BN / 32; ++c) {
     uint32_t rm[32], rc[32];
     ptx::tmem_ld_32x32b_x32(tq + 32 * c, rm);
-    ptx::tmem_ld_32x32b_x32(tq + cross_off + 32 * c, rc);
-    ptx::tmem_ld_wait();
+    ptx::tmem_ld_32x32b_x32(tq + acc_stride + 32 * c, rc);
+    if (NSL == 3) {
+      uint32_t rd[32];
+      ptx::tmem_ld_32x32b_x32(tq + 2 * acc_stride + 32 * c, rd);
+      ptx::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        rc[j] = __float_as_uint(fmaf(__uint_as_float(rd[j]), 0.00390625f, __uint_as_float(rc[j])));
+    } else {
+      ptx::tmem_ld_wait();
+    }
     const float f = fac[c / 2];
 #pragma unroll
     for (int j = 0; j < 32; ++j)
@@ -236,6 +266,7 @@ __device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&
 // One 64 x 64 block (I, J) of a float32 matrix A (leading dimension N) split
 // into the stored format by a CTA of 256 threads: block exponent, slices,
 // matrix maximum, non-finite check.  red: 8 floats of shared scratch.
+template <int NSL = 2>
 __device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, int ld, int I, int J,
                                            __nv_bfloat16* a1p, long long plane, int* bexp,
                                            unsigned* maxbits, unsigned* status, float* red) {
@@ -265,32 +296,33 @@ __device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, i
   }
   if (r < N && c0 < ld) {
     __nv_bfloat16* p1 = a1p + (size_t)r * ld + c0;
-    __nv_bfloat16* p2 = p1 + plane;
     if (c0 + 16 <= ld) {
 #pragma unroll
       for (int g8 = 0; g8 < 2; ++g8) {
-        uint32_t hw[4], lw[4];
+        uint32_t w[NSL][4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
-          float h0, l0, h1, l1;
-          slice(v[8 * g8 + 2 * h], e, &h0, &l0);
-          slice(v[8 * g8 + 2 * h + 1], e, &h1, &l1);
-          __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
-          __nv_bfloat162 lo = __floats2bfloat162_rn(l0, l1);
-          hw[h] = *reinterpret_cast<uint32_t*>(&hi);
-          lw[h] = *reinterpret_cast<uint32_t*>(&lo);
+          float x0[NSL], x1[NSL];
+          slice_n<NSL>(v[8 * g8 + 2 * h], e, x0);
+          slice_n<NSL>(v[8 * g8 + 2 * h + 1], e, x1);
+#pragma unroll
+          for (int k = 0; k < NSL; ++k) {
+            __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
+            w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+          }
         }
-        *reinterpret_cast<uint4*>(p1 + 8 * g8) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(p2 + 8 * g8) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+        for (int k = 0; k < NSL; ++k)
+          *reinterpret_cast<uint4*>(p1 + k * plane + 8 * g8) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
       }
     } else {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         if (c0 + j < ld) {
-          float h, l;
-          slice(v[j], e, &h, &l);
-          p1[j] = __float2bfloat16_rn(h);
-          p2[j] = __float2bfloat16_rn(l);
+          float x[NSL];
+          slice_n<NSL>(v[j], e, x);
+#pragma unroll
+          for (int k = 0; k < NSL; ++k) p1[k * plane + j] = __float2bfloat16_rn(x[k]);
         }
       }
     }

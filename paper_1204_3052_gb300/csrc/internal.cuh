@@ -35,7 +35,11 @@ enum Fmt : int {
   FMT_U32 = 4,     // mod-p residues as uint32, leading dimension roundup(N, 4)
   FMT_FX2 = 5,     // exact block-scaled split: integer slices a1, a2 (two bfloat16
                    // planes) and an int32 exponent per 64 x 64 block; ld roundup(N, 8)
+  FMT_FX3 = 6,     // the same with three slices a1, a2, a3
 };
+
+inline __host__ __device__ int fmt_slices(int fmt) { return fmt == FMT_FX3 ? 3 : 2; }
+inline __host__ __device__ bool fmt_exact(int fmt) { return fmt == FMT_FX2 || fmt == FMT_FX3; }
 
 // Where a product's result goes.
 enum OutMode : int {
@@ -170,10 +174,10 @@ struct PrepDesc {
   int kind;           // 0: absmax/convert, 1: identity (n = 0), 2: copy (n = 1)
   int pad_;
 };
-// Float32 A (leading dimension N) -> the block-scaled exact split (FMT_FX2)
-// at dst; max|A| folds into slot->maxbits.  One CTA per 64 x 64 block.
-cudaError_t launch_prep_fxb(const float* A, int N, void* dst, Scale* slot, unsigned* status,
-                            cudaStream_t s);
+// Float32 A (leading dimension N) -> the block-scaled exact split (FMT_FX2 or
+// FMT_FX3) at dst; max|A| folds into slot->maxbits.  One CTA per 64 x 64 block.
+cudaError_t launch_prep_fxb(const float* A, int N, int fmt, void* dst, Scale* slot,
+                            unsigned* status, cudaStream_t s);
 // Block-scaled split of many matrices (PrepDesc kind 0: nb x nb CTAs each;
 // kinds 1, 2: identity / copy into the user's output).
 cudaError_t launch_prep_fxb_group(const PrepDesc* d, int count, int blocks, Scale* scales,

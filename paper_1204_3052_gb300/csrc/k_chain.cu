@@ -38,17 +38,20 @@ namespace chain {
 constexpr int BM = 128, BK = 64, THREADS = 256, CHUNK_KB = 4;
 constexpr int MAX_LEVELS = 64;
 constexpr uint64_t WAIT_NS = 2000000000ull;
-constexpr int SMEM_RING = 192 * 1024;
-template <int BN>
+template <int BN, int NSL>
 struct Cfg {
   static constexpr int NG = BN / fxb::BLK;
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = SMEM_RING / STAGE_BYTES;
+  static constexpr int STAGE_BYTES = NSL * (A_BYTES + B_BYTES);
+  static constexpr int RING = NSL == 3 ? 216 * 1024 : 192 * 1024;
+  static constexpr int STAGES = RING / STAGE_BYTES;
   static constexpr int KB_MAX = 16;  // N <= 1024
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256 + (2 + NG) * KB_MAX * 4 + 64;
-  static constexpr int TMEM_COLS = 4 * BN;
+  static constexpr int TMEM_USED = 2 * NSL * BN;  // NSL accumulators x 2 buffers
+  static constexpr int TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
+  static_assert(TMEM_USED <= 512, "TMEM");
+  static_assert(NSL * 16384 * NG <= STAGES * STAGE_BYTES, "epilogue staging fits the ring");
 };
 struct Op {
   signed char xb, yb, cb, last;
@@ -57,9 +60,9 @@ struct Op {
 }  // namespace chain
 
 struct ChainParams {
-  CUtensorMap amap[4][2];  // buffer b as the A operand: slices a1, a2 (box 64 x 128)
-  CUtensorMap bmap[4][2];  // buffer b as the B operand: slices a1, a2 (box 64 x 64)
-  void* slices[4];         // slice a1 plane of buffer b (a2 at + plane elements)
+  CUtensorMap amap[4][3];  // buffer b as the A operand: slice planes (box 64 x 128)
+  CUtensorMap bmap[4][3];  // buffer b as the B operand: slice planes (box 64 x 64)
+  void* slices[4];         // first slice plane of buffer b (the next at + plane elements)
   int* bexp[4];            // block exponents of buffer b
   long long plane;
   const float* A;
@@ -110,11 +113,11 @@ __device__ __forceinline__ bool grid_sync(unsigned* gbar, unsigned target, unsig
   return !*cta_abort;
 }
 
-template <int BN>
+template <int BN, int NSL>
 __global__ void __launch_bounds__(chain::THREADS, 1)
     tc_chain_kernel(const __grid_constant__ ChainParams P) {
   using namespace chain;
-  using C = Cfg<BN>;
+  using C = Cfg<BN, NSL>;
   constexpr int STAGES = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -158,12 +161,11 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
     ptx::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
-    for (int b = 0; b < 4; ++b) {
-      ptx::prefetch_tmap(&P.amap[b][0]);
-      ptx::prefetch_tmap(&P.amap[b][1]);
-      ptx::prefetch_tmap(&P.bmap[b][0]);
-      ptx::prefetch_tmap(&P.bmap[b][1]);
-    }
+    for (int b = 0; b < 4; ++b)
+      for (int k = 0; k < NSL; ++k) {
+        ptx::prefetch_tmap(&P.amap[b][k]);
+        ptx::prefetch_tmap(&P.bmap[b][k]);
+      }
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   {
     const int nb = fxb::nblocks(N);
     for (int b = blockIdx.x; b < nb * nb; b += G)
-      fxb::prep_block(P.A, N, ld, b / nb, b % nb, (__nv_bfloat16*)P.slices[0], P.plane, P.bexp[0],
+      fxb::prep_block<NSL>(P.A, N, ld, b / nb, b % nb, (__nv_bfloat16*)P.slices[0], P.plane, P.bexp[0],
                       &P.scales[1].maxbits, P.status, red);
     fence_proxy_async_global();
   }
@@ -198,10 +200,6 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
     if (has) {
       if (warp == 0) {
         if (lane == 0) {
-          const CUtensorMap* am1 = &P.amap[op.xb][0];
-          const CUtensorMap* am2 = &P.amap[op.xb][1];
-          const CUtensorMap* bm1 = &P.bmap[op.yb][0];
-          const CUtensorMap* bm2 = &P.bmap[op.yb][1];
           for (int kb = 0; kb < KB; ++kb) {
             const int g = kb_base + kb;
             const int s = g % STAGES;
@@ -214,14 +212,16 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
             ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
             const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
             const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
-            ptx::tma_load_2d(base, am1, kx, m0, fb);
-            ptx::tma_load_2d(base + C::A_BYTES, am2, kx, m0, fb);
-            const uint32_t bbase = base + 2 * C::A_BYTES;
 #pragma unroll
-            for (int c = 0; c < BN / 64; ++c) {
-              ptx::tma_load_2d(bbase + c * 8192, bm1, n0 + 64 * c, kx, fb);
-              ptx::tma_load_2d(bbase + C::B_BYTES + c * 8192, bm2, n0 + 64 * c, kx, fb);
-            }
+            for (int k = 0; k < NSL; ++k)
+              ptx::tma_load_2d(base + k * C::A_BYTES, &P.amap[op.xb][k], kx, m0, fb);
+            const uint32_t bbase = base + NSL * C::A_BYTES;
+#pragma unroll
+            for (int c = 0; c < BN / 64; ++c)
+#pragma unroll
+              for (int k = 0; k < NSL; ++k)
+                ptx::tma_load_2d(bbase + k * C::B_BYTES + c * 8192, &P.bmap[op.yb][k], n0 + 64 * c, kx,
+                                 fb);
           }
         }
       } else if (warp == 1) {
@@ -230,8 +230,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
           for (int kb = 0; kb < KB; ++kb) {
             const int g = kb_base + kb;
             const int buf = g & 1;
-            const uint32_t t_main = tmem + (uint32_t)(buf * 2 * BN);
-            const uint32_t t_cross = t_main + BN;
+            const uint32_t t0 = tmem + (uint32_t)(buf * NSL * BN);
             if (!ptx::mbar_wait(accempty0 + 8 * buf, ((g >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
               *abort_flag = 1;
               break;
@@ -242,20 +241,26 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
               break;
             }
             ptx::tc_fence_after();
-            const uint32_t a1 = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-            const uint32_t a2 = a1 + C::A_BYTES;
-            const uint32_t b1 = a1 + 2 * C::A_BYTES;
-            const uint32_t b2 = b1 + C::B_BYTES;
+            const uint32_t a0 = ptx::smem_u32(smem + s * C::STAGE_BYTES);
+            const uint32_t b0 = a0 + NSL * C::A_BYTES;
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
-              const uint64_t ad1 = ptx::smem_desc(a1 + 32 * k, 16, 1024);
-              const uint64_t ad2 = ptx::smem_desc(a2 + 32 * k, 16, 1024);
-              const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
-              const uint64_t bd2 = ptx::smem_desc(b2 + 2048 * k, 8192, 1024);
+              uint64_t ad[NSL], bd[NSL];
+#pragma unroll
+              for (int i = 0; i < NSL; ++i) {
+                ad[i] = ptx::smem_desc(a0 + i * C::A_BYTES + 32 * k, 16, 1024);
+                bd[i] = ptx::smem_desc(b0 + i * C::B_BYTES + 2048 * k, 8192, 1024);
+              }
               const uint32_t acc = k == 0 ? 0u : 1u;
-              ptx::mma_f16(t_main, ad1, bd1, idesc, acc);
-              ptx::mma_f16(t_cross, ad1, bd2, idesc, acc);
-              ptx::mma_f16(t_cross, ad2, bd1, idesc, 1);
+              // accumulator w collects the products a_i b_j with i + j = w
+              ptx::mma_f16(t0, ad[0], bd[0], idesc, acc);
+              ptx::mma_f16(t0 + BN, ad[0], bd[1], idesc, acc);
+              ptx::mma_f16(t0 + BN, ad[1], bd[0], idesc, 1);
+              if (NSL == 3) {
+                ptx::mma_f16(t0 + 2 * BN, ad[0], bd[NSL - 1], idesc, acc);
+                ptx::mma_f16(t0 + 2 * BN, ad[1], bd[1], idesc, 1);
+                ptx::mma_f16(t0 + 2 * BN, ad[NSL - 1], bd[0], idesc, 1);
+              }
             }
             ptx::mma_commit(empty0 + 8 * s);
             ptx::mma_commit(accfull0 + 8 * buf);
@@ -290,7 +295,8 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
 #pragma unroll
           for (int gg = 0; gg < NG; ++gg)
             fac[gg] = fxb::pow2f(eA[h * KB + kr] + eB[kr * NG + gg] - 16 - sx - sy);
-          fxb::fold<BN>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN), fac);
+          fxb::fold<BN, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN), fac,
+                             BN);
           ptx::tc_fence_before();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
@@ -314,10 +320,14 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
           }
         } else {
           if (t == 0 && q == 0 && lane == 0) P.scales[op.sc].E = Ec;
-          if (ok)  // the ring is idle here: all k-blocks of this tile were consumed
-            fxb::store_slices_tma<BN, 128>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
-                                           &P.amap[op.cb][0], &P.amap[op.cb][1], P.bexp[op.cb],
-                                           &P.scales[op.sc].maxbits, ered, q == 0 && lane == 0, n0);
+          if (ok) {  // the ring is idle here: all k-blocks of this tile were consumed
+            const CUtensorMap* cm[NSL];
+#pragma unroll
+            for (int k = 0; k < NSL; ++k) cm[k] = &P.amap[op.cb][k];
+            fxb::store_slices_tma<BN, 128, NSL>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
+                                                cm, P.bexp[op.cb], &P.scales[op.sc].maxbits, ered,
+                                                q == 0 && lane == 0, n0);
+          }
           fence_proxy_async_global();
         }
       }
@@ -354,18 +364,25 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
 // host side
 
 cudaError_t tc_chain_init(matpow_plan_s*) {
-  cudaError_t e = cudaFuncSetAttribute(tc_chain_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       chain::Cfg<64>::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc_chain_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              chain::Cfg<128>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_chain_kernel<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       chain::Cfg<64, 2>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_chain_kernel<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             chain::Cfg<128, 2>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_chain_kernel<64, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             chain::Cfg<64, 3>::SMEM);
+  return e;
 }
 
 matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
                            int64_t* dLog2, cudaStream_t s, bool* used) {
   *used = false;
-  if (!p->use_chain || plan_float_fmt(p) != FMT_FX2 || n < 2 || N <= p->tiny_max || N > 1024)
-    return MATPOW_OK;
+  const int fmt = plan_float_fmt(p);
+  if (!p->use_chain || !fmt_exact(fmt) || n < 2 || N <= p->tiny_max || N > 1024) return MATPOW_OK;
+  const int nsl = fmt_slices(fmt);
+  // three accumulators per buffer fit TMEM only at 64-wide tiles
+  if (nsl == 3 && N > 768) return MATPOW_OK;
   const int BN = N <= 768 ? 64 : 128;
   std::vector<LevelOps> levels;
   build_schedule(n, &levels);
@@ -379,18 +396,16 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
 
   static thread_local ChainParams P;  // ~4 KB: kept off the stack
   memset(&P, 0, sizeof P);
-  const int fmt = FMT_FX2;
   const int ld = ld_for(N, fmt);
   const long long plane = plane_offset_elems(N, fmt);
   for (int b = 0; b < 4; ++b) {
     const char* base = (const char*)p->buf[b];
     P.slices[b] = p->buf[b];
-    P.bexp[b] = (int*)((char*)p->buf[b] + fxb::bexp_offset(N, ld_for(N, FMT_FX2)));
-    if (!tc_encode_bf16_map(&P.amap[b][0], base, N, ld, 64, chain::BM) ||
-        !tc_encode_bf16_map(&P.amap[b][1], base + plane * 2, N, ld, 64, chain::BM) ||
-        !tc_encode_bf16_map(&P.bmap[b][0], base, N, ld, 64, 64) ||
-        !tc_encode_bf16_map(&P.bmap[b][1], base + plane * 2, N, ld, 64, 64))
-      return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", N);
+    P.bexp[b] = (int*)((char*)p->buf[b] + fxb::bexp_offset(N, ld, nsl));
+    for (int k = 0; k < nsl; ++k)
+      if (!tc_encode_bf16_map(&P.amap[b][k], base + k * plane * 2, N, ld, 64, chain::BM) ||
+          !tc_encode_bf16_map(&P.bmap[b][k], base + k * plane * 2, N, ld, 64, 64))
+        return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", N);
   }
   P.plane = plane;
   P.A = dA;
@@ -425,12 +440,15 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
   void* args[] = {&P};
   cudaEvent_t ev;
   timed_begin(p, s, &ev);
-  if (BN == 64)
-    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<64>, dim3(G), dim3(chain::THREADS),
-                                    args, chain::Cfg<64>::SMEM, s);
+  if (nsl == 3)
+    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<64, 3>, dim3(G), dim3(chain::THREADS),
+                                    args, chain::Cfg<64, 3>::SMEM, s);
+  else if (BN == 64)
+    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<64, 2>, dim3(G), dim3(chain::THREADS),
+                                    args, chain::Cfg<64, 2>::SMEM, s);
   else
-    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<128>, dim3(G), dim3(chain::THREADS),
-                                    args, chain::Cfg<128>::SMEM, s);
+    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<128, 2>, dim3(G), dim3(chain::THREADS),
+                                    args, chain::Cfg<128, 2>::SMEM, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaLaunchCooperativeKernel(tc_chain_kernel)");
   timed_end(p, s, ev, MATPOW_KERNEL_TC, 2.0 * N * (double)N * N * matpow_gemm_count(n));
   p->launches++;

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 // next product's operand planes.
 
 namespace fx {
-template <int BN>
+template <int BN, int NSL>
 struct Cfg {
   // epilogue warps: 4 lane quadrants x CS column slices of WC columns each
   static constexpr int CS = BN / 64;
@@ -272,24 +272,28 @@ struct Cfg {
   static constexpr int NG = BN / fxb::BLK;
   static constexpr int A_BYTES = tc::BM * tc::BK * 2;
   static constexpr int B_BYTES = BN * tc::BK * 2;
-  static constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = tc::SMEM_RING / STAGE_BYTES;
+  static constexpr int STAGE_BYTES = NSL * (A_BYTES + B_BYTES);
+  static constexpr int RING = NSL == 3 ? 216 * 1024 : tc::SMEM_RING;
+  static constexpr int STAGES = RING / STAGE_BYTES;
   static constexpr int EXP_BYTES = (2 + NG) * fxb::MAX_KB * 4;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256 + EXP_BYTES + 64;
-  static constexpr int TMEM_COLS = 4 * BN;  // 2 buffers x (main, cross)
+  static constexpr int ACC = NSL;                 // accumulators per k-block buffer
+  static constexpr int TMEM_USED = 2 * ACC * BN;  // 2 buffers
+  static constexpr int TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
+  static_assert(TMEM_USED <= 512, "TMEM");
 };
 }  // namespace fx
 
-// One CTA = one output tile t of product d; ax0/ax1 (A operand, slices a1/a2
-// of X) and by0/by1 (B operand, slices of Y) are TMA descriptors in param or
-// global memory.
-template <int BN>
-__device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensorMap* ax0,
-                                        const CUtensorMap* ax1, const CUtensorMap* by0,
-                                        const CUtensorMap* by1, const CUtensorMap* cx0,
-                                        const CUtensorMap* cx1, Scale* scales, unsigned* status) {
+// One CTA = one output tile t of product d.  ax[k] / by[k]: slice k of X as
+// the A operand / of Y as the B operand; cx[k]: slice k of C as TMA store
+// target (param or global memory).  NSL = 2 (BF16X3) or 3 (BF16X6).
+template <int BN, int NSL>
+__device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensorMap* const (&ax)[NSL],
+                                        const CUtensorMap* const (&by)[NSL],
+                                        const CUtensorMap* const (&cx)[NSL], Scale* scales,
+                                        unsigned* status) {
   using namespace tc;
-  using C = fx::Cfg<BN>;
+  using C = fx::Cfg<BN, NSL>;
   constexpr int EW = C::EW, WC = C::WC;
   constexpr int STAGES = C::STAGES;
   constexpr int NG = C::NG;
@@ -314,7 +318,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
   const int m0 = tm * BM, n0 = tn * BN;
   const int N = d.N;
   const int KB = (N + BK - 1) / BK;
-  const size_t boff = fxb::bexp_offset(N, d.ld);
+  const size_t boff = fxb::bexp_offset(N, d.ld, NSL);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -334,10 +338,11 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
     ptx::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
-    ptx::prefetch_tmap(ax0);
-    ptx::prefetch_tmap(ax1);
-    ptx::prefetch_tmap(by0);
-    ptx::prefetch_tmap(by1);
+#pragma unroll
+    for (int k = 0; k < NSL; ++k) {
+      ptx::prefetch_tmap(ax[k]);
+      ptx::prefetch_tmap(by[k]);
+    }
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -358,14 +363,14 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
         const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
-        ptx::tma_load_2d(base, ax0, kx, m0, fb);
-        ptx::tma_load_2d(base + C::A_BYTES, ax1, kx, m0, fb);
-        const uint32_t bbase = base + 2 * C::A_BYTES;
 #pragma unroll
-        for (int c = 0; c < BN / 64; ++c) {
-          ptx::tma_load_2d(bbase + c * 8192, by0, n0 + 64 * c, kx, fb);
-          ptx::tma_load_2d(bbase + C::B_BYTES + c * 8192, by1, n0 + 64 * c, kx, fb);
-        }
+        for (int k = 0; k < NSL; ++k) ptx::tma_load_2d(base + k * C::A_BYTES, ax[k], kx, m0, fb);
+        const uint32_t bbase = base + NSL * C::A_BYTES;
+#pragma unroll
+        for (int c = 0; c < BN / 64; ++c)
+#pragma unroll
+          for (int k = 0; k < NSL; ++k)
+            ptx::tma_load_2d(bbase + k * C::B_BYTES + c * 8192, by[k], n0 + 64 * c, kx, fb);
         ++issued;
       }
       for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
@@ -378,8 +383,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
       for (int kb = 0; kb < KB; ++kb) {
         const int buf = kb & 1;
-        const uint32_t t_main = tmem + (uint32_t)(buf * 2 * BN);
-        const uint32_t t_cross = t_main + BN;
+        const uint32_t t0 = tmem + (uint32_t)(buf * C::ACC * BN);
         if (!ptx::mbar_wait(accempty0 + 8 * buf, ((kb >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
           *abort_flag = 1;
           break;
@@ -390,20 +394,26 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t a1 = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-        const uint32_t a2 = a1 + C::A_BYTES;
-        const uint32_t b1 = a1 + 2 * C::A_BYTES;
-        const uint32_t b2 = b1 + C::B_BYTES;
+        const uint32_t a0 = ptx::smem_u32(smem + s * C::STAGE_BYTES);
+        const uint32_t b0 = a0 + NSL * C::A_BYTES;
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ad1 = ptx::smem_desc(a1 + 32 * k, 16, 1024);
-          const uint64_t ad2 = ptx::smem_desc(a2 + 32 * k, 16, 1024);
-          const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
-          const uint64_t bd2 = ptx::smem_desc(b2 + 2048 * k, 8192, 1024);
+          uint64_t ad[NSL], bd[NSL];
+#pragma unroll
+          for (int i = 0; i < NSL; ++i) {
+            ad[i] = ptx::smem_desc(a0 + i * C::A_BYTES + 32 * k, 16, 1024);
+            bd[i] = ptx::smem_desc(b0 + i * C::B_BYTES + 2048 * k, 8192, 1024);
+          }
           const uint32_t acc = k == 0 ? 0u : 1u;
-          ptx::mma_f16(t_main, ad1, bd1, idesc, acc);
-          ptx::mma_f16(t_cross, ad1, bd2, idesc, acc);
-          ptx::mma_f16(t_cross, ad2, bd1, idesc, 1);
+          // accumulator w collects the products a_i b_j with i + j = w
+          ptx::mma_f16(t0, ad[0], bd[0], idesc, acc);
+          ptx::mma_f16(t0 + BN, ad[0], bd[1], idesc, acc);
+          ptx::mma_f16(t0 + BN, ad[1], bd[0], idesc, 1);
+          if (NSL == 3) {
+            ptx::mma_f16(t0 + 2 * BN, ad[0], bd[NSL - 1], idesc, acc);
+            ptx::mma_f16(t0 + 2 * BN, ad[1], bd[1], idesc, 1);
+            ptx::mma_f16(t0 + 2 * BN, ad[NSL - 1], bd[0], idesc, 1);
+          }
         }
         ptx::mma_commit(empty0 + 8 * s);
         ptx::mma_commit(accfull0 + 8 * buf);
@@ -447,7 +457,8 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
 #pragma unroll
       for (int g = 0; g < WC / 64; ++g)
         fac[g] = fxb::pow2f(eA[h * KB + kr] + eB[kr * NG + cs * (WC / 64) + g] - 16 - sx - sy);
-      fxb::fold<WC>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 2 * BN + cs * WC), fac, BN);
+      fxb::fold<WC, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * C::ACC * BN + cs * WC),
+                         fac, BN);
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
@@ -461,9 +472,9 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
     if (d.mode == OUT_INTERNAL) {
       if (t == 0 && e == 0 && lane == 0) scales[d.sc].E = Ec;
       if (ok)  // every epilogue warp reaches the named barriers inside; the ring is idle
-        fxb::store_slices_tma<WC, 32 * EW>(T, 32 * q + lane, m0, nw, q, lane, N, cs * (WC / 64),
-                                           BN / 64, smem, cx0, cx1, (int*)((char*)d.C + boff),
-                                           &scales[d.sc].maxbits, red, e == 0 && lane == 0, n0);
+        fxb::store_slices_tma<WC, 32 * EW, NSL>(T, 32 * q + lane, m0, nw, q, lane, N, cs * (WC / 64),
+                                                BN / 64, smem, cx, (int*)((char*)d.C + boff),
+                                                &scales[d.sc].maxbits, red, e == 0 && lane == 0, n0);
     } else if (ok) {
       if (t == 0 && e == 0 && lane == 0 && d.mode == OUT_USER_MANT && d.out_log2) *d.out_log2 = Ec;
       if (row < N) {
@@ -486,22 +497,30 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
 }
 
-template <int BN>
-__global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
+template <int BN, int NSL>
+__global__ void __launch_bounds__(fx::Cfg<BN, NSL>::THREADS, 1)
     tc_fxb_kernel(const __grid_constant__ TcPairParams P, Scale* scales, unsigned* status) {
   int t = blockIdx.x;
   const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
   if (which) t -= P.tiles0;
   const TcProblem& pr = P.p[which];
-  fxb_cta<BN>(pr.d, t, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], &pr.cx[0], &pr.cx[1], scales,
-              status);
+  const CUtensorMap* ax[NSL];
+  const CUtensorMap* by[NSL];
+  const CUtensorMap* cx[NSL];
+#pragma unroll
+  for (int k = 0; k < NSL; ++k) {
+    ax[k] = &pr.ax[k];
+    by[k] = &pr.by[k];
+    cx[k] = &pr.cx[k];
+  }
+  fxb_cta<BN, NSL>(pr.d, t, ax, by, cx, scales, status);
 }
 
 // Grouped launch: products from a device table (any number of matrices),
-// TMA descriptors from a device table (4 per stored buffer: A-role a1, a2,
-// B-role a1, a2 at index map_x / map_y).
-template <int BN>
-__global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
+// TMA descriptors from a device table: 2 NSL per stored buffer (A-role slices
+// 0..NSL-1, then B-role slices), at index map_x / map_y / map_c.
+template <int BN, int NSL>
+__global__ void __launch_bounds__(fx::Cfg<BN, NSL>::THREADS, 1)
     tc_fxb_group_kernel(const GemmDesc* __restrict__ descs, int count,
                         const CUtensorMap* __restrict__ maps, Scale* scales, unsigned* status) {
   const int tb = blockIdx.x;
@@ -511,12 +530,21 @@ __global__ void __launch_bounds__(fx::Cfg<BN>::THREADS, 1)
     if (descs[mid].tile_begin <= tb) lo = mid; else hi = mid - 1;
   }
   const GemmDesc d = descs[lo];
-  fxb_cta<BN>(d, tb - d.tile_begin, &maps[d.map_x], &maps[d.map_x + 1], &maps[d.map_y + 2],
-              &maps[d.map_y + 3], &maps[d.map_c], &maps[d.map_c + 1], scales, status);
+  const CUtensorMap* ax[NSL];
+  const CUtensorMap* by[NSL];
+  const CUtensorMap* cx[NSL];
+#pragma unroll
+  for (int k = 0; k < NSL; ++k) {
+    ax[k] = &maps[d.map_x + k];
+    by[k] = &maps[d.map_y + NSL + k];
+    cx[k] = &maps[d.map_c + k];
+  }
+  fxb_cta<BN, NSL>(d, tb - d.tile_begin, ax, by, cx, scales, status);
 }
 
 // A (float32, leading dimension N) -> block-scaled stored format, one CTA per
 // 64 x 64 block.
+template <int NSL>
 __global__ void __launch_bounds__(256) prep_fxb_kernel(const float* __restrict__ A, int N, int ld,
                                                        __nv_bfloat16* dst, long long plane,
                                                        int* bexp, unsigned* maxbits,
@@ -524,7 +552,7 @@ __global__ void __launch_bounds__(256) prep_fxb_kernel(const float* __restrict__
   __shared__ float red[8];
   const int nb = fxb::nblocks(N);
   const int I = blockIdx.x / nb, J = blockIdx.x - (blockIdx.x / nb) * nb;
-  fxb::prep_block(A, N, ld, I, J, dst, plane, bexp, maxbits, status, red);
+  fxb::prep_block<NSL>(A, N, ld, I, J, dst, plane, bexp, maxbits, status, red);
 }
 
 // ---------------------------------------------------------------------------
@@ -556,35 +584,35 @@ cudaError_t tc_init(matpow_plan_s*) {
   if ((e = set_attr<64, 2>()) != cudaSuccess) return e;
   if ((e = set_attr<128, 2>()) != cudaSuccess) return e;
   if ((e = set_attr<256, 2>()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(tc_fxb_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                fx::Cfg<64>::SMEM)) != cudaSuccess)
+#define MP_FXB_ATTR(K, BN, NSL)                                                                  \
+  if ((e = cudaFuncSetAttribute(K<BN, NSL>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                fx::Cfg<BN, NSL>::SMEM)) != cudaSuccess)                          \
     return e;
-  if ((e = cudaFuncSetAttribute(tc_fxb_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                fx::Cfg<128>::SMEM)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(tc_fxb_group_kernel<64>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, fx::Cfg<64>::SMEM)) !=
-      cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(tc_fxb_group_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              fx::Cfg<128>::SMEM);
+  MP_FXB_ATTR(tc_fxb_kernel, 64, 2)
+  MP_FXB_ATTR(tc_fxb_kernel, 128, 2)
+  MP_FXB_ATTR(tc_fxb_kernel, 64, 3)
+  MP_FXB_ATTR(tc_fxb_group_kernel, 64, 2)
+  MP_FXB_ATTR(tc_fxb_group_kernel, 128, 2)
+  MP_FXB_ATTR(tc_fxb_group_kernel, 64, 3)
+#undef MP_FXB_ATTR
+  return cudaSuccess;
 }
 
 void tc_free(matpow_plan_s*) {}
 
 static int pick_bn(matpow_plan_s* p, int N) {
-  const bool fx2 = plan_float_fmt(p) == FMT_FX2;
+  const int fmt = plan_float_fmt(p);
+  if (fmt == FMT_FX3) return 64;  // three accumulators x 2 buffers fit TMEM at 64 columns
+  const bool fx2 = fmt == FMT_FX2;
   if (p->tile_override == 64 || p->tile_override == 128 || p->tile_override == 256) {
     if (fx2 && p->tile_override == 256) return 128;
     return p->tile_override;
   }
-  if (N <= 1024) return 64;
-  if (N <= 3072 || fx2) return 128;
-  return 256;
+  return tc_group_bn(N) == 64 ? 64 : (N <= 3072 || fx2) ? 128 : 256;
 }
 
 matpow_status tc_fill_desc(matpow_plan_s* p, GemmDesc* d, int* ntiles) {
-  if (plan_float_fmt(p) == FMT_FX2 && d->N > fxb::MAX_KB * fxb::BLK)
+  if (fmt_exact(plan_float_fmt(p)) && d->N > fxb::MAX_KB * fxb::BLK)
     return fail(p, MATPOW_EUNSUPPORTED, "exact split: N=%d above %d", d->N, fxb::MAX_KB * fxb::BLK);
   d->bn = pick_bn(p, d->N);
   d->tiles_n = (d->N + d->bn - 1) / d->bn;
@@ -603,24 +631,19 @@ bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box
   return r == CUDA_SUCCESS;
 }
 
-static bool fill_problem(TcProblem* tp, const GemmDesc& d, int PL) {
+static bool fill_problem(TcProblem* tp, const GemmDesc& d, int NPL) {
   tp->d = d;
-  const size_t lo = (size_t)d.plane * 2;
-  if (!tc_encode_bf16_map(&tp->ax[0], d.X, d.N, d.ld, 64, tc::BM)) return false;
-  if (!tc_encode_bf16_map(&tp->by[0], d.Y, d.N, d.ld, 64, 64)) return false;
-  if (PL == 2) {
-    if (!tc_encode_bf16_map(&tp->ax[1], (const char*)d.X + lo, d.N, d.ld, 64, tc::BM)) return false;
-    if (!tc_encode_bf16_map(&tp->by[1], (const char*)d.Y + lo, d.N, d.ld, 64, 64)) return false;
-  } else {
-    tp->ax[1] = tp->ax[0];
-    tp->by[1] = tp->by[0];
-  }
-  if (d.C) {  // TMA store targets of the output planes
-    if (!tc_encode_bf16_map(&tp->cx[0], d.C, d.N, d.ld, 64, tc::BM)) return false;
-    if (!tc_encode_bf16_map(&tp->cx[1], (const char*)d.C + lo, d.N, d.ld, 64, tc::BM)) return false;
-  } else {
-    tp->cx[0] = tp->ax[0];
-    tp->cx[1] = tp->ax[1];
+  const size_t ps = (size_t)d.plane * 2;  // bytes between planes
+  for (int k = 0; k < 3; ++k) {
+    const int kk = k < NPL ? k : NPL - 1;
+    if (!tc_encode_bf16_map(&tp->ax[k], (const char*)d.X + kk * ps, d.N, d.ld, 64, tc::BM)) return false;
+    if (!tc_encode_bf16_map(&tp->by[k], (const char*)d.Y + kk * ps, d.N, d.ld, 64, 64)) return false;
+    if (d.C) {  // TMA store targets of the output planes
+      if (!tc_encode_bf16_map(&tp->cx[k], (const char*)d.C + kk * ps, d.N, d.ld, 64, tc::BM))
+        return false;
+    } else {
+      tp->cx[k] = tp->ax[k];
+    }
   }
   return true;
 }
@@ -635,21 +658,25 @@ static cudaError_t launch(const TcPairParams& P, int grid, Scale* scales, unsign
 matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s) {
   const int fmt = plan_float_fmt(p);
   const int PL = fmt == FMT_BF16 ? 1 : 2;
-  TcPairParams P;
+  static thread_local TcPairParams P;  // ~3 KB: kept off the stack
   memset(&P, 0, sizeof P);
   P.count = g.count;
   for (int i = 0; i < g.count; ++i)
-    if (!fill_problem(&P.p[i], g.d[i], PL))
+    if (!fill_problem(&P.p[i], g.d[i], fmt == FMT_FX3 ? 3 : PL))
       return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", g.d[i].N);
   P.tiles0 = g.count > 1 ? g.d[1].tile_begin : g.tiles_total;
   const int bn = g.d[0].bn;
   cudaError_t e;
-  if (fmt == FMT_FX2) {
+  if (fmt == FMT_FX3) {
+    tc_fxb_kernel<64, 3><<<g.tiles_total, fx::Cfg<64, 3>::THREADS, fx::Cfg<64, 3>::SMEM, s>>>(
+        P, p->scales, p->status);
+    e = cudaGetLastError();
+  } else if (fmt == FMT_FX2) {
     if (bn == 64)
-      tc_fxb_kernel<64><<<g.tiles_total, fx::Cfg<64>::THREADS, fx::Cfg<64>::SMEM, s>>>(P, p->scales,
-                                                                                      p->status);
+      tc_fxb_kernel<64, 2><<<g.tiles_total, fx::Cfg<64, 2>::THREADS, fx::Cfg<64, 2>::SMEM, s>>>(
+          P, p->scales, p->status);
     else
-      tc_fxb_kernel<128><<<g.tiles_total, fx::Cfg<128>::THREADS, fx::Cfg<128>::SMEM, s>>>(
+      tc_fxb_kernel<128, 2><<<g.tiles_total, fx::Cfg<128, 2>::THREADS, fx::Cfg<128, 2>::SMEM, s>>>(
           P, p->scales, p->status);
     e = cudaGetLastError();
   } else if (PL == 2)
@@ -670,13 +697,16 @@ matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int cou
 }
 
 cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
-                             int bn, Scale* scales, unsigned* status, cudaStream_t s) {
+                             int bn, int nsl, Scale* scales, unsigned* status, cudaStream_t s) {
   const CUtensorMap* maps = (const CUtensorMap*)d_maps;
-  if (bn == 64)
-    tc_fxb_group_kernel<64><<<tiles, fx::Cfg<64>::THREADS, fx::Cfg<64>::SMEM, s>>>(d_descs, count, maps,
-                                                                                  scales, status);
+  if (nsl == 3)
+    tc_fxb_group_kernel<64, 3><<<tiles, fx::Cfg<64, 3>::THREADS, fx::Cfg<64, 3>::SMEM, s>>>(
+        d_descs, count, maps, scales, status);
+  else if (bn == 64)
+    tc_fxb_group_kernel<64, 2><<<tiles, fx::Cfg<64, 2>::THREADS, fx::Cfg<64, 2>::SMEM, s>>>(
+        d_descs, count, maps, scales, status);
   else
-    tc_fxb_group_kernel<128><<<tiles, fx::Cfg<128>::THREADS, fx::Cfg<128>::SMEM, s>>>(
+    tc_fxb_group_kernel<128, 2><<<tiles, fx::Cfg<128, 2>::THREADS, fx::Cfg<128, 2>::SMEM, s>>>(
         d_descs, count, maps, scales, status);
   return cudaGetLastError();
 }
@@ -684,23 +714,26 @@ cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, cons
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                                  const void* d_maps, int bn, Scale* scales, unsigned* status,
                                  cudaStream_t s) {
-  if (plan_float_fmt(p) != FMT_FX2)
+  const int fmt = plan_float_fmt(p);
+  if (!fmt_exact(fmt))
     return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches need the exact split");
-  cudaError_t e = launch_fxb_group(d_descs, count, tiles, d_maps, bn, scales, status, s);
+  cudaError_t e = launch_fxb_group(d_descs, count, tiles, d_maps, bn, fmt_slices(fmt), scales, status, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "tc_fxb_group_kernel launch");
   return MATPOW_OK;
 }
 
-int tc_group_bn(int N) { return N <= 1024 ? 64 : 128; }
+int tc_group_bn(int N, int nsl) { return (N <= 1024 || nsl == 3) ? 64 : 128; }
 
-bool tc_encode_buffer_maps(CUtensorMap* m4, const void* base, int N) {
-  const int ld = ld_for(N, FMT_FX2);
+bool tc_encode_buffer_maps(CUtensorMap* m, const void* base, int N, int nsl) {
+  const int fmt = nsl == 3 ? FMT_FX3 : FMT_FX2;
+  const int ld = ld_for(N, fmt);
   const char* b = (const char*)base;
-  const size_t lo = (size_t)plane_offset_elems(N, FMT_FX2) * 2;
-  return tc_encode_bf16_map(&m4[0], b, N, ld, 64, tc::BM) &&
-         tc_encode_bf16_map(&m4[1], b + lo, N, ld, 64, tc::BM) &&
-         tc_encode_bf16_map(&m4[2], b, N, ld, 64, 64) &&
-         tc_encode_bf16_map(&m4[3], b + lo, N, ld, 64, 64);
+  const size_t ps = (size_t)plane_offset_elems(N, fmt) * 2;
+  for (int k = 0; k < nsl; ++k)
+    if (!tc_encode_bf16_map(&m[k], b + k * ps, N, ld, 64, tc::BM) ||
+        !tc_encode_bf16_map(&m[nsl + k], b + k * ps, N, ld, 64, 64))
+      return false;
+  return true;
 }
 
 }  // namespace mp
@@ -731,12 +764,17 @@ __global__ void __launch_bounds__(256) prep_fxb_group_kernel(const PrepDesc* __r
     }
     return;
   }
-  const int ld = ld_for(N, FMT_FX2);
+  const int ld = ld_for(N, d.fmt);
   const int nb = fxb::nblocks(N);
   __nv_bfloat16* a1p = (__nv_bfloat16*)d.dst;
-  int* bexp = (int*)((char*)d.dst + fxb::bexp_offset(N, ld));
-  fxb::prep_block(d.A, N, ld, b / nb, b % nb, a1p, d.plane, bexp, &scales[d.slot_stored].maxbits,
-                  status, red);
+  const int nsl = fmt_slices(d.fmt);
+  int* bexp = (int*)((char*)d.dst + fxb::bexp_offset(N, ld, nsl));
+  if (nsl == 3)
+    fxb::prep_block<3>(d.A, N, ld, b / nb, b % nb, a1p, d.plane, bexp, &scales[d.slot_stored].maxbits,
+                       status, red);
+  else
+    fxb::prep_block<2>(d.A, N, ld, b / nb, b % nb, a1p, d.plane, bexp, &scales[d.slot_stored].maxbits,
+                       status, red);
 }
 
 cudaError_t launch_prep_fxb_group(const PrepDesc* d, int count, int blocks, Scale* scales,
@@ -745,14 +783,19 @@ cudaError_t launch_prep_fxb_group(const PrepDesc* d, int count, int blocks, Scal
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep_fxb(const float* A, int N, void* dst, Scale* slot, unsigned* status,
-                            cudaStream_t s) {
-  const int ld = ld_for(N, FMT_FX2);
+cudaError_t launch_prep_fxb(const float* A, int N, int fmt, void* dst, Scale* slot,
+                            unsigned* status, cudaStream_t s) {
+  const int ld = ld_for(N, fmt);
   const int nb = fxb::nblocks(N);
-  const long long plane = plane_offset_elems(N, FMT_FX2);
-  int* bexp = (int*)((char*)dst + fxb::bexp_offset(N, ld));
-  prep_fxb_kernel<<<nb * nb, 256, 0, s>>>(A, N, ld, (__nv_bfloat16*)dst, plane, bexp, &slot->maxbits,
-                                          status);
+  const long long plane = plane_offset_elems(N, fmt);
+  const int nsl = fmt_slices(fmt);
+  int* bexp = (int*)((char*)dst + fxb::bexp_offset(N, ld, nsl));
+  if (nsl == 3)
+    prep_fxb_kernel<3><<<nb * nb, 256, 0, s>>>(A, N, ld, (__nv_bfloat16*)dst, plane, bexp,
+                                               &slot->maxbits, status);
+  else
+    prep_fxb_kernel<2><<<nb * nb, 256, 0, s>>>(A, N, ld, (__nv_bfloat16*)dst, plane, bexp,
+                                               &slot->maxbits, status);
   return cudaGetLastError();
 }
 }  // namespace mp

@@ -146,10 +146,10 @@ matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int cou
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                                  const void* d_maps, int bn, Scale* scales, unsigned* status,
                                  cudaStream_t s);
-int tc_group_bn(int N);  // tile width of grouped launches for order N
+int tc_group_bn(int N, int nsl = 2);  // tile width of grouped launches for order N
 // Plan-free grouped exact-split launch (descriptor and TMA tables on the device).
 cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
-                             int bn, Scale* scales, unsigned* status, cudaStream_t s);
-// The four TMA descriptors of one block-scaled buffer (A-role a1, a2, B-role a1, a2).
-bool tc_encode_buffer_maps(CUtensorMap* m4, const void* base, int N);
+                             int bn, int nsl, Scale* scales, unsigned* status, cudaStream_t s);
+// The 2 nsl TMA descriptors of one block-scaled buffer (A-role slices, then B-role).
+bool tc_encode_buffer_maps(CUtensorMap* m, const void* base, int N, int nsl);
 }  // namespace mp

@@ -102,8 +102,8 @@ struct Req {
 
 struct matpow_server_s {
   matpow_server_desc desc{};
-  int fmt = FMT_F32;  // FMT_FX2: float levels on the tensor cores (exact split)
-  CUtensorMap* d_maps = nullptr;  // 16 TMA descriptors per slot chunk (4 buffers x 4)
+  int fmt = FMT_F32;  // FMT_FX2 / FMT_FX3: float levels on the tensor cores (exact split)
+  CUtensorMap* d_maps = nullptr;  // 24 TMA descriptors per slot chunk (4 buffers x 2 x 3)
   CUtensorMap* h_maps = nullptr;  // pinned host copy
   cudaStream_t stream = nullptr;
   void* arena_mem = nullptr;
@@ -262,12 +262,13 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
         d.ld = ld_for(r.N, s->fmt);
         d.plane = plane_offset_elems(r.N, s->fmt);
         d.mode = last ? (r.dLog2Scale ? OUT_USER_MANT : OUT_USER_VALUE) : OUT_INTERNAL;
-        if (s->fmt == FMT_FX2) {
-          d.bn = tc_group_bn(r.N);
+        if (fmt_exact(s->fmt)) {
+          const int mpb = 2 * fmt_slices(s->fmt);
+          d.bn = tc_group_bn(r.N, fmt_slices(s->fmt));
           d.tiles_n = (r.N + d.bn - 1) / d.bn;
-          d.map_x = 16 * q->chunk + 4 * op.xb;
-          d.map_y = 16 * q->chunk + 4 * op.yb;
-          d.map_c = 16 * q->chunk + 4 * (last ? op.xb : op.cb);
+          d.map_x = 24 * q->chunk + mpb * op.xb;
+          d.map_y = 24 * q->chunk + mpb * op.yb;
+          d.map_c = 24 * q->chunk + mpb * (last ? op.xb : op.cb);
           const int nt = ((r.N + 127) / 128) * d.tiles_n;
           if (d.bn == 64) {
             d.tile_begin = tiles_f;
@@ -304,7 +305,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   int prep_blocks = 0;
   for (auto& d : prep) {
     size_t e = (size_t)d.N * d.N;
-    if (s->fmt == FMT_FX2 && d.kind == 0) {
+    if (fmt_exact(s->fmt) && d.kind == 0) {
       const size_t nb = ((size_t)d.N + 63) / 64;
       d.blocks = (int)(nb * nb);
     } else {
@@ -342,7 +343,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   }
   if (!prep.empty()) {
     const PrepDesc* pd = (const PrepDesc*)(dd + o_p);
-    if (s->fmt == FMT_FX2) {
+    if (fmt_exact(s->fmt)) {
       e = launch_prep_fxb_group(pd, (int)prep.size(), prep_blocks, s->scales, st0, s->stream);
     } else {
       e = launch_prep_absmax_group(pd, (int)prep.size(), prep_blocks, s->scales, st0, s->stream);
@@ -362,9 +363,9 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p prep");
   }
   if (!gf.empty()) {
-    if (s->fmt == FMT_FX2)
+    if (fmt_exact(s->fmt))
       e = launch_fxb_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->d_maps, 64,
-                           s->scales, st0, s->stream);
+                           fmt_slices(s->fmt), s->scales, st0, s->stream);
     else
       e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->scales, st0,
                             s->stream);
@@ -372,7 +373,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   }
   if (!gw.empty()) {
     e = launch_fxb_group((const GemmDesc*)(dd + o_w), (int)gw.size(), tiles_w, s->d_maps, 128,
-                         s->scales, st0, s->stream);
+                         fmt_slices(s->fmt), s->scales, st0, s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
   }
   if (!gm.empty()) {
@@ -407,16 +408,18 @@ static void scheduler(matpow_server_s* s) {
         q->state = 1;
         q->tiny = q->r.kind == 0 && q->r.N <= tiny_max_supported() && q->r.n >= 2;
         if (q->r.n >= 2) build_schedule(q->r.n, &q->levels);
-        if (s->fmt == FMT_FX2 && q->r.kind == 0 && !q->tiny && q->r.n >= 2) {
+        if (fmt_exact(s->fmt) && q->r.kind == 0 && !q->tiny && q->r.n >= 2) {
           // TMA descriptors of the request's four buffers, uploaded in stream
           // order before its first product
-          CUtensorMap* hm = s->h_maps + 16 * q->chunk;
+          const int nsl = fmt_slices(s->fmt);
+          CUtensorMap* hm = s->h_maps + 24 * q->chunk;
           const size_t mb = fp / 4;
           bool okm = true;
           for (int k = 0; k < 4 && okm; ++k)
-            okm = tc_encode_buffer_maps(hm + 4 * k, (char*)s->arena_mem + off + k * mb, q->r.N);
+            okm = tc_encode_buffer_maps(hm + 2 * nsl * k, (char*)s->arena_mem + off + k * mb, q->r.N,
+                                        nsl);
           if (okm)
-            okm = cudaMemcpyAsync(s->d_maps + 16 * q->chunk, hm, 16 * sizeof(CUtensorMap),
+            okm = cudaMemcpyAsync(s->d_maps + 24 * q->chunk, hm, 24 * sizeof(CUtensorMap),
                                   cudaMemcpyHostToDevice, s->stream) == cudaSuccess;
           if (!okm) {
             q->state = 3;
@@ -512,7 +515,8 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   *out = nullptr;
   if (d->max_n < 1 || d->max_inflight < 1 || d->max_queue < 1 || d->hbm_budget_bytes == 0)
     return fail(nullptr, MATPOW_EINVAL, "matpow_server_create: bad descriptor");
-  if (d->precision != MATPOW_FP32_SIMT && d->precision != MATPOW_BF16 && d->precision != MATPOW_BF16X3)
+  if (d->precision != MATPOW_FP32_SIMT && d->precision != MATPOW_BF16 && d->precision != MATPOW_BF16X3 &&
+      d->precision != MATPOW_BF16X6)
     return fail(nullptr, MATPOW_EINVAL, "matpow_server_create: unknown precision");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev)
@@ -526,7 +530,7 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   s->desc = *d;
   // grouped float levels: the exact-split tensor-core kernels for MATPOW_BF16X3,
   // the float32 SIMT kernels otherwise
-  s->fmt = d->precision == MATPOW_BF16X3 ? FMT_FX2 : FMT_F32;
+  s->fmt = d->precision == MATPOW_BF16X3 ? FMT_FX2 : d->precision == MATPOW_BF16X6 ? FMT_FX3 : FMT_F32;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(d->device);
@@ -537,10 +541,10 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(unsigned) * s->h_status.size());
   if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(unsigned) * s->h_status.size());
   if (e == cudaSuccess) e = tiny_attrs();
-  if (e == cudaSuccess && s->fmt == FMT_FX2) {
+  if (e == cudaSuccess && fmt_exact(s->fmt)) {
     e = tc_init(nullptr);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_maps, sizeof(CUtensorMap) * 16 * d->max_inflight);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->h_maps, sizeof(CUtensorMap) * 16 * d->max_inflight);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_maps, sizeof(CUtensorMap) * 24 * d->max_inflight);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_maps, sizeof(CUtensorMap) * 24 * d->max_inflight);
   }
   cudaSetDevice(prev);
   if (e != cudaSuccess) {

@@ -8,9 +8,9 @@
 namespace mp {
 
 struct TcProblem {
-  CUtensorMap ax[2];  // X as the A operand: its two planes (box 64 x 128)
-  CUtensorMap by[2];  // Y as the B operand: its two planes (box 64 x 64)
-  CUtensorMap cx[2];  // C's two planes as TMA store targets (box 64 x 128)
+  CUtensorMap ax[3];  // X as the A operand: its planes (box 64 x 128)
+  CUtensorMap by[3];  // Y as the B operand: its planes (box 64 x 64)
+  CUtensorMap cx[3];  // C's planes as TMA store targets (box 64 x 128)
   GemmDesc d;
 };
 

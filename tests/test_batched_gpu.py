@@ -10,7 +10,7 @@ from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-EMU = {"bf16x3": "bf16x3blk"}
+EMU = {"bf16x3": "bf16x3blk", "bf16x6": "bf16x6blk"}
 
 
 def floor_for(prec, A, n, M, e):
@@ -22,7 +22,7 @@ def floor_for(prec, A, n, M, e):
     return f
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6"])
 def test_uneven_batch_matches_oracle_and_single_calls(prec):
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
@@ -51,14 +51,16 @@ def test_uneven_batch_matches_oracle_and_single_calls(prec):
     plan.close()
 
 
-def test_batch_with_wide_tiles():
-    # orders above 1024 run in the 128-column grouped launch, next to 64-column ones
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_batch_with_wide_tiles(prec):
+    # orders above 1024 run in the 128-column grouped launch, next to 64-column
+    # ones (three slices keep 64 columns at every order)
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
     Ns = [1100, 300, 1030, 96, 40]
     ns = [13, 77, 2, 1000, 9]
     As = [wl.gaussian(N, 7 + i) for i, N in enumerate(Ns)]
-    plan = mpw.Plan(1100, "bf16x3")
+    plan = mpw.Plan(1100, prec)
     dAs = [to_dev(a) for a in As]
     lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
     outs = plan.batched(dAs, ns, log2=lg)
@@ -70,5 +72,5 @@ def test_batch_with_wide_tiles():
         if Ns[i] <= 300:
             M, e, _ = oracle.matpow_f64(A, n)
             err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
-            assert err <= gate(n, floor_for("bf16x3", A, n, M, e))
+            assert err <= gate(n, floor_for(prec, A, n, M, e))
     plan.close()

@@ -15,13 +15,14 @@ from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-PRECS = ["fp32", "bf16x3", "bf16"]
+PRECS = ["fp32", "bf16x3", "bf16x6", "bf16"]
 # largest Fibonacci power whose partial products are exact in each path:
-# float32 holds F < 2^24; the exact split holds every integer below 2^16
-# (two 8-bit slices of a matrix whose maximum is below 2^16) and sums them
-# exactly; a bfloat16 operand holds integers < 2^8.
-FIB_EXACT = {"fp32": 34, "bf16x3": 23, "bf16": 12}
-EMU = {"bf16": "bf16", "bf16x3": "bf16x3blk"}
+# float32 holds F < 2^24; the two-slice exact split holds every integer below
+# 2^16 (two 8-bit slices of a matrix whose maximum is below 2^16) and sums
+# them exactly; three slices extend that to 24 bits; a bfloat16 operand holds
+# integers < 2^8.
+FIB_EXACT = {"fp32": 34, "bf16x3": 23, "bf16x6": 34, "bf16": 12}
+EMU = {"bf16": "bf16", "bf16x3": "bf16x3blk", "bf16x6": "bf16x6blk"}
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +50,7 @@ def floor_rel(A, n, M, e, prec="fp32"):
     """Error of a CPU run of the same method at the path's precision class."""
     Mf, ef = oracle.fp32_sqmul(A, n)
     f = oracle.rel_frobenius(Mf, ef, M, e)
-    if prec in ("bf16", "bf16x3") and A.shape[0] > 64:  # N <= 64 runs the float32 chain
+    if prec in EMU and A.shape[0] > 64:  # N <= 64 runs the float32 chain
         Me, ee = oracle.emu_sqmul(A, n, EMU[prec])
         f = max(f, oracle.rel_frobenius(Me, ee, M, e))
     return f
@@ -260,11 +261,12 @@ def test_bf16x3_beats_bf16_and_meets_float_bound():
     assert errs["bf16x3"] * 20 < errs["bf16"]
 
 
-def test_exact_split_accumulates_integers_exactly():
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_exact_split_accumulates_integers_exactly(prec):
     # small-integer matrices: the slices are exact and every 256-deep partial
     # sum is an integer below 2^24, so A^2 must equal the integer product
     from paper_1204_3052_gb300 import matpow as mpw
-    plan = mpw.Plan(1024, "bf16x3")
+    plan = mpw.Plan(1024, prec)
     g = wl.rng(21)
     for N in (96, 512, 1000):
         A = g.integers(-15, 16, size=(N, N)).astype(np.float32)
@@ -288,15 +290,16 @@ def test_floating_split_option(n):
     plan.close()
 
 
-@pytest.mark.parametrize("N", [65, 100, 200, 512, 700, 768, 769, 1000, 1024])
-def test_whole_chain_kernel_equals_level_path_bitwise(N):
+@pytest.mark.parametrize("prec,N", [("bf16x3", N) for N in (65, 100, 200, 512, 700, 768, 769, 1000, 1024)]
+                         + [("bf16x6", N) for N in (65, 200, 512, 768, 1000)])
+def test_whole_chain_kernel_equals_level_path_bitwise(prec, N):
     # the cooperative whole-chain kernel and the level-by-level kernels do the
     # same exact-split arithmetic on the same float32 values, so they agree bit
     # for bit; both are also checked against the oracle
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
-    chain = mpw.Plan(1024, "bf16x3")
-    level = mpw.Plan(1024, "bf16x3")
+    chain = mpw.Plan(1024, prec)
+    level = mpw.Plan(1024, prec)
     level.set_option(mpw.OPT_CHAIN, 0)
     A = wl.gaussian(N, N + 7)
     dA = to_dev(A)
@@ -309,12 +312,32 @@ def test_whole_chain_kernel_equals_level_path_bitwise(N):
         assert torch.equal(oc, ol), (N, n)
         M, e, _ = oracle.matpow_f64(A, n)
         err = oracle.rel_frobenius(oc.cpu().numpy(), int(lc.item()), M, e)
-        assert err <= gate(n, floor_rel(A, n, M, e, "bf16x3")), (N, n, err)
+        assert err <= gate(n, floor_rel(A, n, M, e, prec)), (N, n, err)
     # value mode through the chain kernel
     ov = chain.f32(dA, 5)
     assert chain.sync() == 0
     M, e, _ = oracle.matpow_f64(A, 5)
     want = np.ldexp(M, e)
-    assert np.linalg.norm(ov.cpu().numpy() - want) / np.linalg.norm(want) <= gate(5, floor_rel(A, 5, M, e, "bf16x3"))
+    assert np.linalg.norm(ov.cpu().numpy() - want) / np.linalg.norm(want) <= gate(5, floor_rel(A, 5, M, e, prec))
     chain.close()
     level.close()
+
+
+def test_bf16x6_at_float32_accuracy():
+    # three slices (24-bit fixed point per 64 x 64 block): within a small
+    # factor of a float32 run of the same chain, far below two slices
+    from paper_1204_3052_gb300 import matpow as mpw
+    errs = {}
+    for N, n in ((512, 16), (300, 1000), (1000, 7)):
+        A = wl.gaussian(N, N + 1)
+        M, e, _ = oracle.matpow_f64(A, n)
+        Mf, ef = oracle.fp32_sqmul(A, n)
+        ef32 = oracle.rel_frobenius(Mf, ef, M, e)
+        for prec in ("bf16x3", "bf16x6"):
+            plan = mpw.Plan(1024, prec)
+            got, ge = run(plan, A, n)
+            errs[prec] = oracle.rel_frobenius(got, ge, M, e)
+            plan.close()
+        print(N, n, errs, ef32)
+        assert errs["bf16x6"] <= 4 * ef32, (N, n, errs, ef32)
+        assert errs["bf16x6"] * 30 < errs["bf16x3"], (N, n, errs)

@@ -31,7 +31,7 @@ def make_requests(count, seed):
     return reqs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6"])
 def test_mixed_stream_matches_isolated_runs(prec):
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
@@ -71,8 +71,8 @@ def test_mixed_stream_matches_isolated_runs(prec):
             M, e, _ = oracle.matpow_f64(A, n)
             Mf, ef = oracle.fp32_sqmul(A, n)
             floor = oracle.rel_frobenius(Mf, ef, M, e)
-            if prec == "bf16x3" and N > 64:
-                Me, ee = oracle.emu_sqmul(A, n, "bf16x3blk")
+            if prec in ("bf16x3", "bf16x6") and N > 64:
+                Me, ee = oracle.emu_sqmul(A, n, prec + "blk")
                 floor = max(floor, oracle.rel_frobenius(Me, ee, M, e))
             err = oracle.rel_frobenius(out.cpu().numpy(), int(lg.item()), M, e)
             assert err <= gate(n, floor), (N, n, err)
