@@ -6,6 +6,10 @@ square-and-multiply -- G(n) = {1, 4, 7, 10} products, 22 in all.  The metric
 is effective TFLOP/s = sum over the step of G(n) * 2 N^3 / time (the
 algorithmic count: the three (bf16x3) or six (bf16x6) bfloat16 products of
 the split paths and the n-1 products of the naive method are not counted).
+The default precision is the three-slice exact split (bf16x6), the cheapest
+tensor-core path whose errors stay within 2e-5 * ceil(log2 n) on these
+inputs; the line also carries the plain FP32 SIMT path timed on the same
+workload.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -43,20 +47,20 @@ PRODUCTS = {"fp32": 1.0, "bf16": 1.0, "bf16x3": 3.0, "bf16x6": 6.0}
 DTYPE = {"fp32": "f32", "bf16": "bf16", "bf16x3": "bf16x3", "bf16x6": "bf16x6"}
 
 WORKLOADS = {
-    "single512": dict(N=512, ns=[2, 16, 128, 1024], gen="gaussian",
+    "single512": dict(N=512, ns=[2, 16, 128, 1024], gen="gaussian", prec="bf16x6",
                       desc="single N=512 N(0,1/N) float32, n in {2,16,128,1024}, seed 0"),
-    "stoch64": dict(N=64, ns=[100], gen="stochastic",
+    "stoch64": dict(N=64, ns=[100], gen="stochastic", prec="fp32",
                     desc="single N=64 exact row-stochastic float32, n=100, seed 0"),
-    "large8192": dict(N=8192, ns=[2 ** 20], gen="stochastic",
+    "large8192": dict(N=8192, ns=[2 ** 20], gen="stochastic", prec="bf16x3",
                       desc="single N=8192 exact row-stochastic float32, n=2^20, seed 0"),
-    "batched4096": dict(kind="batched", count=4096, n_max=4096, N=256, ns=[],
+    "batched4096": dict(kind="batched", count=4096, n_max=4096, N=256, ns=[], prec="bf16x6",
                         desc="batched: 4096 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
                              "n log-uniform in [1,4096], seed 0; one grouped launch per level"),
-    "serving": dict(kind="serving", count=2000, N=2048, ns=[],
+    "serving": dict(kind="serving", count=2000, N=2048, ns=[], prec="bf16x6",
                     desc="serving: 2000 Poisson-arrival requests, N log-uniform [8,2048], n log-uniform "
                          "[1,2^30], 90% float / 10% mod 65521, seed 0"),
     # one product at N=4096 (operands 64 MB each, beyond L2): profiling case
-    "probe4096": dict(N=4096, ns=[2], gen="stochastic",
+    "probe4096": dict(N=4096, ns=[2], gen="stochastic", prec="bf16x3",
                       desc="single N=4096 exact row-stochastic float32, n=2 (one product), seed 0"),
 }
 
@@ -214,6 +218,7 @@ def cpu_sample_list(items, budget_s):
         k += 1
     dt = time.perf_counter() - t0
     return {"value": done / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "items_per_s": k / dt,
             "sample": "oracle on the first %d items of the workload (%.1f s)" % (k, dt)}
 
 
@@ -228,30 +233,125 @@ def reference_items(wk):
             yield wl.request_matrix(r), r.n, (r.p if r.kind else 0)
 
 
+def config_for(args, wk, world):
+    """The `config` object of a bench line, identical for both arms."""
+    from paper_1204_3052_gb300 import workloads as wl
+    cfg = {"workload": wk["desc"], "precision": args.precision}
+    if wk.get("kind") == "batched":
+        bd = wl.batched_draw(count=wk["count"], seed=0, n_max=wk["n_max"])
+        cfg.update(matrices=wk["count"], gemms_per_step=int(sum(gemm_count(int(n)) for n in bd.ns)),
+                   l2="flushed between timed steps (256 MB write)")
+    elif wk.get("kind") == "serving":
+        cfg.update(offered_req_per_s=args.serving_rate, requests=wk["count"])
+    else:
+        cfg.update(gemms_per_step=sum(gemm_count(n) for n in wk["ns"]),
+                   l2="flushed between timed steps (256 MB write)",
+                   parallelism="replicas" if world > 1 else "single")
+    return cfg
+
+
 def run_reference(args, wk, world, rank):
     if rank != 0:
         return
     res = []
     cb = None
+    serving = wk.get("kind") == "serving"
     for _ in range(max(args.steps, 1)):
         if wk.get("kind") in ("batched", "serving"):
             cb = cpu_sample_list(reference_items(wk), args.ref_budget)
         else:
             cb = cpu_sample(wk, budget_s=args.ref_budget)
-        res.append(cb["value"])
+        res.append(cb["items_per_s"] if serving else cb["value"])
     value = statistics.median(res)
     cb["value"] = value
-    line = {"metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s",
+    metric, unit = ("matpow serving req/s", "req/s") if serving else ("matpow effective TFLOP/s", "TFLOP/s")
+    cb["unit"] = unit
+    line = {"metric": metric, "value": value, "unit": unit,
             "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wk["desc"]}, "cpu_baseline": cb,
-            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+            "config": config_for(args, wk, world), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ---------------------------------------------------------------------------- GPU timing
+
+def stated_tolerance(n: int) -> float:
+    """Relative Frobenius bound for float32-class results: 2e-5 * ceil(log2 n)
+    (an exact copy, 1e-7, for n = 1)."""
+    return 1e-7 if n <= 1 else 2e-5 * math.ceil(math.log2(n))
+
+
+def errors_of(wk, A_host, ns, outs, lgs):
+    """Error of each power against the oracle (float64 square-and-multiply), or
+    for large stochastic powers against the closed form 1 pi^T on 64 sampled
+    rows plus the largest row-sum deviation; with the stated-error verdict."""
+    import oracle
+    N = wk["N"]
+    errs = {}
+    met = True
+    for i, n in enumerate(ns):
+        Mg = outs[i].cpu().numpy().astype(np.float64)
+        lg = int(lgs[i].item())
+        if N > 1024:
+            if wk["gen"] == "stochastic" and n >= 2 ** 10:
+                pi = oracle.stationary(A_host)
+                Vg = np.ldexp(Mg, lg)
+                rows = np.random.default_rng(0).choice(N, 64, replace=False)
+                want = np.tile(pi, (64, 1))
+                errs[str(n)] = float(np.linalg.norm(Vg[rows] - want) / np.linalg.norm(want))
+                errs["max_rowsum_dev"] = float(np.max(np.abs(Vg.sum(axis=1) - 1.0)))
+                met = met and errs[str(n)] <= stated_tolerance(n)
+            continue
+        M, e, _ = oracle.matpow_f64(A_host, n)
+        errs[str(n)] = oracle.rel_frobenius(Mg, lg, M, e)
+        met = met and errs[str(n)] <= stated_tolerance(n)
+    if errs:
+        errs["within_2e-5_ceil_log2_n"] = bool(met)
+    return errs
+
+
+def fp32_compare(args, wk, A, A_host, flush, stream, value):
+    """Time the plain FP32 SIMT path on the same workload (same L2 flush and
+    event timing, fewer steps) and report its value, errors and the ratio."""
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    N, ns = wk["N"], wk["ns"]
+    plan = mpw.Plan(N, "fp32", device=A.device.index)
+    outs = [torch.empty_like(A) for _ in ns]
+    lgs = torch.zeros(len(ns), dtype=torch.int64, device=A.device)
+    steps = max(1, min(args.steps, 3 if N > 2048 else 10))
+
+    def step():
+        for i, n in enumerate(ns):
+            st = mpw.matpow_f32(plan.h, A, N, n, outs[i], lgs[i:i + 1], stream)
+            if st != 0:
+                mpw._check(st, plan.h)
+
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        step()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        plan.check(stream)
+    flop_step = sum(gemm_count(n) for n in ns) * 2.0 * N ** 3
+    v = steps * flop_step / (ms * 1e-3) / 1e12
+    errs = {} if args.no_check else errors_of(wk, A_host, ns, outs, lgs)
+    plan.close()
+    return {"value": v, "unit": "TFLOP/s", "steps": steps, "rel_frobenius_vs_f64": errs,
+            "ratio_this_path_over_fp32": value / v if v else None}
+
 
 def run_ours(args, wk, world, rank, local):
     import torch
@@ -310,23 +410,11 @@ def run_ours(args, wk, world, rank, local):
     value = world * args.steps * flop_step / (t_ms * 1e-3) / 1e12
 
     # ---- accuracy of this run against the oracle (reported, not timed)
-    errs = {}
-    if rank == 0 and not args.no_check:
-        import oracle
-        for i, n in enumerate(ns):
-            if N > 1024:
-                if wk["gen"] == "stochastic" and n >= 2 ** 10:
-                    # closed form: A^n -> 1 pi^T; check 64 sampled rows and all row sums
-                    pi = oracle.stationary(A_host)
-                    Mg = outs[i].cpu().numpy().astype(np.float64)
-                    Vg = np.ldexp(Mg, int(lgs[i].item()))
-                    rows = np.random.default_rng(0).choice(N, 64, replace=False)
-                    want = np.tile(pi, (64, 1))
-                    errs[str(n)] = float(np.linalg.norm(Vg[rows] - want) / np.linalg.norm(want))
-                    errs["max_rowsum_dev"] = float(np.max(np.abs(Vg.sum(axis=1) - 1.0)))
-                continue
-            M, e, _ = oracle.matpow_f64(A_host, n)
-            errs[str(n)] = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lgs[i].item()), M, e)
+    errs = errors_of(wk, A_host, ns, outs, lgs) if rank == 0 and not args.no_check else {}
+    # ---- the plain FP32 SIMT path on the same workload (the comparator of the metric)
+    fp32 = None
+    if world == 1 and prec != "fp32" and not args.no_fp32:
+        fp32 = fp32_compare(args, wk, A, A_host, flush, stream, value)
 
     # ---- end to end through the C-ABI with host buffers
     A_pin = torch.from_numpy(A_host).pin_memory()
@@ -404,10 +492,9 @@ def run_ours(args, wk, world, rank, local):
         "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[prec],
         "data": "synthetic",
-        "config": {"workload": wk["desc"], "precision": prec, "gemms_per_step":
-                   sum(gemm_count(n) for n in ns), "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": config_for(args, wk, world),
         "rel_frobenius_vs_f64": errs,
+        "fp32_simt_same_workload": fp32,
         "status": st,
         "wall_s_timed": wall,
         "clocks": clocks,
@@ -543,9 +630,7 @@ def run_batched(args, wk, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision],
             "data": "synthetic",
-            "config": {"workload": wk["desc"], "precision": args.precision,
-                       "matrices": len(Ns), "gemms_per_step": sum(gemm_count(n) for n in ns),
-                       "l2": "flushed between timed steps (256 MB write)"},
+            "config": config_for(args, wk, world),
             "rel_frobenius_vs_f64": errs, "status": st, "wall_s_timed": wall, "clocks": clocks,
             "e2e": {"value": flop_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                     "h2d_bytes_per_step": int(sum(a.nbytes for a in hostA)),
@@ -631,8 +716,7 @@ def run_serving(args, wk, world, rank, local):
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision],
             "data": "synthetic",
-            "config": {"workload": wk["desc"], "precision": args.precision,
-                       "offered_req_per_s": rate, "requests": count},
+            "config": config_for(args, wk, world),
             "p50_ms": float(np.percentile(lat, 50) / 1e3) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99) / 1e3) if lat.size else None,
             "effective_tflops": flop / wall / 1e12, "failed_requests": bad,
@@ -653,9 +737,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single512")
-    ap.add_argument("--precision", choices=sorted(DTYPE), default="bf16x3")
+    ap.add_argument("--precision", choices=sorted(DTYPE), default=None,
+                    help="default: the cheapest path that meets the stated error on the workload "
+                         "(bf16x6 for Gaussian inputs, bf16x3 for stochastic ones)")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 SIMT comparator")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--ref-budget", type=float, default=5.0)
     ap.add_argument("--serving-rate", type=float, default=400.0)
@@ -663,6 +750,8 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     wk = WORKLOADS[args.workload]
+    if args.precision is None:
+        args.precision = wk["prec"]
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, wk, world, rank)

@@ -81,6 +81,21 @@ inline __host__ __device__ int ld_for(int N, int fmt) {
   return (N + 7) & ~7;
 }
 
+// Output tile t of a tiles_m x tiles_n grid, visited in groups of 8 tile rows
+// and column by column inside a group: a wave of consecutive CTAs covers a
+// compact block of tiles, so it reads few row bands of X and column bands of
+// Y, which stay in L2 while the wave runs.  The arithmetic of a tile does not
+// depend on when it runs.
+__host__ __device__ inline void tile_raster(int t, int tiles_m, int tiles_n, int* tm, int* tn) {
+  const int GM = 8;
+  const int per = GM * tiles_n;
+  const int g = t / per;
+  const int r = t - g * per;
+  const int rows = tiles_m - g * GM < GM ? tiles_m - g * GM : GM;
+  *tm = g * GM + r % rows;
+  *tn = r / rows;
+}
+
 // Exponent s with max * 2^-s in [0.5, 1) (frexp convention); 0 for max = 0.
 __device__ __forceinline__ int scale_exp_from_bits(unsigned bits) {
   if (bits == 0u) return 0;

@@ -31,7 +31,8 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
   __shared__ float red[THREADS / 32];
 
   const int N = d.N, ld = d.ld;
-  const int tm = tile / d.tiles_n, tn = tile - tm * d.tiles_n;
+  int tm, tn;
+  tile_raster(tile, d.tiles_n, d.tiles_n, &tm, &tn);  // square tiles
   const int m0 = tm * BM, n0 = tn * BN;
   const float* __restrict__ X = (const float*)d.X;
   const float* __restrict__ Y = (const float*)d.Y;

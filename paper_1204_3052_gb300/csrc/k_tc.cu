@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   if (which) t -= P.tiles0;
   const TcProblem& pr = P.p[which];
   const GemmDesc& d = pr.d;
-  const int tm = t / d.tiles_n, tn = t - (t / d.tiles_n) * d.tiles_n;
+  int tm, tn;
+  tile_raster(t, (d.N + 127) / 128, d.tiles_n, &tm, &tn);  // 128-row tiles
   const int m0 = tm * BM, n0 = tn * BN;
   const int N = d.N;
   const int KB = (N + BK - 1) / BK;
@@ -314,7 +315,8 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tm = t / d.tiles_n, tn = t - (t / d.tiles_n) * d.tiles_n;
+  int tm, tn;
+  tile_raster(t, (d.N + 127) / 128, d.tiles_n, &tm, &tn);  // 128-row tiles
   const int m0 = tm * BM, n0 = tn * BN;
   const int N = d.N;
   const int KB = (N + BK - 1) / BK;

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
   if (which) t -= P.tiles0;
   const TcProblem& pr = P.p[which];
   const GemmDesc& d = pr.d;
-  const int tm = t / d.tiles_n, tn = t - (t / d.tiles_n) * d.tiles_n;
+  int tm, tn;
+  tile_raster(t, (d.N + BM - 1) / BM, d.tiles_n, &tm, &tn);
   const int m0 = tm * BM, n0 = tn * BN;
   const int N = d.N;
   const int KB = (N + BK - 1) / BK;
