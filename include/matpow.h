@@ -109,10 +109,15 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       the tensor core's float32 accumulator (subject to the
  *                       accumulator's rounding toward zero, whose bias the
  *                       squaring chain amplifies).
- *   MATPOW_OPT_CHAIN    1 (default): for MATPOW_BF16X3 with the exact split and
- *                       64 < N <= 1024, run the whole chain in one cooperative
- *                       launch (grid barriers between levels); 0: one launch
- *                       per level.
+ *   MATPOW_OPT_CHAIN    1 (default): for the exact splits (MATPOW_BF16X3 with
+ *                       64 < N <= 1024, MATPOW_BF16X6 with 64 < N <= 768) run
+ *                       the whole chain in one cooperative launch (grid
+ *                       barriers between levels), with split-K over 2 or 4
+ *                       CTAs of a thread-block cluster per tile when a level
+ *                       has few tiles (results then equal the level path's
+ *                       to rounding, not bit for bit); 2: the same without
+ *                       split-K (bit-for-bit equal to the level path);
+ *                       0: one launch per level.
  *   MATPOW_OPT_MODP_TC  1 (default): matpow_mod_p with 64 < N <= 16384 runs on the
  *                       tensor cores (byte slices of the residues, exact partial
  *                       sums); 0: 64-bit integer products on the CUDA cores.

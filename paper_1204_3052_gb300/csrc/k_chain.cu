@@ -18,6 +18,14 @@
 // Compared with the level-by-level path this removes every kernel launch but
 // one.  The arithmetic is that of fxb.cuh, identical to the level kernels'.
 //
+// Split-K: when a level has few tiles (N up to ~540), S = 2 or 4 CTAs of a
+// thread-block cluster share one output tile, each taking a contiguous run of
+// its (rotated) k-blocks.  The non-leading CTAs push their float32 partial
+// tiles into the leader's shared memory (distributed shared memory stores,
+// then a remote mbarrier arrival); the leader adds them in rank order and
+// runs the epilogue.  The sum order differs from the single-CTA fold, so
+// split-K results equal the level path's to rounding, not bit for bit.
+//
 // Every wait is bounded: an mbarrier or grid barrier that gives up sets
 // MATPOW_ETIMEDOUT in the plan's status word, and all CTAs then leave the
 // chain, drain their copies and MMAs and free TMEM.
@@ -38,20 +46,31 @@ namespace chain {
 constexpr int BM = 128, BK = 64, THREADS = 256, CHUNK_KB = 4;
 constexpr int MAX_LEVELS = 64;
 constexpr uint64_t WAIT_NS = 2000000000ull;
-template <int BN, int NSL>
+constexpr int SMEM_MAX = 227 * 1024;
+template <int BN, int NSL, int S>
 struct Cfg {
   static constexpr int NG = BN / fxb::BLK;
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = NSL * (A_BYTES + B_BYTES);
-  static constexpr int RING = NSL == 3 ? 216 * 1024 : 192 * 1024;
-  static constexpr int STAGES = RING / STAGE_BYTES;
   static constexpr int KB_MAX = 16;  // N <= 1024
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256 + (2 + NG) * KB_MAX * 4 + 64;
+  // after the ring: barriers (256 B), exponent tables, epilogue scratch, then
+  // the split-K buffer at XOFF (16-byte aligned); 1024 B of alignment slack
+  static constexpr int XOFF = 256 + (2 + NG) * KB_MAX * 4 + 64;
+  static constexpr int EXTRA = 1024 + XOFF;
+  // partial tiles of the S - 1 other CTAs of the cluster (leader only)
+  static constexpr int XBUF = (S - 1) * BM * BN * 4;
+  static constexpr int RING_WANT = NSL == 3 ? 216 * 1024 : 192 * 1024;
+  static constexpr int RING_FIT = SMEM_MAX - EXTRA - XBUF;
+  static constexpr int RING = RING_WANT < RING_FIT ? RING_WANT : RING_FIT;
+  static constexpr int STAGES = RING / STAGE_BYTES;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + EXTRA + XBUF;
   static constexpr int TMEM_USED = 2 * NSL * BN;  // NSL accumulators x 2 buffers
   static constexpr int TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
   static_assert(TMEM_USED <= 512, "TMEM");
+  static_assert(STAGES >= 2, "at least two ring stages");
   static_assert(NSL * 16384 * NG <= STAGES * STAGE_BYTES, "epilogue staging fits the ring");
+  static_assert(SMEM <= SMEM_MAX, "shared memory");
 };
 struct Op {
   signed char xb, yb, cb, last;
@@ -86,6 +105,50 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// ---- thread-block cluster helpers (split-K)
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster executes this the same number of
+// times (at kernel start and end only), so it cannot wait for a thread that
+// never comes.
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared-memory address `a` of this CTA -> the same offset in CTA `rank`.
+__device__ __forceinline__ uint32_t mapa_rank(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t a, float x, float y, float z, float w) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z),
+               "f"(w)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t a) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
+}
+// Bounded wait on a local mbarrier whose arrivals come from other CTAs of the
+// cluster (acquire at cluster scope).
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, uint64_t budget_ns) {
+  const uint64_t t0 = ptx::globaltimer();
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255u) == 255u && ptx::globaltimer() - t0 > budget_ns) return false;
+  }
+}
+
 // Grid-wide barrier number `k` (1, 2, ...) over `G` co-resident CTAs.
 __device__ __forceinline__ bool grid_sync(unsigned* gbar, unsigned target, unsigned* status,
                                           volatile int* cta_abort) {
@@ -113,11 +176,11 @@ __device__ __forceinline__ bool grid_sync(unsigned* gbar, unsigned target, unsig
   return !*cta_abort;
 }
 
-template <int BN, int NSL>
+template <int BN, int NSL, int S>
 __global__ void __launch_bounds__(chain::THREADS, 1)
     tc_chain_kernel(const __grid_constant__ ChainParams P) {
   using namespace chain;
-  using C = Cfg<BN, NSL>;
+  using C = Cfg<BN, NSL, S>;
   constexpr int STAGES = C::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -131,6 +194,10 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   int* eA = (int*)(smem + STAGES * C::STAGE_BYTES + 256);
   int* eB = eA + 2 * C::KB_MAX;
   float* ered = (float*)(eB + NG * C::KB_MAX);
+  // split-K: partial tiles pushed by the other CTAs of the cluster, as
+  // float4 [rank - 1][BN / 4][128 rows]; xbar completes once per level
+  float4* xbuf = (float4*)(smem + STAGES * C::STAGE_BYTES + C::XOFF);
+  const uint32_t xbar = ptx::smem_u32(bars + 2 * STAGES + 5 + 8);  // past tmem_slot..red
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
   const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
@@ -142,6 +209,10 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   const int KB = (N + BK - 1) / BK;
   const unsigned G = gridDim.x;
   unsigned bar_no = 0;
+  const int rank = S > 1 ? (int)cluster_ctarank() : 0;
+  // this CTA's run of the tile's k-blocks (in the rotated visiting order)
+  const int i0 = rank * KB / S, i1 = (rank + 1) * KB / S;
+  const int nkb = i1 - i0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -153,9 +224,13 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
       ptx::mbar_init(accempty0 + 8 * b, 4);
     }
     ptx::mbar_init(drainb, 1);
+    if (S > 1) ptx::mbar_init(xbar, (S - 1) * 128);
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
+  // every CTA of the cluster has started and initialised its barriers before
+  // any remote store or arrival
+  if (S > 1) cluster_sync_all();
   if (warp == 2) {
     ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
     ptx::tmem_relinquish();
@@ -184,10 +259,11 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   fence_proxy_async_global();
 
   int kb_base = 0;  // k-blocks done by this CTA: ring and accumulator-buffer phases
+  uint32_t xph = 0;  // phase of xbar (leader)
   float T[BN];
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
     const int nops = P.lvl_nops[L];
-    const int t_all = blockIdx.x;
+    const int t_all = blockIdx.x / S;
     const bool has = t_all < nops * P.tiles_per_op;
     const int oi = has ? t_all / P.tiles_per_op : 0;
     const int t = has ? t_all - oi * P.tiles_per_op : 0;
@@ -200,8 +276,8 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
     if (has) {
       if (warp == 0) {
         if (lane == 0) {
-          for (int kb = 0; kb < KB; ++kb) {
-            const int g = kb_base + kb;
+          for (int kb = i0; kb < i1; ++kb) {
+            const int g = kb_base + kb - i0;
             const int s = g % STAGES;
             const uint32_t ph = (g / STAGES) & 1;
             if (!ptx::mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, WAIT_NS)) {
@@ -227,8 +303,8 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
       } else if (warp == 1) {
         if (lane == 0) {
           constexpr uint32_t idesc = idesc_bf16(BM, BN);
-          for (int kb = 0; kb < KB; ++kb) {
-            const int g = kb_base + kb;
+          for (int kb = i0; kb < i1; ++kb) {
+            const int g = kb_base + kb - i0;
             const int buf = g & 1;
             const uint32_t t0 = tmem + (uint32_t)(buf * NSL * BN);
             if (!ptx::mbar_wait(accempty0 + 8 * buf, ((g >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
@@ -280,8 +356,8 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
         for (int j = 0; j < BN; ++j) T[j] = 0.f;
         asm volatile("bar.sync 2, 160;" ::: "memory");  // exponents staged
         bool ok = true;
-        for (int kb = 0; kb < KB; ++kb) {
-          const int g = kb_base + kb;
+        for (int kb = i0; kb < i1; ++kb) {
+          const int g = kb_base + kb - i0;
           const int buf = g & 1;
           int dummy = 0;
           if (!ptx::mbar_wait(accfull0 + 8 * buf, (g >> 1) & 1, &dummy, 2 * WAIT_NS)) {
@@ -301,37 +377,71 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
         }
-        // one verdict for all four epilogue warps (they share named barriers below)
-        fxb::epi_bar();
-        if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
-        fxb::epi_bar();
-        ok = *epi_ok != 0;
-        if (op.last) {
-          if (ok) {
-            if (t == 0 && q == 0 && lane == 0 && P.out_log2) *P.out_log2 = Ec;
-            if (row < N) {
-              float* O = P.out + (size_t)row * N;
+        const int et = 32 * q + lane;  // epilogue thread = tile row
+        const bool lead = S == 1 || rank == 0;
+        if (!lead) {
+          // push this partial tile into the leader's buffer, then arrive there
+          const uint32_t dst = mapa_rank(ptx::smem_u32(xbuf + (size_t)(rank - 1) * (BN / 4) * 128), 0);
 #pragma unroll
-              for (int j = 0; j < BN; ++j) {
-                const int c = n0 + j;
-                if (c < N) O[c] = P.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+          for (int c = 0; c < BN / 4; ++c)
+            st_cluster_v4(dst + (uint32_t)((c * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
+                          T[4 * c + 3]);
+          mbar_arrive_remote(mapa_rank(xbar, 0));
+        } else if (S > 1) {
+          // the other CTAs' partial tiles, added in rank order
+          if (!mbar_wait_cluster(xbar, xph, 2 * WAIT_NS)) {
+            *abort_flag = 1;
+            ok = false;
+          }
+          xph ^= 1;
+          if (ok) {
+#pragma unroll 1
+            for (int r = 1; r < S; ++r) {
+              const float4* src = xbuf + (size_t)(r - 1) * (BN / 4) * 128 + et;
+#pragma unroll
+              for (int c = 0; c < BN / 4; ++c) {
+                const float4 v = src[c * 128];
+                T[4 * c] += v.x;
+                T[4 * c + 1] += v.y;
+                T[4 * c + 2] += v.z;
+                T[4 * c + 3] += v.w;
               }
             }
           }
-        } else {
-          if (t == 0 && q == 0 && lane == 0) P.scales[op.sc].E = Ec;
-          if (ok) {  // the ring is idle here: all k-blocks of this tile were consumed
-            const CUtensorMap* cm[NSL];
+        }
+        if (lead) {
+          // one verdict for all four epilogue warps (they share named barriers below)
+          fxb::epi_bar();
+          if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
+          fxb::epi_bar();
+          ok = *epi_ok != 0;
+          if (op.last) {
+            if (ok) {
+              if (t == 0 && q == 0 && lane == 0 && P.out_log2) *P.out_log2 = Ec;
+              if (row < N) {
+                float* O = P.out + (size_t)row * N;
 #pragma unroll
-            for (int k = 0; k < NSL; ++k) cm[k] = &P.amap[op.cb][k];
-            fxb::store_slices_tma<BN, 128, NSL>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
-                                                cm, P.bexp[op.cb], &P.scales[op.sc].maxbits, ered,
-                                                q == 0 && lane == 0, n0);
+                for (int j = 0; j < BN; ++j) {
+                  const int c = n0 + j;
+                  if (c < N) O[c] = P.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+                }
+              }
+            }
+          } else {
+            if (t == 0 && q == 0 && lane == 0) P.scales[op.sc].E = Ec;
+            if (ok) {  // the ring is idle here: all k-blocks of this tile were consumed
+              const CUtensorMap* cm[NSL];
+#pragma unroll
+              for (int k = 0; k < NSL; ++k) cm[k] = &P.amap[op.cb][k];
+              fxb::store_slices_tma<BN, 128, NSL>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
+                                                  cm, P.bexp[op.cb], &P.scales[op.sc].maxbits, ered,
+                                                  q == 0 && lane == 0, n0);
+            }
+            fence_proxy_async_global();
           }
-          fence_proxy_async_global();
         }
       }
-      kb_base += KB;  // ring and accumulator counters advance only with work done
+      kb_base += nkb;  // ring and accumulator counters advance only with work done
     }
     if (P.ops[2 * L + nops - 1].last) break;  // the final product has been written
     // this level's slices, exponents and maxima are visible to every CTA
@@ -358,28 +468,79 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
     ptx::tmem_dealloc(tmem, C::TMEM_COLS);
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(P.status, ST_TIMEOUT);
+  // no CTA leaves while another of its cluster may still write to its shared memory
+  if (S > 1) cluster_sync_all();
 }
 
 // ---------------------------------------------------------------------------
 // host side
 
+template <int BN, int NSL, int S>
+static cudaError_t chain_attr() {
+  return cudaFuncSetAttribute(tc_chain_kernel<BN, NSL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              chain::Cfg<BN, NSL, S>::SMEM);
+}
+
 cudaError_t tc_chain_init(matpow_plan_s*) {
-  cudaError_t e = cudaFuncSetAttribute(tc_chain_kernel<64, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       chain::Cfg<64, 2>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_chain_kernel<128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             chain::Cfg<128, 2>::SMEM);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(tc_chain_kernel<64, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             chain::Cfg<64, 3>::SMEM);
+  cudaError_t e = chain_attr<64, 2, 1>();
+  if (e == cudaSuccess) e = chain_attr<128, 2, 1>();
+  if (e == cudaSuccess) e = chain_attr<64, 3, 1>();
+  if (e == cudaSuccess) e = chain_attr<64, 2, 2>();
+  if (e == cudaSuccess) e = chain_attr<64, 2, 4>();
+  if (e == cudaSuccess) e = chain_attr<64, 3, 2>();
   return e;
+}
+
+// Cooperative launch of G CTAs in clusters of S (S = 1: no cluster).
+template <int BN, int NSL, int S>
+static cudaError_t chain_launch(ChainParams* P, int G, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(chain::THREADS);
+  cfg.dynamicSmemBytes = chain::Cfg<BN, NSL, S>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = S;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = S > 1 ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, tc_chain_kernel<BN, NSL, S>, *P);
+}
+
+// Clusters of S co-resident with one CTA per SM (0 if the query fails).
+template <int BN, int NSL, int S>
+static int chain_max_clusters() {
+  static int cached = -1;
+  if (cached >= 0) return cached;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(S * 64);
+  cfg.blockDim = dim3(chain::THREADS);
+  cfg.dynamicSmemBytes = chain::Cfg<BN, NSL, S>::SMEM;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = S;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, tc_chain_kernel<BN, NSL, S>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached = n;
+  return n;
 }
 
 matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
                            int64_t* dLog2, cudaStream_t s, bool* used) {
   *used = false;
   const int fmt = plan_float_fmt(p);
-  if (!p->use_chain || !fmt_exact(fmt) || n < 2 || N <= p->tiny_max || N > 1024) return MATPOW_OK;
+  if (p->chain_mode == 0 || !fmt_exact(fmt) || n < 2 || N <= p->tiny_max || N > 1024) return MATPOW_OK;
   const int nsl = fmt_slices(fmt);
   // three accumulators per buffer fit TMEM only at 64-wide tiles
   if (nsl == 3 && N > 768) return MATPOW_OK;
@@ -391,8 +552,24 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
   const int tiles_per_op = ((N + chain::BM - 1) / chain::BM) * tiles_n;
   int maxops = 1;
   for (auto& lv : levels) maxops = std::max(maxops, (int)lv.ops.size());
-  const int G = maxops * tiles_per_op;
-  if (G > p->num_sms) return MATPOW_OK;
+  const int G1 = maxops * tiles_per_op;
+  if (G1 > p->num_sms) return MATPOW_OK;
+  // split-K: 2 or 4 CTAs per tile when the SMs allow it (each keeps >= 1 k-block)
+  const int KB = (N + chain::BK - 1) / chain::BK;
+  int S = 1;
+  if (p->chain_mode == 1 && BN == 64) {
+    const int smax = nsl == 3 ? 2 : 4;
+    for (int c = smax; c >= 2; c /= 2) {
+      if (G1 * c > p->num_sms || c > KB) continue;
+      const int mc = nsl == 3 ? chain_max_clusters<64, 3, 2>()
+                     : c == 4 ? chain_max_clusters<64, 2, 4>() : chain_max_clusters<64, 2, 2>();
+      if (mc >= G1) {
+        S = c;
+        break;
+      }
+    }
+  }
+  const int G = G1 * S;
 
   static thread_local ChainParams P;  // ~4 KB: kept off the stack
   memset(&P, 0, sizeof P);
@@ -437,19 +614,21 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
   cudaError_t e = cudaMemsetAsync(p->scales, 0, sizeof(Scale) * nslots, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->gbar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemsetAsync");
-  void* args[] = {&P};
   cudaEvent_t ev;
   timed_begin(p, s, &ev);
   if (nsl == 3)
-    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<64, 3>, dim3(G), dim3(chain::THREADS),
-                                    args, chain::Cfg<64, 3>::SMEM, s);
+    e = S == 2 ? chain_launch<64, 3, 2>(&P, G, s) : chain_launch<64, 3, 1>(&P, G1, s);
   else if (BN == 64)
-    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<64, 2>, dim3(G), dim3(chain::THREADS),
-                                    args, chain::Cfg<64, 2>::SMEM, s);
+    e = S == 4 ? chain_launch<64, 2, 4>(&P, G, s)
+        : S == 2 ? chain_launch<64, 2, 2>(&P, G, s) : chain_launch<64, 2, 1>(&P, G1, s);
   else
-    e = cudaLaunchCooperativeKernel((const void*)tc_chain_kernel<128, 2>, dim3(G), dim3(chain::THREADS),
-                                    args, chain::Cfg<128, 2>::SMEM, s);
-  if (e != cudaSuccess) return cuda_fail(p, e, "cudaLaunchCooperativeKernel(tc_chain_kernel)");
+    e = chain_launch<128, 2, 1>(&P, G1, s);
+  if (e != cudaSuccess && S > 1) {
+    // a cooperative launch with clusters was refused: run without split-K
+    cudaGetLastError();
+    e = nsl == 3 ? chain_launch<64, 3, 1>(&P, G1, s) : chain_launch<64, 2, 1>(&P, G1, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(p, e, "cooperative launch of tc_chain_kernel");
   timed_end(p, s, ev, MATPOW_KERNEL_TC, 2.0 * N * (double)N * N * matpow_gemm_count(n));
   p->launches++;
   *used = true;

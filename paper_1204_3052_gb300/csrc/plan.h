@@ -93,7 +93,7 @@ struct matpow_plan_s {
   int tiny_max = 64;
   int tile_override = 0;
   int split_mode = 0;  // BF16X3: 0 exact fixed-point slices, 1 floating hi/lo planes
-  bool use_chain = true;  // whole-chain cooperative kernel where it applies
+  int chain_mode = 1;  // whole-chain kernel: 0 off, 1 with split-K where it fits, 2 without
   bool modp_tc = true;    // mod-p products on the tensor cores (64 < N <= 16384)
   int group_bn = 64;      // tile width of the current grouped tensor-core launch
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel

@@ -31,6 +31,7 @@ def test_uneven_batch_matches_oracle_and_single_calls(prec):
     ns = [int(x) for x in bd.ns]
     ns[0], ns[1] = 0, 1  # trivial powers inside the batch
     plan = mpw.Plan(256, prec)
+    plan.set_option(mpw.OPT_CHAIN, 2)  # single calls without split-K: same sums as the batch
     dAs = [to_dev(a) for a in As]
     lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
     outs = plan.batched(dAs, ns, log2=lg)
@@ -61,6 +62,7 @@ def test_batch_with_wide_tiles(prec):
     ns = [13, 77, 2, 1000, 9]
     As = [wl.gaussian(N, 7 + i) for i, N in enumerate(Ns)]
     plan = mpw.Plan(1100, prec)
+    plan.set_option(mpw.OPT_CHAIN, 2)
     dAs = [to_dev(a) for a in As]
     lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
     outs = plan.batched(dAs, ns, log2=lg)

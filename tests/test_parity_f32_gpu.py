@@ -299,6 +299,7 @@ def test_whole_chain_kernel_equals_level_path_bitwise(prec, N):
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
     chain = mpw.Plan(1024, prec)
+    chain.set_option(mpw.OPT_CHAIN, 2)  # whole chain, one CTA per tile
     level = mpw.Plan(1024, prec)
     level.set_option(mpw.OPT_CHAIN, 0)
     A = wl.gaussian(N, N + 7)
@@ -341,3 +342,31 @@ def test_bf16x6_at_float32_accuracy():
         print(N, n, errs, ef32)
         assert errs["bf16x6"] <= 4 * ef32, (N, n, errs, ef32)
         assert errs["bf16x6"] * 30 < errs["bf16x3"], (N, n, errs)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("N", [65, 100, 130, 256, 300, 512, 540])
+def test_split_k_chain_matches_oracle_and_unsplit_chain(prec, N):
+    # split-K over a cluster changes only the order in which the exact
+    # k-block partial sums are added: the result stays within rounding of the
+    # unsplit chain and within the same bound against the oracle
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    split = mpw.Plan(1024, prec)  # default: split-K where it fits
+    whole = mpw.Plan(1024, prec)
+    whole.set_option(mpw.OPT_CHAIN, 2)
+    A = wl.gaussian(N, 3 * N + 1)
+    dA = to_dev(A)
+    for n in (2, 3, 16, 1000):
+        os_, ls = split.f32(dA, n, mantissa=True)
+        ow, lw = whole.f32(dA, n, mantissa=True)
+        split.check()
+        whole.check()
+        M, e, _ = oracle.matpow_f64(A, n)
+        err = oracle.rel_frobenius(os_.cpu().numpy(), int(ls.item()), M, e)
+        assert err <= gate(n, floor_rel(A, n, M, e, prec)), (N, n, err)
+        d = oracle.rel_frobenius(os_.cpu().numpy(), int(ls.item()),
+                                 ow.cpu().numpy().astype(np.float64), int(lw.item()))
+        assert d <= 1e-5 * n ** 0.5 * (30 if prec == "bf16x3" else 1), (N, n, d)
+    split.close()
+    whole.close()

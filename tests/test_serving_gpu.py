@@ -37,6 +37,7 @@ def test_mixed_stream_matches_isolated_runs(prec):
     from paper_1204_3052_gb300 import matpow as mpw
     server = mpw.Server(300, prec, hbm_budget_bytes=64 << 20, max_inflight=12)
     plan = mpw.Plan(300, prec)
+    plan.set_option(mpw.OPT_CHAIN, 2)  # isolated runs without split-K: same sums as the server
     reqs = make_requests(60, 5)
     dev = []
     tickets = []
