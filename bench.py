@@ -59,6 +59,12 @@ WORKLOADS = {
     "serving": dict(kind="serving", count=2000, N=2048, ns=[], prec="bf16x6",
                     desc="serving: 2000 Poisson-arrival requests, N log-uniform [8,2048], n log-uniform "
                          "[1,2^30], 90% float / 10% mod 65521, seed 0"),
+    "modp2048": dict(kind="modp", N=2048, ns=[1000], p=65521, prec="bf16x3",
+                     desc="single N=2048 U{0..65520} uint32, A^1000 mod 65521 (14 products), seed 0"),
+    # a smaller batch of the same mix (profiling case: a few hundred MB on the device)
+    "batched512": dict(kind="batched", count=512, n_max=4096, N=256, ns=[], prec="bf16x6",
+                       desc="batched: 512 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
+                            "n log-uniform in [1,4096], seed 0; one grouped launch per level"),
     # one product at N=4096 (operands 64 MB each, beyond L2): profiling case
     "probe4096": dict(N=4096, ns=[2], gen="stochastic", prec="bf16x3",
                       desc="single N=4096 exact row-stochastic float32, n=2 (one product), seed 0"),
@@ -201,6 +207,26 @@ def cpu_sample(wk, budget_s: float = 15.0, threads: int = 0):
                 N, ns, reps, t_total)}
 
 
+def cpu_sample_modp(wk, budget_s):
+    """Oracle A^64 mod p (6 products) of the workload's leading 512 x 512 block,
+    repeated for about budget_s; effective TFLOP/s."""
+    import oracle
+    from paper_1204_3052_gb300 import workloads as wl
+    A = wl.modp_uniform(wk["N"], wk["p"], 0)[:512, :512].copy()
+    cores = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.matpow_modp(A, 64, wk["p"])
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or reps >= 100:
+            break
+    return {"value": reps * 6 * 2.0 * 512 ** 3 / dt / 1e12, "unit": "TFLOP/s", "cores": cores,
+            "kind": "oracle", "sample": "uint64 triple-loop A^64 mod p of the leading 512 x 512 block "
+                                        "x %d (%.1f s)" % (reps, dt)}
+
+
 def cpu_sample_list(items, budget_s):
     """Oracle over (A, n, p) items in order until ~budget_s; effective TFLOP/s."""
     import oracle
@@ -242,11 +268,17 @@ def config_for(args, wk, world):
         cfg.update(matrices=wk["count"], gemms_per_step=int(sum(gemm_count(int(n)) for n in bd.ns)),
                    l2="flushed between timed steps (256 MB write)")
     elif wk.get("kind") == "serving":
-        cfg.update(offered_req_per_s=args.serving_rate, requests=wk["count"])
+        cfg.update(requests=wk["count"], load_sweep=list(args.sweep), sweep_requests=args.sweep_count)
+    elif wk.get("kind") == "modp":
+        cfg.update(p=wk["p"], gemms_per_step=sum(gemm_count(n) for n in wk["ns"]),
+                   l2="flushed between timed steps (256 MB write)")
+        cfg["precision"] = "exact mod p (byte-sliced bfloat16 tensor-core products)"
     else:
         cfg.update(gemms_per_step=sum(gemm_count(n) for n in wk["ns"]),
                    l2="flushed between timed steps (256 MB write)",
                    parallelism="replicas" if world > 1 else "single")
+        if args.chain_mode != 1:
+            cfg["chain_mode"] = args.chain_mode
     return cfg
 
 
@@ -259,6 +291,8 @@ def run_reference(args, wk, world, rank):
     for _ in range(max(args.steps, 1)):
         if wk.get("kind") in ("batched", "serving"):
             cb = cpu_sample_list(reference_items(wk), args.ref_budget)
+        elif wk.get("kind") == "modp":
+            cb = cpu_sample_modp(wk, args.ref_budget)
         else:
             cb = cpu_sample(wk, budget_s=args.ref_budget)
         res.append(cb["items_per_s"] if serving else cb["value"])
@@ -269,8 +303,8 @@ def run_reference(args, wk, world, rank):
     line = {"metric": metric, "value": value, "unit": unit,
             "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_for(args, wk, world), "cpu_baseline": cb,
+            "vs_baseline": None, "dtype": "u64 mod p" if wk.get("kind") == "modp" else "f64",
+            "data": "synthetic", "config": config_for(args, wk, world), "cpu_baseline": cb,
             "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -371,6 +405,7 @@ def run_ours(args, wk, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     plan = mpw.Plan(N, prec, device=local)
+    plan.set_option(mpw.OPT_CHAIN, args.chain_mode)
 
     def step(s):
         for i, n in enumerate(ns):
@@ -509,6 +544,117 @@ def run_ours(args, wk, world, rank, local):
     plan.close()
 
 
+def run_modp(args, wk, world, rank, local):
+    """A^n mod p through matpow_mod_p (exact byte-sliced tensor-core products)."""
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    from paper_1204_3052_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_src = load_peaks()
+    N, ns, pm = wk["N"], wk["ns"], wk["p"]
+    flop_step = sum(gemm_count(n) for n in ns) * 2.0 * N ** 3
+    A_host = wl.modp_uniform(N, pm, 0)
+    A = torch.from_numpy(A_host.view(np.int32)).to(dev)
+    outs = [torch.empty_like(A) for _ in ns]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = mpw.Plan(N, "fp32", device=local)
+
+    def step(s):
+        for i, n in enumerate(ns):
+            st = mpw.matpow_mod_p(plan.h, A, N, n, pm, outs[i], s)
+            if st != 0:
+                mpw._check(st, plan.h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(stream)
+        plan.check(stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = plan.launch_count()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step(stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        barrier(world)
+        clocks = sampler.stop()
+        launches = plan.launch_count() - launches0
+        st = plan.sync(stream)
+    t_ms = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in evs), dev)
+    value = world * args.steps * flop_step / (t_ms * 1e-3) / 1e12
+    exact = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        exact = True
+        for i, n in enumerate(ns):
+            want, _ = oracle.matpow_modp(A_host, n, pm)
+            got = outs[i].cpu().numpy().view(np.uint32).astype(np.uint64)
+            exact = exact and bool(np.array_equal(got, want))
+    # e2e: host input in, result out, through the C-ABI
+    A_pin = torch.from_numpy(A_host.view(np.int32)).pin_memory()
+    outs_pin = [torch.empty(A_host.shape, dtype=torch.int32).pin_memory() for _ in ns]
+    e2e_steps = max(args.steps, 3)
+    with torch.cuda.stream(stream):
+        def e2e_step():
+            A.copy_(A_pin, non_blocking=True)
+            step(stream)
+            for i in range(len(ns)):
+                outs_pin[i].copy_(outs[i], non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(world, e0.elapsed_time(e1), dev)
+    # dominant kernel: per-launch CUDA-event time of the mod-p products
+    plan.set_option(mpw.OPT_TIMING, 1)
+    with torch.cuda.stream(stream):
+        plan.kernel_time(mpw.KERNEL_MODP, reset=True)
+        for _ in range(max(args.steps, 3)):
+            flush.zero_()
+            step(stream)
+        torch.cuda.synchronize()
+        kl, kms, kflop = plan.kernel_time(mpw.KERNEL_MODP, reset=True)
+    plan.set_option(mpw.OPT_TIMING, 0)
+    plan.close()
+    # four byte-slice products per product: 4 x 2N^3 bfloat16 tensor flop
+    achieved = 4.0 * kflop / (kms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / peaks["bf16_tflops"], "traffic": None, "kernel": "tc_modp_kernel",
+            "peak_source": peak_src + " bf16 burst", "counted": "4 bfloat16 byte-slice products per term",
+            "launches_timed": kl, "avg_launch_us": kms * 1e3 / max(kl, 1)}
+    if rank != 0:
+        return
+    cb = cpu_sample_modp(wk, args.cpu_budget) if world == 1 and not args.no_cpu else None
+    line = {"metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32 mod p",
+            "data": "synthetic", "config": config_for(args, wk, world),
+            "bit_exact_vs_oracle": exact, "status": st, "wall_s_timed": wall, "clocks": clocks,
+            "e2e": {"value": e2e_steps * flop_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": int(A_host.nbytes),
+                    "d2h_bytes_per_step": int(A_host.nbytes * len(ns))},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb}
+    print(json.dumps(line))
+
+
 def run_batched(args, wk, world, rank, local):
     """Config 3: one matpow_batched call over an uneven batch per step."""
     import torch
@@ -606,7 +752,7 @@ def run_batched(args, wk, world, rank, local):
     achieved = kflop * products / (kms * 1e-3) / 1e12 if kms else 0.0
     roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
             "frac": achieved / peaks["bf16_tflops"], "traffic": None,
-            "kernel": "tc_fxb_group_kernel (grouped level launches, N > 64)",
+            "kernel": "tc_fxb_persist_kernel (persistent grouped level launches, N > 64)",
             "peak_source": peak_src + " bf16 burst", "launches_timed": kl,
             "avg_launch_us": kms * 1e3 / max(kl, 1),
             "tiny_chain_share_ms": tms / 2, "level_kernels_ms": kms / 2}
@@ -640,8 +786,28 @@ def run_batched(args, wk, world, rank, local):
     plan.close()
 
 
+def _lindley(arrivals, service):
+    """Latencies of a single FIFO server (one request at a time) by Lindley's
+    recursion: start_i = max(arrival_i, finish_(i-1)), latency = finish - arrival."""
+    lat = np.empty(len(arrivals))
+    free = 0.0
+    for i, (t, d) in enumerate(zip(arrivals, service)):
+        start = max(t, free)
+        free = start + d
+        lat[i] = free - t
+    return lat
+
+
 def run_serving(args, wk, world, rank, local):
-    """Config 5 (scaled): Poisson arrivals through matpow_submit / matpow_poll."""
+    """Config 5 (scaled): requests through matpow_submit / matpow_poll.
+
+    1. capacity: the whole stream submitted at once (closed burst), req/s;
+    2. Poisson arrivals at 0.5, 0.8, 1.0 and 1.2 x that capacity on the first
+       `sweep_count` requests: served req/s, p50 and p99 latency;
+    3. comparator: the same requests one at a time through single-request
+       plan calls (each timed with CUDA events), and the p50/p99 an unbatched
+       FIFO server with those service times would give at the same loads.
+    """
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
     from paper_1204_3052_gb300 import workloads as wl
@@ -649,9 +815,9 @@ def run_serving(args, wk, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     count = wk["count"]
-    # offered load: requests per second (about the measured capacity by default)
-    rate = args.serving_rate
-    reqs = wl.serving_stream(count=count, seed=0, rate_per_s=rate)
+    sweep_count = min(count, args.sweep_count)
+    base_rate = 1000.0
+    reqs = wl.serving_stream(count=count, seed=0, rate_per_s=base_rate)
     host = [wl.request_matrix(r) for r in reqs]
     dA, outs, lgs = [], [], []
     for r, a in zip(reqs, host):
@@ -662,26 +828,52 @@ def run_serving(args, wk, world, rank, local):
     flop = sum(gemm_count(r.n) * 2.0 * r.N ** 3 for r in reqs)
     server = mpw.Server(2048, args.precision, device=local, hbm_budget_bytes=16 << 30,
                         max_inflight=256, max_queue=count + 16)
-    # warm-up requests (not timed)
-    for i in range(min(8, count)):
+
+    def submit(i):
         r = reqs[i]
-        server.wait(server.submit(dA[i], r.n, outs[i], kind=r.kind, p=r.p, log2_scale=lgs[i]))
-    base_lat = len(server.latencies_us())
-    torch.cuda.synchronize()
+        return server.submit(dA[i], r.n, outs[i], kind=r.kind, p=r.p, log2_scale=lgs[i])
+
+    def drain(tickets):
+        bad = 0
+        for t in tickets:
+            if server.wait(t, timeout_s=600) != mpw.OK:
+                bad += 1
+        torch.cuda.synchronize()
+        return bad
+
+    # warm-up requests (not timed)
+    drain([submit(i) for i in range(min(8, count))])
+    # ---- 1. capacity: closed burst of the whole stream
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    n0 = len(server.latencies_us())
     t0 = time.perf_counter()
-    tickets = []
-    for i, r in enumerate(reqs):
-        delay = r.t_arrival - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(server.submit(dA[i], r.n, outs[i], kind=r.kind, p=r.p, log2_scale=lgs[i]))
-    bad = 0
-    for t in tickets:
-        if server.wait(t, timeout_s=600) != mpw.OK:
-            bad += 1
-    torch.cuda.synchronize()
+    bad = drain([submit(i) for i in range(count)])
     wall = time.perf_counter() - t0
-    lat = server.latencies_us()[base_lat:]
+    clocks = sampler.stop()
+    capacity = count / wall
+    burst_lat = np.asarray(server.latencies_us()[n0:])
+    # ---- 2. Poisson load sweep
+    sweep = []
+    arr0 = np.array([r.t_arrival for r in reqs[:sweep_count]])
+    for f in args.sweep:
+        rate = f * capacity
+        arr = arr0 * base_rate / rate
+        n0 = len(server.latencies_us())
+        t0 = time.perf_counter()
+        tickets = []
+        for i in range(sweep_count):
+            delay = arr[i] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(submit(i))
+        bad += drain(tickets)
+        w = time.perf_counter() - t0
+        lat = np.asarray(server.latencies_us()[n0:])
+        sweep.append({"load": f, "offered_req_per_s": rate, "served_req_per_s": sweep_count / w,
+                      "p50_ms": float(np.percentile(lat, 50) / 1e3),
+                      "p99_ms": float(np.percentile(lat, 99) / 1e3)})
     server.close()
     # exact mod-p requests checked against the oracle (those with N <= 256)
     checked = mism = 0
@@ -692,38 +884,59 @@ def run_serving(args, wk, world, rank, local):
                 want, _ = oracle.matpow_modp(a, r.n, r.p)
                 checked += 1
                 mism += int(not np.array_equal(o.cpu().numpy().view(np.uint32).astype(np.uint64), want))
-    # unbatched comparator: the same requests one at a time through plans
+    # ---- 3. unbatched comparator: single-request calls, one at a time
     plan_f = mpw.Plan(2048, args.precision, device=local)
     plan_m = mpw.Plan(2048, "fp32", device=local)
-    sample = list(range(0, count, max(1, count // 200)))
-    torch.cuda.synchronize()
-    u0 = time.perf_counter()
-    for i in sample:
+    stream = torch.cuda.current_stream(dev)
+
+    def single(i):
         r = reqs[i]
         if r.kind:
             mpw._check(mpw.matpow_mod_p(plan_m.h, dA[i], r.N, r.n, r.p, outs[i]), plan_m.h)
         else:
             mpw._check(mpw.matpow_f32(plan_f.h, dA[i], r.N, r.n, outs[i], lgs[i]), plan_f.h)
+
+    for i in range(min(8, sweep_count)):
+        single(i)
     torch.cuda.synchronize()
-    unb = (time.perf_counter() - u0) / len(sample)
+    svc = np.empty(sweep_count)
+    for i in range(sweep_count):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        single(i)
+        e1.record(stream)
+        e1.synchronize()
+        svc[i] = e0.elapsed_time(e1) * 1e-3
     plan_f.close()
     plan_m.close()
+    unb_cap = sweep_count / svc.sum()
+    unb = {"req_per_s": unb_cap, "ms_per_request_mean": float(svc.mean() * 1e3),
+           "note": "device time of each request alone through matpow_f32 / matpow_mod_p; "
+                   "latencies of a one-at-a-time FIFO server with these service times"}
+    unb["sweep"] = []
+    for f in args.sweep:
+        rate = f * capacity
+        lat = _lindley(arr0 * base_rate / rate, svc)
+        unb["sweep"].append({"load": f, "offered_req_per_s": rate,
+                             "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                             "p99_ms": float(np.percentile(lat, 99) * 1e3)})
     if rank != 0:
         return
-    lat = np.asarray(lat)
-    line = {"metric": "matpow serving req/s", "value": count / wall, "unit": "req/s", "n_gpus": world,
+    line = {"metric": "matpow serving req/s", "value": capacity, "unit": "req/s", "n_gpus": world,
             "steps": 1, "warmup": 8, "ms_per_step": wall * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": config_for(args, wk, world),
-            "p50_ms": float(np.percentile(lat, 50) / 1e3) if lat.size else None,
-            "p99_ms": float(np.percentile(lat, 99) / 1e3) if lat.size else None,
-            "effective_tflops": flop / wall / 1e12, "failed_requests": bad,
+            "p50_ms": float(np.percentile(burst_lat, 50) / 1e3) if burst_lat.size else None,
+            "p99_ms": float(np.percentile(burst_lat, 99) / 1e3) if burst_lat.size else None,
+            "latency_note": "p50/p99 of the closed burst (queueing included); see load_sweep",
+            "load_sweep": sweep, "effective_tflops": flop / wall / 1e12, "failed_requests": bad,
             "modp_checked": checked, "modp_mismatches": mism,
-            "unbatched_ms_per_request_sampled": unb * 1e3,
-            "unbatched_req_per_s_estimate": 1.0 / unb if unb else None,
-            "e2e": {"value": count / wall, "unit": "req/s", "h2d_bytes_per_step": 0,
+            "unbatched": unb, "speedup_over_unbatched": capacity / unb_cap,
+            "clocks": clocks,
+            "e2e": {"value": capacity, "unit": "req/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0,
                     "note": "inputs resident; submit-to-completion through the public API"},
             "gpu_launches": None, "roofline": None, "cpu_baseline": None}
@@ -743,9 +956,14 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 SIMT comparator")
+    ap.add_argument("--chain-mode", type=int, choices=[0, 1, 2], default=1,
+                    help="whole-chain kernel for N <= 1024: 1 with split-K (default), 2 without, "
+                         "0 level-by-level launches")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--ref-budget", type=float, default=5.0)
-    ap.add_argument("--serving-rate", type=float, default=400.0)
+    ap.add_argument("--sweep", type=float, nargs="*", default=[0.5, 0.8, 1.0, 1.2],
+                    help="serving: offered loads as fractions of the measured capacity")
+    ap.add_argument("--sweep-count", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -759,6 +977,8 @@ def main():
         run_batched(args, wk, world, rank, local)
     elif wk.get("kind") == "serving":
         run_serving(args, wk, world, rank, local)
+    elif wk.get("kind") == "modp":
+        run_modp(args, wk, world, rank, local)
     else:
         run_ours(args, wk, world, rank, local)
     if world > 1:

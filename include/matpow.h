@@ -121,9 +121,13 @@ const char* matpow_last_error(matpow_plan_t plan);
  *   MATPOW_OPT_MODP_TC  1 (default): matpow_mod_p with 64 < N <= 16384 runs on the
  *                       tensor cores (byte slices of the residues, exact partial
  *                       sums); 0: 64-bit integer products on the CUDA cores.
+ *   MATPOW_OPT_PERSIST  1 (default): matpow_batched runs each level's 64-column
+ *                       tensor-core tiles (orders up to 4096) in one persistent
+ *                       launch, one CTA per SM walking the whole tile list; 0:
+ *                       one CTA per tile.  Results are identical either way.
  */
 enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4,
-       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6, MATPOW_OPT_MODP_TC = 7 };
+       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6, MATPOW_OPT_MODP_TC = 7, MATPOW_OPT_PERSIST = 8 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
 /* ---- the power ------------------------------------------------------------ */

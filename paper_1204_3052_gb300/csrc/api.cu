@@ -253,6 +253,9 @@ extern "C" matpow_status matpow_plan_set_option(matpow_plan_t p, int key, int64_
       if (value < 0 || value > 2) return fail(p, MATPOW_EINVAL, "chain mode must be 0, 1 or 2");
       p->chain_mode = (int)value;
       return MATPOW_OK;
+    case MATPOW_OPT_PERSIST:
+      p->persist = value != 0;
+      return MATPOW_OK;
     case MATPOW_OPT_MODP_TC:
       p->modp_tc = value != 0;
       drop_graphs(p);

@@ -31,6 +31,7 @@ void mp::batch_free(matpow_plan_s* p) {
   if (b.descs) cudaFree(b.descs);
   if (b.h_descs) cudaFreeHost(b.h_descs);
   if (b.staged) cudaEventDestroy(b.staged);
+  if (b.exec) cudaGraphExecDestroy(b.exec);
   b = BatchState();
 }
 
@@ -84,6 +85,37 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   cudaStream_t s = (cudaStream_t)stream;
   const int fmt = plan_float_fmt(p);
   const bool tc = p->prec != MATPOW_FP32_SIMT;
+
+  // ---- replay: the same call as the last captured one needs no host work
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(p, cudaStreamIsCapturing(s, &cs));
+  const bool graphable = p->use_graphs && !p->timing_on && cs == cudaStreamCaptureStatusNone;
+  std::vector<uint64_t> sig;
+  if (graphable) {
+    sig.reserve(4 * (size_t)count + 6);
+    sig.push_back((uint64_t)count);
+    sig.push_back((uint64_t)(uintptr_t)dLog2Scale);
+    sig.push_back((uint64_t)fmt);
+    sig.push_back((uint64_t)p->tiny_max);
+    sig.push_back((uint64_t)p->persist);
+    sig.push_back((uint64_t)p->modp_tc);
+    for (int i = 0; i < count; ++i) {
+      sig.push_back((uint64_t)(uintptr_t)dA[i]);
+      sig.push_back((uint64_t)(uintptr_t)dOut[i]);
+      sig.push_back((uint64_t)N[i]);
+      sig.push_back(n[i]);
+    }
+    if (p->batch.exec && sig == p->batch.sig) {
+      CK(p, cudaGraphLaunch(p->batch.exec, s));
+      p->launches += p->batch.exec_kernels;
+      return MATPOW_OK;
+    }
+    if (p->batch.exec) {
+      cudaGraphExecDestroy(p->batch.exec);
+      p->batch.exec = nullptr;
+      p->batch.sig.clear();
+    }
+  }
 
   // ---- classify
   std::vector<TinyDesc> tiny;
@@ -156,22 +188,24 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   // ---- product descriptors per level; tensor-core levels get one launch per
   // tile width (64 columns for N <= 1024, 128 above)
   struct Launch {
-    int begin, count, tiles, bn;
+    int begin, count, tiles, bn, max_n, td;  // td: offset of the tile -> product table
   };
   int max_levels = 0;
   for (auto& b : big) max_levels = std::max(max_levels, (int)b.levels.size());
   std::vector<GemmDesc> gd;
   std::vector<std::vector<Launch>> lvl_launches(max_levels);
+  std::vector<int4> trec;  // persistent-kernel tile records of every launch
   const int passes[2] = {64, 128};
   for (int L = 0; L < max_levels; ++L) {
     for (int pi = 0; pi < (tc ? 2 : 1); ++pi) {
       const int bn = tc ? passes[pi] : 0;
-      int begin = (int)gd.size(), tiles = 0;
+      int begin = (int)gd.size(), tiles = 0, max_n = 0;
       for (size_t bi = 0; bi < big.size(); ++bi) {
         const Big& b = big[bi];
         if (L >= (int)b.levels.size()) continue;
         const int Ni = N[b.i];
         if (tc && tc_group_bn(Ni, nsl) != bn) continue;
+        max_n = std::max(max_n, Ni);
         const bool final_level = L + 1 == (int)b.levels.size();
         const LevelOps& lv = b.levels[L];
         for (size_t k = 0; k < lv.ops.size(); ++k) {
@@ -206,7 +240,11 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
           gd.push_back(d);
         }
       }
-      if ((int)gd.size() > begin) lvl_launches[L].push_back({begin, (int)gd.size() - begin, tiles, bn});
+      if ((int)gd.size() > begin) {
+        const int td = (int)trec.size();
+        if (tc && bn == 64) persist_tile_records(gd.data() + begin, (int)gd.size() - begin, nsl, &trec);
+        lvl_launches[L].push_back({begin, (int)gd.size() - begin, tiles, bn, max_n, td});
+      }
     }
   }
   // ---- TMA descriptors of every batch buffer (tensor-core levels), rebuilt
@@ -244,7 +282,8 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   size_t o_tiny = 0;
   size_t o_prep = align_up(o_tiny + tiny.size() * sizeof(TinyDesc), 256);
   size_t o_gd = align_up(o_prep + prep.size() * sizeof(PrepDesc), 256);
-  size_t total = std::max<size_t>(align_up(o_gd + gd.size() * sizeof(GemmDesc), 256), 256);
+  size_t o_td = align_up(o_gd + gd.size() * sizeof(GemmDesc), 256);
+  size_t total = std::max<size_t>(align_up(o_td + trec.size() * sizeof(int4), 256), 256);
   if ((st = grow(p, &p->batch.h_descs, &p->batch.h_desc_bytes, total, true))) return st;
   if ((st = grow(p, &p->batch.descs, &p->batch.desc_bytes, total, false))) return st;
   if (!p->batch.staged) CK(p, cudaEventCreateWithFlags(&p->batch.staged, cudaEventDisableTiming));
@@ -253,11 +292,15 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   if (!tiny.empty()) memcpy(h + o_tiny, tiny.data(), tiny.size() * sizeof(TinyDesc));
   if (!prep.empty()) memcpy(h + o_prep, prep.data(), prep.size() * sizeof(PrepDesc));
   if (!gd.empty()) memcpy(h + o_gd, gd.data(), gd.size() * sizeof(GemmDesc));
+  if (!trec.empty()) memcpy(h + o_td, trec.data(), trec.size() * sizeof(int4));
   CK(p, cudaMemcpyAsync(p->batch.descs, h, total, cudaMemcpyHostToDevice, s));
   CK(p, cudaEventRecord(p->batch.staged, s));
   char* dd = (char*)p->batch.descs;
+  // ---- enqueue: directly, or captured once into a graph that later calls
+  // with the same signature replay (the tables uploaded above stay valid
+  // until a call with another signature rebuilds them)
+  auto enqueue = [&](cudaStream_t s) -> matpow_status {
   cudaEvent_t ev;
-  // ---- enqueue
   if (!tiny.empty()) {
     double flop = 0;
     for (auto& t : tiny) flop += 2.0 * t.N * (double)t.N * t.N * matpow_gemm_count(t.n);
@@ -288,7 +331,8 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
       }
       timed_begin(p, s, &ev);
       if (tc) {
-        if ((st = tc_launch_group_bn(p, g, la.count, la.tiles, p->batch.maps, la.bn, p->batch.scales,
+        if ((st = tc_launch_group_bn(p, g, la.count, la.tiles, (const int4*)(dd + o_td) + la.td,
+                                     p->batch.maps, la.bn, la.max_n, p->batch.scales,
                                      p->status, s)))
           return st;
         timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
@@ -299,5 +343,29 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
       p->launches++;
     }
   }
+  return MATPOW_OK;
+  };
+  if (!graphable) return enqueue(s);
+  const int64_t before = p->launches;
+  CK(p, cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+  matpow_status st2 = enqueue(p->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(p->cap_stream, &graph);
+  if (st2 != MATPOW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    p->launches = before;
+    return st2;
+  }
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaGraphInstantiate");
+  p->batch.exec = exec;
+  p->batch.exec_kernels = p->launches - before;
+  p->batch.sig.swap(sig);
+  p->launches = before;
+  CK(p, cudaGraphLaunch(exec, s));
+  p->launches += p->batch.exec_kernels;
   return MATPOW_OK;
 }

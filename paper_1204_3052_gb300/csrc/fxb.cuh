@@ -88,15 +88,14 @@ __device__ __forceinline__ void epi_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
 }
 
-// Epilogue warps 4..7 (q = warp - 4 owns rows 32q..32q+31 of the 128-row
-// tile; rows 64h..64h+63 form block row h = q / 2).  T holds this thread's
-// row `row` of the tile, columns n0..n0+BN-1.  Computes each 64 x 64 block's
-// maximum over the warp pair, writes the block exponents, the two slice
-// planes and folds the block maxima into the matrix maximum (*maxbits).
-// red: shared scratch of 4 * (BN / 64) floats.
-// (WC columns per epilogue warp starting at n0; NT epilogue threads share
-// named barrier 1; red is this column slice's 4 x (WC / 64) scratch.)
-template <int BN, int NT = 128>
+// Epilogue warps (q = warp % 4 owns rows 32q..32q+31 of the 128-row tile;
+// rows 64h..64h+63 form block row h = q / 2).  T holds this thread's row `row`
+// of the tile, columns n0..n0+BN-1.  Computes each 64 x 64 block's maximum
+// over the warp pair, writes the block exponents and the NSL slice planes
+// with plain global stores (a1p: first plane, the next at + plane elements)
+// and folds the block maxima into the matrix maximum (*maxbits).  NT epilogue
+// threads share named barrier 1; red: shared scratch of 4 * (BN / 64) floats.
+template <int BN, int NT = 128, int NSL = 2>
 __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int m0, int n0, int q,
                                              int lane, int N, int ld, __nv_bfloat16* a1p,
                                              long long plane, int* bexp, unsigned* maxbits,
@@ -123,35 +122,29 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
       if (bm > 0.f) atomicMax(maxbits, __float_as_uint(bm));
     }
     if (row < N) {
+      // 16-byte groups of 8 columns; a group that starts below N ends within
+      // the row's padding to ld (a multiple of 8), which no product reads, and
+      // its columns past N hold exact zeros (zero-filled operands)
       const int c0 = n0 + BLK * g;
       __nv_bfloat16* p1 = a1p + (size_t)row * ld + c0;
-      __nv_bfloat16* p2 = p1 + plane;
-      if (c0 + BLK <= N) {
 #pragma unroll
-        for (int g8 = 0; g8 < BLK / 8; ++g8) {
-          uint32_t hw[4], lw[4];
+      for (int g8 = 0; g8 < BLK / 8; ++g8) {
+        if (c0 + 8 * g8 < N) {
+          uint32_t w[NSL][4];
 #pragma unroll
           for (int h = 0; h < 4; ++h) {
-            float h0, l0, h1, l1;
-            slice(T[BLK * g + 8 * g8 + 2 * h], e, &h0, &l0);
-            slice(T[BLK * g + 8 * g8 + 2 * h + 1], e, &h1, &l1);
-            __nv_bfloat162 hi = __floats2bfloat162_rn(h0, h1);
-            __nv_bfloat162 lo = __floats2bfloat162_rn(l0, l1);
-            hw[h] = *reinterpret_cast<uint32_t*>(&hi);
-            lw[h] = *reinterpret_cast<uint32_t*>(&lo);
-          }
-          *reinterpret_cast<uint4*>(p1 + 8 * g8) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(p2 + 8 * g8) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-      } else {
+            float x0[NSL], x1[NSL];
+            slice_n<NSL>(T[BLK * g + 8 * g8 + 2 * h], e, x0);
+            slice_n<NSL>(T[BLK * g + 8 * g8 + 2 * h + 1], e, x1);
 #pragma unroll
-        for (int j = 0; j < BLK; ++j) {
-          if (c0 + j < N) {
-            float h, l;
-            slice(T[BLK * g + j], e, &h, &l);
-            p1[j] = __float2bfloat16_rn(h);
-            p2[j] = __float2bfloat16_rn(l);
+            for (int k = 0; k < NSL; ++k) {
+              __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
+              w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+            }
           }
+#pragma unroll
+          for (int k = 0; k < NSL; ++k)
+            *reinterpret_cast<uint4*>(p1 + k * plane + 8 * g8) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
         }
       }
     }

@@ -1,0 +1,409 @@
+// Persistent grouped level launch for the exact splits (64-column tiles,
+// orders up to 4096): one CTA per SM walks the level's whole tile list
+// (tiles b, b + G, b + 2G, ... of every product in the device table), so the
+// per-CTA set-up (barriers, TMEM allocation, descriptor prefetch) is paid once
+// per SM instead of once per tile, and the epilogue of one tile (fold, block
+// maxima, re-split, stores) overlaps the loads and MMAs of the next:
+//
+//   warp 0  TMA producer over the ring (runs ahead across tile boundaries)
+//   warp 1  tcgen05.mma issuer; NBUF k-block accumulator sets in TMEM
+//   warp 2  TMEM owner
+//   warp 3  stages the block exponents and record of the next four tiles
+//           (one per group of 8 lanes), so the epilogue never waits on a
+//           global load to start a tile
+//
+// The host gives one 16-byte record per tile (product, depth, origin, the
+// two tensor-map indices), so the producer and MMA warps read one record
+// per tile and prefetch the next.
+//   warps 4-7  fold finished k-blocks into float32 registers, then write the
+//           next operand's slices with plain global stores (no staging in
+//           the ring, which the next tile is already filling)
+//
+// The arithmetic per tile is that of tc_fxb_group_kernel: the same k-block
+// order, the same fold, the same slicing, so the results are bit-for-bit the
+// same.  Every wait is bounded; an abort drains copies and MMAs, frees TMEM
+// and reports MATPOW_ETIMEDOUT through the status word.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "fxb.cuh"
+#include "internal.cuh"
+#include "plan.h"
+#include "tc_ptx.cuh"
+
+#include <vector>
+
+namespace mp {
+namespace persist {
+
+constexpr int BM = 128, BN = 64, BK = 64, THREADS = 256;
+constexpr int KB_MAX = 64;  // N <= 4096
+constexpr int EXPB = 4;     // tiles staged ahead by warp 3 (one per group of 8 lanes)
+constexpr uint64_t WAIT_NS = 2000000000ull;
+
+
+// Per-tile record staged by warp 3 for the epilogue: product index, k-blocks,
+// origin, operand scale exponents, output exponent.
+struct TileInfo {
+  int di, KB, m0, n0, sx, sy;
+  long long Ec;
+};
+
+template <int NSL>
+struct Cfg {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = NSL * (A_BYTES + B_BYTES);
+  static constexpr int RING = NSL == 3 ? 216 * 1024 : 192 * 1024;
+  static constexpr int STAGES = RING / STAGE_BYTES;
+  // accumulator sets (NSL x 64 columns each) that fit 512 TMEM columns
+  static constexpr int NBUF = NSL == 3 ? 2 : 4;
+  static constexpr int TMEM_COLS = 512;
+  // barriers: full[S], empty[S], accfull[NBUF], accempty[NBUF], expfull[EXPB],
+  // expempty[EXPB], drain; then tmem slot, abort flag, epilogue verdict
+  static constexpr int NBARS = 2 * STAGES + 2 * NBUF + 2 * EXPB + 1;
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int EXP_INTS = 3 * KB_MAX;  // eA (2 block rows) + eB (1 block column)
+  static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + BAR_BYTES + EXPB * EXP_INTS * 4 + 64 +
+                              EXPB * (int)sizeof(TileInfo);
+  static_assert(NBARS * 8 + 16 <= BAR_BYTES, "barrier area");
+  static_assert(STAGES >= 2, "ring");
+  static_assert(NBUF * NSL * BN <= TMEM_COLS, "TMEM");
+};
+
+}  // namespace persist
+
+template <int NSL>
+__global__ void __launch_bounds__(persist::THREADS, 1)
+    tc_fxb_persist_kernel(const GemmDesc* __restrict__ descs, int tiles_total,
+                          const int4* __restrict__ recs, const CUtensorMap* __restrict__ maps,
+                          Scale* scales, unsigned* status) {
+  using namespace persist;
+  using C = Cfg<NSL>;
+  constexpr int STAGES = C::STAGES, NBUF = C::NBUF;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + C::NBARS);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  volatile int* epi_ok = (volatile int*)(tmem_slot + 2);
+  int* expbuf = (int*)((uint8_t*)bars + C::BAR_BYTES);  // [EXPB][EXP_INTS]
+  float* red = (float*)(expbuf + EXPB * C::EXP_INTS);   // 4 floats (16 slots)
+  TileInfo* info = (TileInfo*)(red + 16);                // [EXPB]
+  const uint32_t full0 = ptx::smem_u32(bars);
+  const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
+  const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
+  const uint32_t accempty0 = ptx::smem_u32(bars + 2 * STAGES + NBUF);
+  const uint32_t expfull0 = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF);
+  const uint32_t expempty0 = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF + EXPB);
+  const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF + 2 * EXPB);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(full0 + 8 * s, 1);
+      ptx::mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < NBUF; ++b) {
+      ptx::mbar_init(accfull0 + 8 * b, 1);
+      ptx::mbar_init(accempty0 + 8 * b, 4);  // one arrival per epilogue warp
+    }
+    for (int b = 0; b < EXPB; ++b) {
+      ptx::mbar_init(expfull0 + 8 * b, 8);     // the 8 lanes of one group of warp 3
+      ptx::mbar_init(expempty0 + 8 * b, 128);  // every epilogue thread
+    }
+    ptx::mbar_init(drainb, 1);
+    *abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // recs[t] = {product | k-blocks << 24, m0 | n0 << 16, A map, B map}
+  int gk = 0;  // k-blocks handled by this role so far (ring / accumulator phases)
+  if (warp == 0) {
+    if (lane == 0) {
+      int4 r = blockIdx.x < tiles_total ? recs[blockIdx.x] : make_int4(0, 0, 0, 0);
+      if (blockIdx.x < tiles_total) {
+#pragma unroll
+        for (int k = 0; k < NSL; ++k) {
+          ptx::prefetch_tmap(maps + r.z + k);
+          ptx::prefetch_tmap(maps + r.w + k);
+        }
+      }
+      for (int tb = blockIdx.x; tb < tiles_total && !*abort_flag; tb += G) {
+        // the next tile's record, loaded while this tile's copies are issued
+        const int4 rn = tb + G < tiles_total ? recs[tb + G] : make_int4(0, 0, 0, 0);
+        const int KB = r.x >> 24;
+        const int m0 = r.y & 0xFFFF, n0 = r.y >> 16;
+        const CUtensorMap* ax = maps + r.z;
+        const CUtensorMap* by = maps + r.w;
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb, ++gk) {
+          const int s = gk % STAGES;
+          if (!ptx::mbar_wait(empty0 + 8 * s, ((gk / STAGES) & 1) ^ 1, abort_flag, WAIT_NS)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * s;
+          ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
+          const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
+          const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
+#pragma unroll
+          for (int k = 0; k < NSL; ++k) ptx::tma_load_2d(base + k * C::A_BYTES, ax + k, kx, m0, fb);
+          const uint32_t bbase = base + NSL * C::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < NSL; ++k) ptx::tma_load_2d(bbase + k * C::B_BYTES, by + k, n0, kx, fb);
+        }
+        if (!ok) break;
+        if (rn.z != r.z || rn.w != r.w) {
+#pragma unroll
+          for (int k = 0; k < NSL; ++k) {
+            ptx::prefetch_tmap(maps + rn.z + k);
+            ptx::prefetch_tmap(maps + rn.w + k);
+          }
+        }
+        r = rn;
+      }
+      // no copy may still be in flight when the CTA ends
+      for (int g = gk - STAGES < 0 ? 0 : gk - STAGES; g < gk; ++g) {
+        int dummy = 0;
+        ptx::mbar_wait(full0 + 8 * (g % STAGES), (g / STAGES) & 1, &dummy, WAIT_NS);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int KB = blockIdx.x < tiles_total ? recs[blockIdx.x].x >> 24 : 0;
+      for (int tb = blockIdx.x; tb < tiles_total && !*abort_flag; tb += G) {
+        // the next tile's depth, loaded while this tile's MMAs are issued
+        const int KBn = tb + G < tiles_total ? recs[tb + G].x >> 24 : 0;
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb, ++gk) {
+          const int buf = gk % NBUF;
+          const uint32_t t0 = tmem + (uint32_t)(buf * NSL * BN);
+          if (!ptx::mbar_wait(accempty0 + 8 * buf, ((gk / NBUF) & 1) ^ 1, abort_flag, WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          const int s = gk % STAGES;
+          if (!ptx::mbar_wait(full0 + 8 * s, (gk / STAGES) & 1, abort_flag, WAIT_NS)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t a0 = ptx::smem_u32(smem + s * C::STAGE_BYTES);
+          const uint32_t b0 = a0 + NSL * C::A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            uint64_t ad[NSL], bd[NSL];
+#pragma unroll
+            for (int i = 0; i < NSL; ++i) {
+              ad[i] = ptx::smem_desc(a0 + i * C::A_BYTES + 32 * k, 16, 1024);
+              bd[i] = ptx::smem_desc(b0 + i * C::B_BYTES + 2048 * k, 8192, 1024);
+            }
+            const uint32_t acc = k == 0 ? 0u : 1u;
+            // accumulator w collects the products a_i b_j with i + j = w
+            ptx::mma_f16(t0, ad[0], bd[0], idesc, acc);
+            ptx::mma_f16(t0 + BN, ad[0], bd[1], idesc, acc);
+            ptx::mma_f16(t0 + BN, ad[1], bd[0], idesc, 1);
+            if (NSL == 3) {
+              ptx::mma_f16(t0 + 2 * BN, ad[0], bd[NSL - 1], idesc, acc);
+              ptx::mma_f16(t0 + 2 * BN, ad[1], bd[1], idesc, 1);
+              ptx::mma_f16(t0 + 2 * BN, ad[NSL - 1], bd[0], idesc, 1);
+            }
+          }
+          ptx::mma_commit(empty0 + 8 * s);
+          ptx::mma_commit(accfull0 + 8 * buf);
+        }
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        KB = KBn;
+      }
+      ptx::mma_commit(drainb);
+      int dummy = 0;
+      ptx::mbar_wait(drainb, 0, &dummy, WAIT_NS);
+    }
+  } else if (warp == 3) {
+    // four groups of 8 lanes; group g stages the CTA's tiles g, g + 4, ...
+    // (block exponents and the tile's record) into buffer (tile index) % 4,
+    // so the dependent global loads of four tiles are in flight at once
+    const int grp = lane >> 3, gl = lane & 7;
+    for (int lt = grp;; lt += EXPB) {
+      const int tb = blockIdx.x + lt * G;
+      if (tb >= tiles_total || *abort_flag) break;
+      const int4 r = recs[tb];
+      const int di = r.x & 0xFFFFFF, KB = r.x >> 24;
+      const int m0 = r.y & 0xFFFF, n0 = r.y >> 16;
+      const GemmDesc& d = descs[di];
+      const int e = lt & (EXPB - 1);
+      if (!ptx::mbar_wait(expempty0 + 8 * e, ((lt / EXPB) & 1) ^ 1, abort_flag, WAIT_NS)) {
+        *abort_flag = 1;
+        break;
+      }
+      const int N = d.N;
+      const int nb = fxb::nblocks(N);
+      const size_t boff = fxb::bexp_offset(N, d.ld, NSL);
+      const int* bx = (const int*)((const char*)d.X + boff);
+      const int* byx = (const int*)((const char*)d.Y + boff);
+      int* eA = expbuf + e * C::EXP_INTS;
+      int* eB = eA + 2 * KB_MAX;
+      const int I0 = m0 / fxb::BLK, J0 = n0 / fxb::BLK;
+      for (int i = gl; i < 2 * KB; i += 8) {
+        const int hh = i / KB, kb = i - hh * KB;
+        eA[i] = (I0 + hh < nb) ? __ldcg(bx + (I0 + hh) * nb + kb) : 0;
+      }
+      for (int kb = gl; kb < KB; kb += 8) eB[kb] = (J0 < nb) ? __ldcg(byx + kb * nb + J0) : 0;
+      if (gl == 0) {
+        TileInfo ti;
+        ti.di = di;
+        ti.KB = KB;
+        ti.m0 = m0;
+        ti.n0 = n0;
+        ti.sx = scale_exp_from_bits(scales[d.sx].maxbits);
+        ti.sy = scale_exp_from_bits(scales[d.sy].maxbits);
+        ti.Ec = scales[d.sx].E + scales[d.sy].E + ti.sx + ti.sy;
+        info[e] = ti;
+      }
+      ptx::mbar_arrive(expfull0 + 8 * e);  // release: this lane's writes are visible
+    }
+  } else if (warp >= 4) {
+    const int q = warp - 4;
+    const int h = q >> 1;
+    float T[BN];
+    for (int lt = 0;; ++lt) {
+      const int tb = blockIdx.x + lt * G;
+      if (tb >= tiles_total) break;
+      const int e = lt & (EXPB - 1);
+      bool ok = true;
+      int dummy = 0;
+      if (!ptx::mbar_wait(expfull0 + 8 * e, (lt / EXPB) & 1, &dummy, 2 * WAIT_NS)) ok = false;
+      const TileInfo ti = info[e];
+      const int KB = ok ? ti.KB : 0;
+      // the store phase's fields, loaded now and used after the fold (a
+      // record that never arrived is not dereferenced)
+      const GemmDesc& d = descs[ok ? ti.di : 0];
+      const int N = d.N, ld = d.ld, mode = d.mode, sc = d.sc;
+      const long long plane = d.plane;
+      void* Cp = d.C;
+      void* outp = d.out;
+      long long* out_log2 = d.out_log2;
+      const int row = ti.m0 + 32 * q + lane;
+      const int* eA = expbuf + e * C::EXP_INTS;
+      const int* eB = eA + 2 * KB_MAX;
+#pragma unroll
+      for (int j = 0; j < BN; ++j) T[j] = 0.f;
+      for (int kb = 0; kb < KB; ++kb, ++gk) {
+        const int buf = gk % NBUF;
+        if (!ptx::mbar_wait(accfull0 + 8 * buf, (gk / NBUF) & 1, &dummy, 2 * WAIT_NS)) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const int kr = fxb::rot_kb(kb, KB, (ti.m0 + ti.n0) / 128);
+        float fac[1];
+        fac[0] = fxb::pow2f(eA[h * KB + kr] + eB[kr] - 16 - ti.sx - ti.sy);
+        fxb::fold<BN, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN), fac, BN);
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
+      }
+      ptx::mbar_arrive(expempty0 + 8 * e);  // this tile's exponents and record are no longer read
+      // one verdict for the four epilogue warps (they share named barrier 1)
+      fxb::epi_bar<128>();
+      if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
+      fxb::epi_bar<128>();
+      if (!*epi_ok) {
+        *abort_flag = 1;
+        break;
+      }
+      const bool first = ti.m0 == 0 && ti.n0 == 0;  // tile 0 of its product
+      if (mode == OUT_INTERNAL) {
+        if (first && q == 0 && lane == 0) scales[sc].E = ti.Ec;
+        fxb::store_slices<BN, 128, NSL>(T, row, ti.m0, ti.n0, q, lane, N, ld, (__nv_bfloat16*)Cp, plane,
+                                        (int*)((char*)Cp + fxb::bexp_offset(N, ld, NSL)),
+                                        &scales[sc].maxbits, red);
+      } else {
+        if (first && q == 0 && lane == 0 && mode == OUT_USER_MANT && out_log2) *out_log2 = ti.Ec;
+        if (row < N) {
+          float* O = (float*)outp + (size_t)row * N;
+          const bool mant = mode == OUT_USER_MANT;
+#pragma unroll
+          for (int j = 0; j < BN; ++j)
+            if (!mant) T[j] = final_value(T[j], ti.Ec, status);
+          if ((N & 3) == 0 && ((uintptr_t)outp & 15) == 0) {  // rows start on 16 bytes: float4 stores
+#pragma unroll
+            for (int j = 0; j < BN; j += 4)
+              if (ti.n0 + j < N)
+                *reinterpret_cast<float4*>(O + ti.n0 + j) = make_float4(T[j], T[j + 1], T[j + 2], T[j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < BN; ++j)
+              if (ti.n0 + j < N) O[ti.n0 + j] = T[j];
+          }
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, Cfg<NSL>::TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+cudaError_t tc_persist_init() {
+  cudaError_t e = cudaFuncSetAttribute(tc_fxb_persist_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       persist::Cfg<2>::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_fxb_persist_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             persist::Cfg<3>::SMEM);
+  return e;
+}
+
+void persist_tile_records(const GemmDesc* descs, int count, int nsl, std::vector<int4>* out) {
+  for (int k = 0; k < count; ++k) {
+    const GemmDesc& d = descs[k];
+    const int tiles_m = (d.N + persist::BM - 1) / persist::BM;
+    const int KB = (d.N + persist::BK - 1) / persist::BK;
+    for (int t = 0; t < tiles_m * d.tiles_n; ++t) {
+      int tm, tn;
+      tile_raster(t, tiles_m, d.tiles_n, &tm, &tn);
+      out->push_back(make_int4(k | (KB << 24), (tm * persist::BM) | ((tn * persist::BN) << 16), d.map_x,
+                               d.map_y + nsl));
+    }
+  }
+}
+
+cudaError_t launch_fxb_persist(const GemmDesc* d_descs, int tiles, const int4* d_tile_rec,
+                               const void* d_maps, int nsl, int num_sms, Scale* scales, unsigned* status,
+                               cudaStream_t s) {
+  const int grid = tiles < num_sms ? tiles : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  const CUtensorMap* maps = (const CUtensorMap*)d_maps;
+  if (nsl == 3)
+    tc_fxb_persist_kernel<3><<<grid, persist::THREADS, persist::Cfg<3>::SMEM, s>>>(
+        d_descs, tiles, d_tile_rec, maps, scales, status);
+  else
+    tc_fxb_persist_kernel<2><<<grid, persist::THREADS, persist::Cfg<2>::SMEM, s>>>(
+        d_descs, tiles, d_tile_rec, maps, scales, status);
+  return cudaGetLastError();
+}
+
+}  // namespace mp

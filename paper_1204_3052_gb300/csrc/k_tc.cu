@@ -597,7 +597,7 @@ cudaError_t tc_init(matpow_plan_s*) {
   MP_FXB_ATTR(tc_fxb_group_kernel, 128, 2)
   MP_FXB_ATTR(tc_fxb_group_kernel, 64, 3)
 #undef MP_FXB_ATTR
-  return cudaSuccess;
+  return tc_persist_init();
 }
 
 void tc_free(matpow_plan_s*) {}
@@ -693,13 +693,12 @@ matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s
   return MATPOW_OK;
 }
 
-matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
-                              Scale* scales, cudaStream_t s) {
-  return tc_launch_group_bn(p, d_descs, count, tiles, p->batch.maps, p->group_bn, scales, p->status, s);
-}
 
-cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
-                             int bn, int nsl, Scale* scales, unsigned* status, cudaStream_t s) {
+cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const int4* d_tile_rec,
+                             const void* d_maps, int bn, int nsl, int max_n, int num_sms, bool persist,
+                             Scale* scales, unsigned* status, cudaStream_t s) {
+  if (persist && d_tile_rec && bn == 64 && max_n <= 4096 && num_sms > 0)
+    return launch_fxb_persist(d_descs, tiles, d_tile_rec, d_maps, nsl, num_sms, scales, status, s);
   const CUtensorMap* maps = (const CUtensorMap*)d_maps;
   if (nsl == 3)
     tc_fxb_group_kernel<64, 3><<<tiles, fx::Cfg<64, 3>::THREADS, fx::Cfg<64, 3>::SMEM, s>>>(
@@ -714,12 +713,13 @@ cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, cons
 }
 
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
-                                 const void* d_maps, int bn, Scale* scales, unsigned* status,
-                                 cudaStream_t s) {
+                                 const int4* d_tile_rec, const void* d_maps, int bn, int max_n,
+                                 Scale* scales, unsigned* status, cudaStream_t s) {
   const int fmt = plan_float_fmt(p);
   if (!fmt_exact(fmt))
     return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches need the exact split");
-  cudaError_t e = launch_fxb_group(d_descs, count, tiles, d_maps, bn, fmt_slices(fmt), scales, status, s);
+  cudaError_t e = launch_fxb_group(d_descs, count, tiles, d_tile_rec, d_maps, bn, fmt_slices(fmt), max_n,
+                                   p->num_sms, p->persist, scales, status, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "tc_fxb_group_kernel launch");
   return MATPOW_OK;
 }

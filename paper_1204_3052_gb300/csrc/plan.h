@@ -69,6 +69,11 @@ struct BatchState {
   std::vector<CUtensorMap> h_maps;  // host copy; rebuilt when the layout changes
   std::vector<std::pair<const void*, int>> map_keys;  // (buffer, N) per 4 descriptors
   cudaEvent_t staged = nullptr; // the last upload from h_descs has been consumed
+  // the last call captured as a CUDA graph: replayed while the call's
+  // signature (pointers, orders, powers, options) is unchanged
+  std::vector<uint64_t> sig;
+  cudaGraphExec_t exec = nullptr;
+  int64_t exec_kernels = 0;
 };
 
 }  // namespace mp
@@ -95,7 +100,7 @@ struct matpow_plan_s {
   int split_mode = 0;  // BF16X3: 0 exact fixed-point slices, 1 floating hi/lo planes
   int chain_mode = 1;  // whole-chain kernel: 0 off, 1 with split-K where it fits, 2 without
   bool modp_tc = true;    // mod-p products on the tensor cores (64 < N <= 16384)
-  int group_bn = 64;      // tile width of the current grouped tensor-core launch
+  bool persist = true;    // batched 64-column levels: persistent grouped kernel
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
   // graphs
   std::vector<mp::GraphEntry> graphs;
@@ -141,15 +146,28 @@ int tc_modp_tile_n();
 cudaError_t launch_prep_modp_slices(const unsigned* A, int N, unsigned p, void* dst,
                                     unsigned* status, cudaStream_t s);
 matpow_status tc_modp_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s);
-matpow_status tc_launch_group(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
-                              Scale* scales, cudaStream_t s);
+// Grouped exact-split level launch of the plan's batch (max_n: largest order
+// among the products).
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
-                                 const void* d_maps, int bn, Scale* scales, unsigned* status,
-                                 cudaStream_t s);
+                                 const int4* d_tile_rec, const void* d_maps, int bn, int max_n,
+                                 Scale* scales, unsigned* status, cudaStream_t s);
 int tc_group_bn(int N, int nsl = 2);  // tile width of grouped launches for order N
-// Plan-free grouped exact-split launch (descriptor and TMA tables on the device).
-cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
-                             int bn, int nsl, Scale* scales, unsigned* status, cudaStream_t s);
+// Plan-free grouped exact-split launch (descriptor and TMA tables on the
+// device): the persistent kernel (one CTA per SM over the whole tile list;
+// d_tile_desc[t] = index of the product owning tile t | its k-blocks << 24)
+// for 64-column tiles
+// and orders up to 4096 when `persist` is set and the table is given, else
+// one CTA per tile.
+cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, const int4* d_tile_rec,
+                             const void* d_maps, int bn, int nsl, int max_n, int num_sms, bool persist,
+                             Scale* scales, unsigned* status, cudaStream_t s);
+cudaError_t tc_persist_init();
+// Per-tile records of a 64-column grouped level, in tile order: {product
+// index | k-blocks << 24, m0 | n0 << 16, A-role map index, B-role map index}.
+void persist_tile_records(const GemmDesc* descs, int count, int nsl, std::vector<int4>* out);
+cudaError_t launch_fxb_persist(const GemmDesc* d_descs, int tiles, const int4* d_tile_rec,
+                               const void* d_maps, int nsl, int num_sms, Scale* scales, unsigned* status,
+                               cudaStream_t s);
 // The 2 nsl TMA descriptors of one block-scaled buffer (A-role slices, then B-role).
 bool tc_encode_buffer_maps(CUtensorMap* m, const void* base, int N, int nsl);
 }  // namespace mp

@@ -103,6 +103,7 @@ struct Req {
 struct matpow_server_s {
   matpow_server_desc desc{};
   int fmt = FMT_F32;  // FMT_FX2 / FMT_FX3: float levels on the tensor cores (exact split)
+  int num_sms = 0;
   CUtensorMap* d_maps = nullptr;  // 24 TMA descriptors per slot chunk (4 buffers x 2 x 3)
   CUtensorMap* h_maps = nullptr;  // pinned host copy
   cudaStream_t stream = nullptr;
@@ -182,7 +183,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   std::vector<TinyDesc> tiny;
   std::vector<PrepDesc> prep;
   std::vector<GemmDesc> gf, gw, gm;  // float (64-wide tiles), float (128-wide), mod p
-  int tiles_f = 0, tiles_w = 0, tiles_m = 0;
+  int tiles_f = 0, tiles_w = 0, tiles_m = 0, maxn_f = 0;
   std::vector<Req*> modp_prep;
   for (Req* q : act) {
     if (q->state != 1) continue;
@@ -273,6 +274,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
           if (d.bn == 64) {
             d.tile_begin = tiles_f;
             tiles_f += nt;
+            maxn_f = std::max(maxn_f, r.N);
             gf.push_back(d);
           } else {
             d.tile_begin = tiles_w;
@@ -320,7 +322,11 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   const size_t o_f = align256(o_p + prep.size() * sizeof(PrepDesc));
   const size_t o_w = align256(o_f + gf.size() * sizeof(GemmDesc));
   const size_t o_m = align256(o_w + gw.size() * sizeof(GemmDesc));
-  const size_t total = std::max<size_t>(align256(o_m + gm.size() * sizeof(GemmDesc)), 256);
+  // tile records of the 64-column float group (persistent kernel)
+  std::vector<int4> trec;
+  if (fmt_exact(s->fmt)) persist_tile_records(gf.data(), (int)gf.size(), fmt_slices(s->fmt), &trec);
+  const size_t o_td = align256(o_m + gm.size() * sizeof(GemmDesc));
+  const size_t total = std::max<size_t>(align256(o_td + trec.size() * sizeof(int4)), 256);
   if (!ensure_tab(s, total)) return fail(nullptr, MATPOW_ENOMEM, "server: descriptor table");
   const int ti = s->tab_i;
   s->tab_i ^= 1;
@@ -332,6 +338,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   if (!gf.empty()) memcpy(h + o_f, gf.data(), gf.size() * sizeof(GemmDesc));
   if (!gw.empty()) memcpy(h + o_w, gw.data(), gw.size() * sizeof(GemmDesc));
   if (!gm.empty()) memcpy(h + o_m, gm.data(), gm.size() * sizeof(GemmDesc));
+  if (!trec.empty()) memcpy(h + o_td, trec.data(), trec.size() * sizeof(int4));
   cudaError_t e = cudaMemcpyAsync(dd, h, total, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: upload");
   if (!s->tab_ev[ti]) cudaEventCreateWithFlags(&s->tab_ev[ti], cudaEventDisableTiming);
@@ -364,16 +371,17 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   }
   if (!gf.empty()) {
     if (fmt_exact(s->fmt))
-      e = launch_fxb_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->d_maps, 64,
-                           fmt_slices(s->fmt), s->scales, st0, s->stream);
+      e = launch_fxb_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, (const int4*)(dd + o_td),
+                           s->d_maps, 64, fmt_slices(s->fmt), maxn_f, s->num_sms, true, s->scales, st0,
+                           s->stream);
     else
       e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->scales, st0,
                             s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
   }
   if (!gw.empty()) {
-    e = launch_fxb_group((const GemmDesc*)(dd + o_w), (int)gw.size(), tiles_w, s->d_maps, 128,
-                         fmt_slices(s->fmt), s->scales, st0, s->stream);
+    e = launch_fxb_group((const GemmDesc*)(dd + o_w), (int)gw.size(), tiles_w, nullptr, s->d_maps, 128,
+                         fmt_slices(s->fmt), 0, s->num_sms, false, s->scales, st0, s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
   }
   if (!gm.empty()) {
@@ -528,8 +536,9 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   auto* s = new (std::nothrow) matpow_server_s();
   if (!s) return fail(nullptr, MATPOW_ENOMEM, "matpow_server_create: host allocation");
   s->desc = *d;
-  // grouped float levels: the exact-split tensor-core kernels for MATPOW_BF16X3,
-  // the float32 SIMT kernels otherwise
+  s->num_sms = prop.multiProcessorCount;
+  // grouped float levels: the exact-split tensor-core kernels for MATPOW_BF16X3
+  // and MATPOW_BF16X6, the float32 SIMT kernels otherwise
   s->fmt = d->precision == MATPOW_BF16X3 ? FMT_FX2 : d->precision == MATPOW_BF16X6 ? FMT_FX3 : FMT_F32;
   int prev = 0;
   cudaGetDevice(&prev);

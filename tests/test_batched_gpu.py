@@ -76,3 +76,63 @@ def test_batch_with_wide_tiles(prec):
             err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
             assert err <= gate(n, floor_for(prec, A, n, M, e))
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_persistent_levels_equal_per_tile_levels(prec):
+    # the persistent grouped kernel (one CTA per SM over the whole tile list,
+    # many tiles per CTA here) does each tile's arithmetic in the same order as
+    # the one-CTA-per-tile kernel: identical bits
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    bd = wl.batched_draw(count=600, seed=9, n_max=5000)
+    Ns = [max(int(N), 65) for N in bd.Ns]  # every matrix on the tensor-core path
+    ns = [int(x) for x in bd.ns]
+    As = [wl.gaussian(N, int(s)) for N, s in zip(Ns, bd.seeds)]
+    dAs = [to_dev(a) for a in As]
+    res = {}
+    for persist in (1, 0):
+        plan = mpw.Plan(256, prec)
+        plan.set_option(mpw.OPT_PERSIST, persist)
+        lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
+        outs = plan.batched(dAs, ns, log2=lg)
+        plan.check()
+        res[persist] = ([o.clone() for o in outs], lg.clone())
+        plan.close()
+    for a, b in zip(res[1][0], res[0][0]):
+        assert torch.equal(a, b)
+    assert torch.equal(res[1][1], res[0][1])
+    # and a few against the oracle
+    for i in range(0, len(As), 97):
+        M, e, _ = oracle.matpow_f64(As[i], ns[i])
+        err = oracle.rel_frobenius(res[1][0][i].cpu().numpy(), int(res[1][1][i].item()), M, e)
+        assert err <= gate(ns[i], floor_for(prec, As[i], ns[i], M, e)), (i, Ns[i], ns[i], err)
+
+
+def test_batched_graph_replay_follows_new_contents():
+    # the second call with the same pointers, orders and powers replays the
+    # captured graph; it must read the matrices' current contents
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    Ns = [96, 40, 200, 130]
+    ns = [5, 17, 2, 1000]
+    plan = mpw.Plan(256, "bf16x6")
+    ref = mpw.Plan(256, "bf16x6")
+    ref.set_option(mpw.OPT_GRAPHS, 0)
+    dAs = [to_dev(wl.gaussian(N, 50 + i)) for i, N in enumerate(Ns)]
+    lg = torch.zeros(len(Ns), dtype=torch.int64, device="cuda")
+    lr = torch.zeros(len(Ns), dtype=torch.int64, device="cuda")
+    outs = [torch.empty_like(a) for a in dAs]
+    want = [torch.empty_like(a) for a in dAs]
+    for rnd in range(3):
+        for i, N in enumerate(Ns):
+            dAs[i].copy_(to_dev(wl.gaussian(N, 100 * rnd + i)))
+        plan.batched(dAs, ns, outs=outs, log2=lg)
+        ref.batched(dAs, ns, outs=want, log2=lr)
+        plan.check()
+        ref.check()
+        for a, b in zip(outs, want):
+            assert torch.equal(a, b), rnd
+        assert torch.equal(lg, lr)
+    plan.close()
+    ref.close()
