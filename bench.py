@@ -496,7 +496,8 @@ def run_ours(args, wk, world, rank, local):
         peak = peaks["bf16_tflops"]
         exact = prec in ("bf16x3", "bf16x6")
         chain_max = 768 if prec == "bf16x6" else 1024
-        kname = ("tc_chain_kernel" if exact and 64 < N <= chain_max else
+        kname = (("tc_chain_split_kernel (split-K clusters) or tc_chain_kernel" if args.chain_mode == 1
+                  else "tc_chain_kernel") if exact and 64 < N <= chain_max and args.chain_mode else
                  "tc_fxb_kernel" if exact else "tc_gemm_kernel")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,

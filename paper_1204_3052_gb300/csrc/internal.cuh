@@ -131,6 +131,29 @@ __device__ __forceinline__ float final_value(float s, long long E, unsigned* sta
   return f;
 }
 
+// One thread's row of a final float32 result: columns c0 .. c0 + W - 1 of
+// row O (clipped at N), as mantissas (mant) or rescaled by 2^E (T is
+// overwritten).  16-byte stores when every row of the N x N output starts on
+// 16 bytes (N % 4 == 0 and a 16-byte aligned base); W and c0 are multiples of 4.
+template <int W>
+__device__ __forceinline__ void store_row_f32(float (&T)[W], float* O, int c0, int N, bool mant, long long E,
+                                              unsigned* status, const void* out_base) {
+  if (!mant) {
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (c0 + j < N) T[j] = final_value(T[j], E, status);
+  }
+  if ((N & 3) == 0 && ((uintptr_t)out_base & 15) == 0) {
+#pragma unroll
+    for (int j = 0; j < W; j += 4)
+      if (c0 + j < N) *reinterpret_cast<float4*>(O + c0 + j) = make_float4(T[j], T[j + 1], T[j + 2], T[j + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (c0 + j < N) O[c0 + j] = T[j];
+  }
+}
+
 }  // namespace mp
 
 // Launchers implemented in the .cu files (host side).

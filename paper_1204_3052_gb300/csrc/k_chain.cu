@@ -176,9 +176,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* gbar, unsigned target, unsig
   return !*cta_abort;
 }
 
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
 template <int BN, int NSL, int S>
-__global__ void __launch_bounds__(chain::THREADS, 1)
-    tc_chain_kernel(const __grid_constant__ ChainParams P) {
+__device__ __forceinline__ void chain_body(const ChainParams& P) {
   using namespace chain;
   using C = Cfg<BN, NSL, S>;
   constexpr int STAGES = C::STAGES;
@@ -209,9 +214,15 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   const int KB = (N + BK - 1) / BK;
   const unsigned G = gridDim.x;
   unsigned bar_no = 0;
-  const int rank = S > 1 ? (int)cluster_ctarank() : 0;
+  // split-K needs the launch's clusters of S; launched without them (each CTA
+  // its own cluster), the first CTA of each group of S computes the tile alone
+  // and the others only take part in the grid barriers
+  const bool clustered = S > 1 && cluster_nctarank() == (uint32_t)S;
+  const int rank = clustered ? (int)cluster_ctarank() : 0;
+  const bool idle = S > 1 && !clustered && (blockIdx.x % S) != 0;
+  const int SE = clustered ? S : 1;
   // this CTA's run of the tile's k-blocks (in the rotated visiting order)
-  const int i0 = rank * KB / S, i1 = (rank + 1) * KB / S;
+  const int i0 = rank * KB / SE, i1 = (rank + 1) * KB / SE;
   const int nkb = i1 - i0;
 
   if (threadIdx.x == 0) {
@@ -224,13 +235,13 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
       ptx::mbar_init(accempty0 + 8 * b, 4);
     }
     ptx::mbar_init(drainb, 1);
-    if (S > 1) ptx::mbar_init(xbar, (S - 1) * 128);
+    if (clustered) ptx::mbar_init(xbar, (S - 1) * 128);
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
   // every CTA of the cluster has started and initialised its barriers before
   // any remote store or arrival
-  if (S > 1) cluster_sync_all();
+  if (clustered) cluster_sync_all();
   if (warp == 2) {
     ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
     ptx::tmem_relinquish();
@@ -264,7 +275,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
     const int nops = P.lvl_nops[L];
     const int t_all = blockIdx.x / S;
-    const bool has = t_all < nops * P.tiles_per_op;
+    const bool has = !idle && t_all < nops * P.tiles_per_op;
     const int oi = has ? t_all / P.tiles_per_op : 0;
     const int t = has ? t_all - oi * P.tiles_per_op : 0;
     const chain::Op op = P.ops[2 * L + oi];
@@ -378,7 +389,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
           if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
         }
         const int et = 32 * q + lane;  // epilogue thread = tile row
-        const bool lead = S == 1 || rank == 0;
+        const bool lead = rank == 0;
         if (!lead) {
           // push this partial tile into the leader's buffer, then arrive there
           const uint32_t dst = mapa_rank(ptx::smem_u32(xbuf + (size_t)(rank - 1) * (BN / 4) * 128), 0);
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
             st_cluster_v4(dst + (uint32_t)((c * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
                           T[4 * c + 3]);
           mbar_arrive_remote(mapa_rank(xbar, 0));
-        } else if (S > 1) {
+        } else if (clustered) {
           // the other CTAs' partial tiles, added in rank order
           if (!mbar_wait_cluster(xbar, xph, 2 * WAIT_NS)) {
             *abort_flag = 1;
@@ -469,15 +480,38 @@ __global__ void __launch_bounds__(chain::THREADS, 1)
   }
   if (threadIdx.x == 0 && *abort_flag) atomicOr(P.status, ST_TIMEOUT);
   // no CTA leaves while another of its cluster may still write to its shared memory
-  if (S > 1) cluster_sync_all();
+  if (clustered) cluster_sync_all();
 }
+
+// Whole chain, one CTA per tile.
+template <int BN, int NSL>
+__global__ void __launch_bounds__(chain::THREADS, 1) tc_chain_kernel(const __grid_constant__ ChainParams P) {
+  chain_body<BN, NSL, 1>(P);
+}
+
+// Whole chain with split-K over clusters of S CTAs (the cluster shape is part
+// of the kernel).
+template <int BN, int NSL, int S>
+__global__ void __cluster_dims__(S, 1, 1) __launch_bounds__(chain::THREADS, 1)
+    tc_chain_split_kernel(const __grid_constant__ ChainParams P) {
+  chain_body<BN, NSL, S>(P);
+}
+
+template <int BN, int NSL, int S>
+struct ChainKernel {
+  static constexpr auto fn = tc_chain_split_kernel<BN, NSL, S>;
+};
+template <int BN, int NSL>
+struct ChainKernel<BN, NSL, 1> {
+  static constexpr auto fn = tc_chain_kernel<BN, NSL>;
+};
 
 // ---------------------------------------------------------------------------
 // host side
 
 template <int BN, int NSL, int S>
 static cudaError_t chain_attr() {
-  return cudaFuncSetAttribute(tc_chain_kernel<BN, NSL, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(ChainKernel<BN, NSL, S>::fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               chain::Cfg<BN, NSL, S>::SMEM);
 }
 
@@ -491,7 +525,8 @@ cudaError_t tc_chain_init(matpow_plan_s*) {
   return e;
 }
 
-// Cooperative launch of G CTAs in clusters of S (S = 1: no cluster).
+// Cooperative launch of G CTAs (in clusters of S: the split kernels carry
+// their cluster shape).
 template <int BN, int NSL, int S>
 static cudaError_t chain_launch(ChainParams* P, int G, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -499,16 +534,12 @@ static cudaError_t chain_launch(ChainParams* P, int G, cudaStream_t s) {
   cfg.blockDim = dim3(chain::THREADS);
   cfg.dynamicSmemBytes = chain::Cfg<BN, NSL, S>::SMEM;
   cfg.stream = s;
-  cudaLaunchAttribute at[2];
+  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeCooperative;
   at[0].val.cooperative = 1;
-  at[1].id = cudaLaunchAttributeClusterDimension;
-  at[1].val.clusterDim.x = S;
-  at[1].val.clusterDim.y = 1;
-  at[1].val.clusterDim.z = 1;
   cfg.attrs = at;
-  cfg.numAttrs = S > 1 ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, tc_chain_kernel<BN, NSL, S>, *P);
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, ChainKernel<BN, NSL, S>::fn, *P);
 }
 
 // Clusters of S co-resident with one CTA per SM (0 if the query fails).
@@ -520,15 +551,8 @@ static int chain_max_clusters() {
   cfg.gridDim = dim3(S * 64);
   cfg.blockDim = dim3(chain::THREADS);
   cfg.dynamicSmemBytes = chain::Cfg<BN, NSL, S>::SMEM;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = S;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, tc_chain_kernel<BN, NSL, S>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, ChainKernel<BN, NSL, S>::fn, &cfg) != cudaSuccess) {
     cudaGetLastError();
     n = 0;
   }

@@ -336,23 +336,9 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
                                         &scales[sc].maxbits, red);
       } else {
         if (first && q == 0 && lane == 0 && mode == OUT_USER_MANT && out_log2) *out_log2 = ti.Ec;
-        if (row < N) {
-          float* O = (float*)outp + (size_t)row * N;
-          const bool mant = mode == OUT_USER_MANT;
-#pragma unroll
-          for (int j = 0; j < BN; ++j)
-            if (!mant) T[j] = final_value(T[j], ti.Ec, status);
-          if ((N & 3) == 0 && ((uintptr_t)outp & 15) == 0) {  // rows start on 16 bytes: float4 stores
-#pragma unroll
-            for (int j = 0; j < BN; j += 4)
-              if (ti.n0 + j < N)
-                *reinterpret_cast<float4*>(O + ti.n0 + j) = make_float4(T[j], T[j + 1], T[j + 2], T[j + 3]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < BN; ++j)
-              if (ti.n0 + j < N) O[ti.n0 + j] = T[j];
-          }
-        }
+        if (row < N)
+          store_row_f32<BN>(T, (float*)outp + (size_t)row * N, ti.n0, N, mode == OUT_USER_MANT, ti.Ec, status,
+                            outp);
       }
     }
   }

@@ -482,11 +482,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
       if (row < N) {
         float* O = (float*)d.out + (size_t)row * N;
         const bool mant = d.mode == OUT_USER_MANT;
-#pragma unroll
-        for (int j = 0; j < WC; ++j) {
-          const int c = nw + j;
-          if (c < N) O[c] = mant ? T[j] : final_value(T[j], Ec, status);
-        }
+        store_row_f32<WC>(T, O, nw, N, mant, Ec, status, d.out);
       }
     }
   }

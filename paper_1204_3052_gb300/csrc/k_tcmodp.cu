@@ -218,13 +218,25 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
         res[j] = barrett(v, pm, bm);
       }
       if (d.mode == OUT_INTERNAL) {
+        // 16-byte groups of 8 columns: a group that starts below N ends within
+        // the row's padding to ld (a multiple of 8), which no product reads;
+        // its columns past N are zero (zero-filled operands)
         __nv_bfloat16* p1 = (__nv_bfloat16*)d.C + (size_t)row * d.ld + nw;
         __nv_bfloat16* p0 = p1 + d.plane;
 #pragma unroll
-        for (int j = 0; j < WC; ++j) {
-          if (nw + j < N) {
-            p1[j] = __float2bfloat16_rn((float)(res[j] >> 8));
-            p0[j] = __float2bfloat16_rn((float)(res[j] & 255u));
+        for (int g8 = 0; g8 < WC / 8; ++g8) {
+          if (nw + 8 * g8 < N) {
+            uint32_t w1[4], w0[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+              const unsigned a = res[8 * g8 + 2 * h], b = res[8 * g8 + 2 * h + 1];
+              __nv_bfloat162 hi = __floats2bfloat162_rn((float)(a >> 8), (float)(b >> 8));
+              __nv_bfloat162 lo = __floats2bfloat162_rn((float)(a & 255u), (float)(b & 255u));
+              w1[h] = *reinterpret_cast<uint32_t*>(&hi);
+              w0[h] = *reinterpret_cast<uint32_t*>(&lo);
+            }
+            *reinterpret_cast<uint4*>(p1 + 8 * g8) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+            *reinterpret_cast<uint4*>(p0 + 8 * g8) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
           }
         }
       } else {
