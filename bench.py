@@ -11,6 +11,10 @@ tensor-core path whose errors stay within 2e-5 * ceil(log2 n) on these
 inputs; the line also carries the plain FP32 SIMT path timed on the same
 workload.
 
+The four powers go through one matpow_batched call (`--api batched`, the
+default), which runs them side by side in one cooperative whole-chain launch;
+`--api single` issues one matpow_f32 call per power.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
 """
@@ -38,7 +42,8 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 # the summaries under profiles/ give the command.  Reset to None whenever the
 # kernel changes.
 TRAFFIC = {
-    # re-captured whenever the kernels change; empty until then
+    ("large8192", "bf16x3"): (3.21e9, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
+                                      "tc_fxb_kernel<128, 2> at full size (profiles/tc_fxb_kernel_large8192.md)"),
 }
 
 # bfloat16 tensor-core products per algorithmic product (roofline counting)
@@ -61,6 +66,12 @@ WORKLOADS = {
                          "[1,2^30], 90% float / 10% mod 65521, seed 0"),
     "modp2048": dict(kind="modp", N=2048, ns=[1000], p=65521, prec="bf16x3",
                      desc="single N=2048 U{0..65520} uint32, A^1000 mod 65521 (14 products), seed 0"),
+    # the paper's comparison (Sec. 5.2): square-and-multiply against the naive
+    # GPU method (n - 1 products, one launch each) at its orders and powers
+    "vs_naive": dict(kind="naive", Ns=[128, 256, 512], ns_list=[64, 256, 1024], N=512, ns=[],
+                     prec="bf16x6", gen="gaussian",
+                     desc="N in {128,256,512} N(0,1/N) float32, n in {64,256,1024}, seed 0: "
+                          "square-and-multiply vs the naive n-1 product method on the GPU"),
     # a smaller batch of the same mix (profiling case: a few hundred MB on the device)
     "batched512": dict(kind="batched", count=512, n_max=4096, N=256, ns=[], prec="bf16x6",
                        desc="batched: 512 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
@@ -269,6 +280,8 @@ def config_for(args, wk, world):
                    l2="flushed between timed steps (256 MB write)")
     elif wk.get("kind") == "serving":
         cfg.update(requests=wk["count"], load_sweep=list(args.sweep), sweep_requests=args.sweep_count)
+    elif wk.get("kind") == "naive":
+        cfg.update(orders=wk["Ns"], powers=wk["ns_list"], l2="flushed between timed runs (256 MB write)")
     elif wk.get("kind") == "modp":
         cfg.update(p=wk["p"], gemms_per_step=sum(gemm_count(n) for n in wk["ns"]),
                    l2="flushed between timed steps (256 MB write)")
@@ -279,6 +292,8 @@ def config_for(args, wk, world):
                    parallelism="replicas" if world > 1 else "single")
         if args.chain_mode != 1:
             cfg["chain_mode"] = args.chain_mode
+        cfg["api"] = ("one matpow_batched call over the %d powers" % len(wk["ns"])
+                      if args.api == "batched" and len(wk["ns"]) > 1 else "matpow_f32 per power")
     return cfg
 
 
@@ -293,6 +308,8 @@ def run_reference(args, wk, world, rank):
             cb = cpu_sample_list(reference_items(wk), args.ref_budget)
         elif wk.get("kind") == "modp":
             cb = cpu_sample_modp(wk, args.ref_budget)
+        elif wk.get("kind") == "naive":
+            cb = cpu_sample(dict(wk, ns=wk["ns_list"]), budget_s=args.ref_budget)
         else:
             cb = cpu_sample(wk, budget_s=args.ref_budget)
         res.append(cb["items_per_s"] if serving else cb["value"])
@@ -408,6 +425,11 @@ def run_ours(args, wk, world, rank, local):
     plan.set_option(mpw.OPT_CHAIN, args.chain_mode)
 
     def step(s):
+        if args.api == "batched" and len(ns) > 1:  # the powers side by side, one matpow_batched call
+            st = mpw.matpow_batched(plan.h, [A] * len(ns), [N] * len(ns), ns, outs, lgs, s)
+            if st != 0:
+                mpw._check(st, plan.h)
+            return
         for i, n in enumerate(ns):
             st = mpw.matpow_f32(plan.h, A, N, n, outs[i], lgs[i:i + 1], s)
             if st != 0:
@@ -653,6 +675,71 @@ def run_modp(args, wk, world, rank, local):
                     "h2d_bytes_per_step": int(A_host.nbytes),
                     "d2h_bytes_per_step": int(A_host.nbytes * len(ns))},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb}
+    print(json.dumps(line))
+
+
+def run_naive(args, wk, world, rank, local):
+    """Square-and-multiply vs the naive GPU method (n - 1 products R <- R A, one
+    launch each; the paper's Sec. 4.2 method) with the same product kernels,
+    at the paper's orders and powers; the paper reports ~44x on a C2050."""
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    from paper_1204_3052_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    fast = mpw.Plan(max(wk["Ns"]), args.precision, device=local)
+    naive = mpw.Plan(max(wk["Ns"]), args.precision, device=local)
+    naive.set_option(mpw.OPT_NAIVE, 1)
+    naive.set_option(mpw.OPT_TINY_MAX, 0)
+    rows, t_fast, t_naive, flop_alg = [], 0.0, 0.0, 0.0
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    for N in wk["Ns"]:
+        A = torch.from_numpy(wl.gaussian(N, 0)).to(dev)
+        out = torch.empty_like(A)
+        lg = torch.zeros(1, dtype=torch.int64, device=dev)
+        for n in wk["ns_list"]:
+            ms = {}
+            for name, plan, reps in (("fast", fast, max(args.steps, 3)), ("naive", naive, 2)):
+                with torch.cuda.stream(stream):
+                    for _ in range(args.warmup if name == "fast" else 1):
+                        mpw._check(mpw.matpow_f32(plan.h, A, N, n, out, lg, stream), plan.h)
+                    plan.check(stream)
+                    tot = 0.0
+                    for _ in range(reps):
+                        flush.zero_()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        mpw._check(mpw.matpow_f32(plan.h, A, N, n, out, lg, stream), plan.h)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        tot += e0.elapsed_time(e1)
+                    plan.check(stream)
+                ms[name] = tot / reps
+            t_fast += ms["fast"]
+            t_naive += ms["naive"]
+            flop_alg += gemm_count(n) * 2.0 * N ** 3
+            rows.append({"N": N, "n": n, "square_multiply_ms": ms["fast"], "naive_ms": ms["naive"],
+                         "speedup": ms["naive"] / ms["fast"], "products": [gemm_count(n), n - 1]})
+    clocks = sampler.stop()
+    fast.close()
+    naive.close()
+    if rank != 0:
+        return
+    value = flop_alg / (t_fast * 1e-3) / 1e12
+    line = {"metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_fast,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic", "config": config_for(args, wk, world),
+            "vs_naive_gpu": rows, "speedup_over_naive_total": t_naive / t_fast,
+            "paper_context": "Sec. 5.2 reports about 44x over its naive GPU kernel on a Tesla C2050",
+            "clocks": clocks,
+            "e2e": None, "gpu_launches": None, "roofline": None, "cpu_baseline": None}
     print(json.dumps(line))
 
 
@@ -957,6 +1044,9 @@ def main():
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 SIMT comparator")
+    ap.add_argument("--api", choices=["batched", "single"], default="batched",
+                    help="single-matrix workloads: all powers in one matpow_batched call (default) or "
+                         "one matpow_f32 call per power")
     ap.add_argument("--chain-mode", type=int, choices=[0, 1, 2], default=1,
                     help="whole-chain kernel for N <= 1024: 1 with split-K (default), 2 without, "
                          "0 level-by-level launches")
@@ -980,6 +1070,8 @@ def main():
         run_serving(args, wk, world, rank, local)
     elif wk.get("kind") == "modp":
         run_modp(args, wk, world, rank, local)
+    elif wk.get("kind") == "naive":
+        run_naive(args, wk, world, rank, local)
     else:
         run_ours(args, wk, world, rank, local)
     if world > 1:

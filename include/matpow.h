@@ -125,9 +125,17 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       tensor-core tiles (orders up to 4096) in one persistent
  *                       launch, one CTA per SM walking the whole tile list; 0:
  *                       one CTA per tile.  Results are identical either way.
+ *   MATPOW_OPT_NAIVE    0 (default); 1: matpow_f32 with N above the whole-chain
+ *                       limit (MATPOW_OPT_TINY_MAX) computes A^n the way the
+ *                       paper's naive GPU method does (Sec. 4.2): n - 1
+ *                       products R <- R A, one kernel launch each, with the
+ *                       plan's product kernels and arithmetic.  A comparison
+ *                       method: it costs n - 1 products instead of about
+ *                       2 log2(n).
  */
 enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4,
-       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6, MATPOW_OPT_MODP_TC = 7, MATPOW_OPT_PERSIST = 8 };
+       MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6, MATPOW_OPT_MODP_TC = 7, MATPOW_OPT_PERSIST = 8,
+       MATPOW_OPT_NAIVE = 9 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
 /* ---- the power ------------------------------------------------------------ */

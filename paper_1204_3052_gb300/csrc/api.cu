@@ -253,6 +253,10 @@ extern "C" matpow_status matpow_plan_set_option(matpow_plan_t p, int key, int64_
       if (value < 0 || value > 2) return fail(p, MATPOW_EINVAL, "chain mode must be 0, 1 or 2");
       p->chain_mode = (int)value;
       return MATPOW_OK;
+    case MATPOW_OPT_NAIVE:
+      p->naive = value != 0;
+      drop_graphs(p);
+      return MATPOW_OK;
     case MATPOW_OPT_PERSIST:
       p->persist = value != 0;
       return MATPOW_OK;
@@ -410,8 +414,23 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
   const int ld = ld_for(N, fmt);
   const bool fx2 = fmt_exact(fmt);
   std::vector<LevelOps> levels;
-  build_schedule(n, &levels);
-  int nslots = 2 + matpow_gemm_count(n);
+  int nslots;
+  if (p->naive) {
+    // the comparison method (§4.2): n - 1 products R <- R A, one launch each;
+    // R alternates between buffers 1 and 2 and scale slots 2 and 3 (a slot
+    // is cleared before the product that writes it)
+    for (uint64_t k = 1; k < n; ++k) {
+      LevelOps lv;
+      const int xb = k == 1 ? 0 : 1 + (int)(k & 1), xs = k == 1 ? 1 : 2 + (int)(k & 1);
+      const int cb = 1 + (int)((k + 1) & 1), cs = 2 + (int)((k + 1) & 1);
+      lv.ops.push_back({xb, 0, cb, xs, 1, cs, false});
+      levels.push_back(lv);
+    }
+    nslots = 4;
+  } else {
+    build_schedule(n, &levels);
+    nslots = 2 + matpow_gemm_count(n);
+  }
   CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * nslots, s));
   if (fx2) {
     // slot 1 describes A itself (exponent 0): block slices, max|A|
@@ -456,6 +475,8 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       }
     }
     g.tiles_total = t;
+    if (p->naive && li >= 2)  // the slot this product writes held R two products ago
+      CK(p, cudaMemsetAsync(&p->scales[lv.ops[0].sc], 0, sizeof(Scale), s));
     const double flop = 2.0 * N * (double)N * N * g.count;
     timed_begin(p, s, &ev);
     if (tc) {

@@ -45,6 +45,11 @@ static matpow_status grow(matpow_plan_s* p, void** ptr, size_t* cap, size_t need
     e = cudaMallocHost(&q, n);
   } else {
     cudaDeviceSynchronize();  // the old array may still be in use by queued work
+    if (p->batch.exec) {      // the captured graph refers to the old array
+      cudaGraphExecDestroy(p->batch.exec);
+      p->batch.exec = nullptr;
+      p->batch.sig.clear();
+    }
     e = cudaMalloc(&q, n);
   }
   if (e != cudaSuccess) {
@@ -85,6 +90,41 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   cudaStream_t s = (cudaStream_t)stream;
   const int fmt = plan_float_fmt(p);
   const bool tc = p->prec != MATPOW_FP32_SIMT;
+
+  // ---- up to four powers that all fit the whole-chain kernel: one
+  // cooperative launch runs them side by side (level L of every power between
+  // the same grid barriers)
+  if (count <= 4 && fmt_exact(fmt) && p->chain_mode != 0 && !p->naive) {
+    bool all = true;
+    for (int i = 0; i < count && all; ++i)
+      all = N[i] > p->tiny_max && N[i] <= 1024 && n[i] >= 2;
+    if (all) {
+      size_t need = 0, mb[4];
+      int slots = 0, slot0[4];
+      for (int i = 0; i < count; ++i) {
+        mb[i] = matrix_bytes(N[i], fmt);
+        need += 4 * mb[i];
+        slot0[i] = slots;
+        slots += 2 + matpow_gemm_count(n[i]);
+      }
+      matpow_status st;
+      if ((st = grow(p, &p->batch.ws, &p->batch.ws_bytes, need, false))) return st;
+      if ((st = grow(p, (void**)&p->batch.scales, &p->batch.scale_cap, sizeof(Scale) * slots, false)))
+        return st;
+      ChainJob jobs[4];
+      size_t off = 0;
+      for (int i = 0; i < count; ++i) {
+        char* base = (char*)p->batch.ws + off;
+        jobs[i] = ChainJob{dA[i], N[i], n[i], dOut[i], dLog2Scale ? dLog2Scale + i : nullptr,
+                           {base, base + mb[i], base + 2 * mb[i], base + 3 * mb[i]},
+                           p->batch.scales + slot0[i]};
+        off += 4 * mb[i];
+      }
+      bool used = false;
+      if ((st = tc_chain_launch(p, jobs, count, s, &used))) return st;
+      if (used) return MATPOW_OK;
+    }
+  }
 
   // ---- replay: the same call as the last captured one needs no host work
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;

@@ -53,14 +53,20 @@ __device__ __forceinline__ float pow2f(int k) {
   return mul_pow2(1.0f, k);
 }
 
-// The i-th k-block a tile visits: tiles start at different k-blocks ((m0 + n0) / 128,
-// the same for 64- and 128-wide tiles covering an element)
+// The i-th k-block a tile visits: tiles start at different k-blocks (tile_rot:
+// (m0 + n0) / 128, the same for 64- and 128-wide tiles covering an element)
 // so that CTAs sharing an operand band do not read the same lines at the same
 // time.  The fold order follows it, identically in every kernel.
 __device__ __forceinline__ int rot_kb(int i, int KB, int rot) {
   int k = i + rot % KB;
   return k >= KB ? k - KB : k;
 }
+
+// The rotation of the tile at (m0, n0) of a product with KB k-blocks:
+// (m0 + n0) / 128 up to KB = 32 (N <= 2048); above, every tile starts at
+// k-block 0 so that the CTAs of a wave move through k together and share each
+// k-slab of their bands in L2.
+__device__ __forceinline__ int tile_rot(int m0, int n0, int KB) { return KB > 32 ? 0 : (m0 + n0) / 128; }
 
 __device__ __forceinline__ int frexp_exp(float m) { return scale_exp_from_bits(__float_as_uint(m)); }
 

@@ -81,13 +81,14 @@ inline __host__ __device__ int ld_for(int N, int fmt) {
   return (N + 7) & ~7;
 }
 
-// Output tile t of a tiles_m x tiles_n grid, visited in groups of 8 tile rows
-// and column by column inside a group: a wave of consecutive CTAs covers a
-// compact block of tiles, so it reads few row bands of X and column bands of
-// Y, which stay in L2 while the wave runs.  The arithmetic of a tile does not
-// depend on when it runs.
+// Output tile t of a tiles_m x tiles_n grid, visited in groups of GM tile
+// rows and column by column inside a group: a wave of consecutive CTAs covers
+// a compact block of tiles, so it reads few row bands of X and column bands of
+// Y, which stay in L2 while the wave runs; the next waves of the group reuse
+// its row bands, and Y is streamed once per group (GM = 16 for tall grids).
+// The arithmetic of a tile does not depend on when it runs.
 __host__ __device__ inline void tile_raster(int t, int tiles_m, int tiles_n, int* tm, int* tn) {
-  const int GM = 8;
+  const int GM = tiles_m >= 32 ? 16 : 8;
   const int per = GM * tiles_n;
   const int g = t / per;
   const int r = t - g * per;

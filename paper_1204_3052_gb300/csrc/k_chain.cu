@@ -78,7 +78,8 @@ struct Op {
 };
 }  // namespace chain
 
-struct ChainParams {
+// One power A^n of the launch (its own four buffers and scale slots).
+struct ChainProblem {
   CUtensorMap amap[4][3];  // buffer b as the A operand: slice planes (box 64 x 128)
   CUtensorMap bmap[4][3];  // buffer b as the B operand: slice planes (box 64 x 64)
   void* slices[4];         // first slice plane of buffer b (the next at + plane elements)
@@ -87,12 +88,22 @@ struct ChainParams {
   const float* A;
   float* out;
   long long* out_log2;
-  Scale* scales;
+  Scale* scales;  // this power's slots (ops' slot numbers are relative to it)
+  int N, ld, tiles_n, tiles_per_op;
+  chain::Op ops[2 * chain::MAX_LEVELS];
+};
+constexpr int CHAIN_MAXP = 4;  // independent powers in one launch
+// Up to four independent powers in one cooperative launch: level L of every
+// power runs between the same pair of grid barriers; the CTAs of level L are
+// dealt out to the powers' tiles in order (lvl_begin[L][p] = first CTA group
+// of power p; lvl_begin[L][nprob] = the level's tile count).
+struct ChainParams {
+  ChainProblem pr[CHAIN_MAXP];
   unsigned* status;
   unsigned* gbar;
-  int N, ld, nlevels, tiles_n, tiles_per_op;
-  signed char lvl_nops[chain::MAX_LEVELS];
-  chain::Op ops[2 * chain::MAX_LEVELS];
+  int nprob, nlevels;
+  int prep_begin[CHAIN_MAXP + 1];  // first 64 x 64 prep block of power p
+  short lvl_begin[chain::MAX_LEVELS][CHAIN_MAXP + 1];
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -210,8 +221,6 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int N = P.N, ld = P.ld;
-  const int KB = (N + BK - 1) / BK;
   const unsigned G = gridDim.x;
   unsigned bar_no = 0;
   // split-K needs the launch's clusters of S; launched without them (each CTA
@@ -221,9 +230,6 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   const int rank = clustered ? (int)cluster_ctarank() : 0;
   const bool idle = S > 1 && !clustered && (blockIdx.x % S) != 0;
   const int SE = clustered ? S : 1;
-  // this CTA's run of the tile's k-blocks (in the rotated visiting order)
-  const int i0 = rank * KB / SE, i1 = (rank + 1) * KB / SE;
-  const int nkb = i1 - i0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -247,23 +253,30 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
     ptx::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
-    for (int b = 0; b < 4; ++b)
-      for (int k = 0; k < NSL; ++k) {
-        ptx::prefetch_tmap(&P.amap[b][k]);
-        ptx::prefetch_tmap(&P.bmap[b][k]);
-      }
+    for (int pi = 0; pi < P.nprob; ++pi)
+      for (int b = 0; b < 4; ++b)
+        for (int k = 0; k < NSL; ++k) {
+          ptx::prefetch_tmap(&P.pr[pi].amap[b][k]);
+          ptx::prefetch_tmap(&P.pr[pi].bmap[b][k]);
+        }
   }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // ---- prep: block-scaled exact split of A into buffer 0, max|A| into slot 1
+  // ---- prep: block-scaled exact split of each A into its buffer 0, max|A|
+  // into its slot 1
   {
-    const int nb = fxb::nblocks(N);
-    for (int b = blockIdx.x; b < nb * nb; b += G)
-      fxb::prep_block<NSL>(P.A, N, ld, b / nb, b % nb, (__nv_bfloat16*)P.slices[0], P.plane, P.bexp[0],
-                      &P.scales[1].maxbits, P.status, red);
+    for (int b = blockIdx.x; b < P.prep_begin[P.nprob]; b += G) {
+      int pi = 0;
+      while (pi + 1 < P.nprob && b >= P.prep_begin[pi + 1]) ++pi;
+      const ChainProblem& Q = P.pr[pi];
+      const int nb = fxb::nblocks(Q.N);
+      const int lb = b - P.prep_begin[pi];
+      fxb::prep_block<NSL>(Q.A, Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0], Q.plane, Q.bexp[0],
+                           &Q.scales[1].maxbits, P.status, red);
+    }
     fence_proxy_async_global();
   }
   grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag);
@@ -273,13 +286,21 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   uint32_t xph = 0;  // phase of xbar (leader)
   float T[BN];
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
-    const int nops = P.lvl_nops[L];
     const int t_all = blockIdx.x / S;
-    const bool has = !idle && t_all < nops * P.tiles_per_op;
-    const int oi = has ? t_all / P.tiles_per_op : 0;
-    const int t = has ? t_all - oi * P.tiles_per_op : 0;
-    const chain::Op op = P.ops[2 * L + oi];
-    const int tm = t / P.tiles_n, tn = t - (t / P.tiles_n) * P.tiles_n;
+    int pi = 0;  // the power this CTA group works for at level L
+    while (pi + 1 < P.nprob && t_all >= P.lvl_begin[L][pi + 1]) ++pi;
+    const bool has = !idle && t_all < P.lvl_begin[L][P.nprob];
+    const ChainProblem& Q = P.pr[pi];
+    const int local = has ? t_all - P.lvl_begin[L][pi] : 0;
+    const int oi = local / Q.tiles_per_op;
+    const int t = local - oi * Q.tiles_per_op;
+    const chain::Op op = Q.ops[2 * L + oi];
+    const int N = Q.N;
+    const int KB = (N + BK - 1) / BK;
+    // this CTA's run of the tile's k-blocks (in the rotated visiting order)
+    const int i0 = rank * KB / SE, i1 = (rank + 1) * KB / SE;
+    const int nkb = i1 - i0;
+    const int tm = t / Q.tiles_n, tn = t - (t / Q.tiles_n) * Q.tiles_n;
     const int m0 = tm * BM, n0 = tn * BN;
     const int q = warp - 4;
     const int row = m0 + 32 * q + lane;
@@ -298,16 +319,16 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
             const uint32_t fb = full0 + 8 * s;
             ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
             const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-            const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
+            const int kx = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB)) * BK;
 #pragma unroll
             for (int k = 0; k < NSL; ++k)
-              ptx::tma_load_2d(base + k * C::A_BYTES, &P.amap[op.xb][k], kx, m0, fb);
+              ptx::tma_load_2d(base + k * C::A_BYTES, &Q.amap[op.xb][k], kx, m0, fb);
             const uint32_t bbase = base + NSL * C::A_BYTES;
 #pragma unroll
             for (int c = 0; c < BN / 64; ++c)
 #pragma unroll
               for (int k = 0; k < NSL; ++k)
-                ptx::tma_load_2d(bbase + k * C::B_BYTES + c * 8192, &P.bmap[op.yb][k], n0 + 64 * c, kx,
+                ptx::tma_load_2d(bbase + k * C::B_BYTES + c * 8192, &Q.bmap[op.yb][k], n0 + 64 * c, kx,
                                  fb);
           }
         }
@@ -354,15 +375,15 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           }
         }
       } else if (warp == 3) {
-        fxb::load_tile_exponents<BN>(P.bexp[op.xb], P.bexp[op.yb], N, m0, n0, KB, eA, eB, lane);
+        fxb::load_tile_exponents<BN>(Q.bexp[op.xb], Q.bexp[op.yb], N, m0, n0, KB, eA, eB, lane);
         __syncwarp();
         asm volatile("bar.arrive 2, 160;" ::: "memory");
       } else if (warp >= 4) {
         const int h = q >> 1;
         // scale slots are written by other CTAs: read them from L2, not L1
-        const int sx = scale_exp_from_bits(__ldcg(&P.scales[op.sx].maxbits));
-        const int sy = scale_exp_from_bits(__ldcg(&P.scales[op.sy].maxbits));
-        const long long Ec = __ldcg(&P.scales[op.sx].E) + __ldcg(&P.scales[op.sy].E) + sx + sy;
+        const int sx = scale_exp_from_bits(__ldcg(&Q.scales[op.sx].maxbits));
+        const int sy = scale_exp_from_bits(__ldcg(&Q.scales[op.sy].maxbits));
+        const long long Ec = __ldcg(&Q.scales[op.sx].E) + __ldcg(&Q.scales[op.sy].E) + sx + sy;
 #pragma unroll
         for (int j = 0; j < BN; ++j) T[j] = 0.f;
         asm volatile("bar.sync 2, 160;" ::: "memory");  // exponents staged
@@ -377,7 +398,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
             break;
           }
           ptx::tc_fence_after();
-          const int kr = fxb::rot_kb(kb, KB, (m0 + n0) / 128);
+          const int kr = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB));
           float fac[NG];
 #pragma unroll
           for (int gg = 0; gg < NG; ++gg)
@@ -428,24 +449,24 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           ok = *epi_ok != 0;
           if (op.last) {
             if (ok) {
-              if (t == 0 && q == 0 && lane == 0 && P.out_log2) *P.out_log2 = Ec;
+              if (t == 0 && q == 0 && lane == 0 && Q.out_log2) *Q.out_log2 = Ec;
               if (row < N) {
-                float* O = P.out + (size_t)row * N;
+                float* O = Q.out + (size_t)row * N;
 #pragma unroll
                 for (int j = 0; j < BN; ++j) {
                   const int c = n0 + j;
-                  if (c < N) O[c] = P.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+                  if (c < N) O[c] = Q.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
                 }
               }
             }
           } else {
-            if (t == 0 && q == 0 && lane == 0) P.scales[op.sc].E = Ec;
+            if (t == 0 && q == 0 && lane == 0) Q.scales[op.sc].E = Ec;
             if (ok) {  // the ring is idle here: all k-blocks of this tile were consumed
               const CUtensorMap* cm[NSL];
 #pragma unroll
-              for (int k = 0; k < NSL; ++k) cm[k] = &P.amap[op.cb][k];
+              for (int k = 0; k < NSL; ++k) cm[k] = &Q.amap[op.cb][k];
               fxb::store_slices_tma<BN, 128, NSL>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
-                                                  cm, P.bexp[op.cb], &P.scales[op.sc].maxbits, ered,
+                                                  cm, Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered,
                                                   q == 0 && lane == 0, n0);
             }
             fence_proxy_async_global();
@@ -454,7 +475,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
       }
       kb_base += nkb;  // ring and accumulator counters advance only with work done
     }
-    if (P.ops[2 * L + nops - 1].last) break;  // the final product has been written
+    if (L + 1 == P.nlevels) break;  // every power's final product has been written
     // this level's slices, exponents and maxima are visible to every CTA
     if (!grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag)) break;
     fence_proxy_async_global();
@@ -560,31 +581,54 @@ static int chain_max_clusters() {
   return n;
 }
 
-matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
-                           int64_t* dLog2, cudaStream_t s, bool* used) {
+// Whole-chain launch of up to four independent powers (same tile width and
+// slice count); *used stays false when the powers do not fit one cooperative
+// wave (the caller then runs the level-by-level path).
+matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cudaStream_t s, bool* used) {
   *used = false;
   const int fmt = plan_float_fmt(p);
-  if (p->chain_mode == 0 || !fmt_exact(fmt) || n < 2 || N <= p->tiny_max || N > 1024) return MATPOW_OK;
+  if (p->chain_mode == 0 || p->naive || !fmt_exact(fmt) || nj < 1 || nj > CHAIN_MAXP) return MATPOW_OK;
   const int nsl = fmt_slices(fmt);
-  // three accumulators per buffer fit TMEM only at 64-wide tiles
-  if (nsl == 3 && N > 768) return MATPOW_OK;
-  const int BN = N <= 768 ? 64 : 128;
-  std::vector<LevelOps> levels;
-  build_schedule(n, &levels);
-  if ((int)levels.size() > chain::MAX_LEVELS) return MATPOW_OK;
-  const int tiles_n = (N + BN - 1) / BN;
-  const int tiles_per_op = ((N + chain::BM - 1) / chain::BM) * tiles_n;
-  int maxops = 1;
-  for (auto& lv : levels) maxops = std::max(maxops, (int)lv.ops.size());
-  const int G1 = maxops * tiles_per_op;
+  int maxN = 0, minKB = 1 << 30;
+  for (int j = 0; j < nj; ++j) {
+    const int N = jobs[j].N;
+    if (jobs[j].n < 2 || N <= p->tiny_max || N > 1024) return MATPOW_OK;
+    // three accumulators per buffer fit TMEM only at 64-wide tiles
+    if (nsl == 3 && N > 768) return MATPOW_OK;
+    maxN = std::max(maxN, N);
+    minKB = std::min(minKB, (N + chain::BK - 1) / chain::BK);
+  }
+  const int BN = maxN <= 768 ? 64 : 128;
+  if (BN == 128 && nj > 1) return MATPOW_OK;  // one tile width per launch
+  static thread_local ChainParams P;  // ~20 KB: kept off the stack
+  memset(&P, 0, sizeof P);
+  std::vector<LevelOps> levels[CHAIN_MAXP];
+  int nlevels = 0;
+  for (int j = 0; j < nj; ++j) {
+    build_schedule(jobs[j].n, &levels[j]);
+    if ((int)levels[j].size() > chain::MAX_LEVELS) return MATPOW_OK;
+    nlevels = std::max(nlevels, (int)levels[j].size());
+  }
+  // CTA groups per level: the powers' tiles one after another
+  int G1 = 0;
+  for (int L = 0; L < nlevels; ++L) {
+    int acc = 0;
+    for (int j = 0; j < nj; ++j) {
+      P.lvl_begin[L][j] = (short)acc;
+      const int N = jobs[j].N;
+      const int tpo = ((N + chain::BM - 1) / chain::BM) * ((N + BN - 1) / BN);
+      if (L < (int)levels[j].size()) acc += (int)levels[j][L].ops.size() * tpo;
+    }
+    P.lvl_begin[L][nj] = (short)acc;
+    G1 = std::max(G1, acc);
+  }
   if (G1 > p->num_sms) return MATPOW_OK;
   // split-K: 2 or 4 CTAs per tile when the SMs allow it (each keeps >= 1 k-block)
-  const int KB = (N + chain::BK - 1) / chain::BK;
   int S = 1;
   if (p->chain_mode == 1 && BN == 64) {
     const int smax = nsl == 3 ? 2 : 4;
     for (int c = smax; c >= 2; c /= 2) {
-      if (G1 * c > p->num_sms || c > KB) continue;
+      if (G1 * c > p->num_sms || c > minKB) continue;
       const int mc = nsl == 3 ? chain_max_clusters<64, 3, 2>()
                      : c == 4 ? chain_max_clusters<64, 2, 4>() : chain_max_clusters<64, 2, 2>();
       if (mc >= G1) {
@@ -595,49 +639,59 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
   }
   const int G = G1 * S;
 
-  static thread_local ChainParams P;  // ~4 KB: kept off the stack
-  memset(&P, 0, sizeof P);
-  const int ld = ld_for(N, fmt);
-  const long long plane = plane_offset_elems(N, fmt);
-  for (int b = 0; b < 4; ++b) {
-    const char* base = (const char*)p->buf[b];
-    P.slices[b] = p->buf[b];
-    P.bexp[b] = (int*)((char*)p->buf[b] + fxb::bexp_offset(N, ld, nsl));
-    for (int k = 0; k < nsl; ++k)
-      if (!tc_encode_bf16_map(&P.amap[b][k], base + k * plane * 2, N, ld, 64, chain::BM) ||
-          !tc_encode_bf16_map(&P.bmap[b][k], base + k * plane * 2, N, ld, 64, 64))
-        return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", N);
+  int prep = 0;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < nj; ++j) {
+    const ChainJob& J = jobs[j];
+    ChainProblem& Q = P.pr[j];
+    const int N = J.N;
+    const int ld = ld_for(N, fmt);
+    const long long plane = plane_offset_elems(N, fmt);
+    for (int b = 0; b < 4; ++b) {
+      const char* base = (const char*)J.buf[b];
+      Q.slices[b] = J.buf[b];
+      Q.bexp[b] = (int*)((char*)J.buf[b] + fxb::bexp_offset(N, ld, nsl));
+      for (int k = 0; k < nsl; ++k)
+        if (!tc_encode_bf16_map(&Q.amap[b][k], base + k * plane * 2, N, ld, 64, chain::BM) ||
+            !tc_encode_bf16_map(&Q.bmap[b][k], base + k * plane * 2, N, ld, 64, 64))
+          return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", N);
+    }
+    Q.plane = plane;
+    Q.A = J.A;
+    Q.out = J.out;
+    Q.out_log2 = (long long*)J.log2;
+    Q.scales = J.scales;
+    Q.N = N;
+    Q.ld = ld;
+    Q.tiles_n = (N + BN - 1) / BN;
+    Q.tiles_per_op = ((N + chain::BM - 1) / chain::BM) * Q.tiles_n;
+    const std::vector<LevelOps>& lv = levels[j];
+    for (size_t L = 0; L < lv.size(); ++L)
+      for (size_t i = 0; i < lv[L].ops.size(); ++i) {
+        const Op& o = lv[L].ops[i];
+        chain::Op& c = Q.ops[2 * L + i];
+        c.xb = (signed char)o.xb;
+        c.yb = (signed char)o.yb;
+        c.cb = (signed char)o.cb;
+        c.sx = (short)o.sx;
+        c.sy = (short)o.sy;
+        c.sc = (short)o.sc;
+        c.last = (L + 1 == lv.size() && i + 1 == lv[L].ops.size()) ? 1 : 0;
+      }
+    P.prep_begin[j] = prep;
+    const int nb = fxb::nblocks(N);
+    prep += nb * nb;
+    if (e == cudaSuccess) e = cudaMemsetAsync(J.scales, 0, sizeof(Scale) * (2 + matpow_gemm_count(J.n)), s);
   }
-  P.plane = plane;
-  P.A = dA;
-  P.out = dOut;
-  P.out_log2 = (long long*)dLog2;
-  P.scales = p->scales;
+  P.prep_begin[nj] = prep;
+  P.nprob = nj;
+  P.nlevels = nlevels;
   P.status = p->status;
   P.gbar = p->gbar;
-  P.N = N;
-  P.ld = ld;
-  P.nlevels = (int)levels.size();
-  P.tiles_n = tiles_n;
-  P.tiles_per_op = tiles_per_op;
-  for (size_t L = 0; L < levels.size(); ++L) {
-    P.lvl_nops[L] = (signed char)levels[L].ops.size();
-    for (size_t i = 0; i < levels[L].ops.size(); ++i) {
-      const Op& o = levels[L].ops[i];
-      chain::Op& c = P.ops[2 * L + i];
-      c.xb = (signed char)o.xb;
-      c.yb = (signed char)o.yb;
-      c.cb = (signed char)o.cb;
-      c.sx = (short)o.sx;
-      c.sy = (short)o.sy;
-      c.sc = (short)o.sc;
-      c.last = (L + 1 == levels.size() && i + 1 == levels[L].ops.size()) ? 1 : 0;
-    }
-  }
-  const int nslots = 2 + matpow_gemm_count(n);
-  cudaError_t e = cudaMemsetAsync(p->scales, 0, sizeof(Scale) * nslots, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->gbar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemsetAsync");
+  double flop = 0;
+  for (int j = 0; j < nj; ++j) flop += 2.0 * jobs[j].N * (double)jobs[j].N * jobs[j].N * matpow_gemm_count(jobs[j].n);
   cudaEvent_t ev;
   timed_begin(p, s, &ev);
   if (nsl == 3)
@@ -653,10 +707,16 @@ matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n,
     e = nsl == 3 ? chain_launch<64, 3, 1>(&P, G1, s) : chain_launch<64, 2, 1>(&P, G1, s);
   }
   if (e != cudaSuccess) return cuda_fail(p, e, "cooperative launch of tc_chain_kernel");
-  timed_end(p, s, ev, MATPOW_KERNEL_TC, 2.0 * N * (double)N * N * matpow_gemm_count(n));
+  timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
   p->launches++;
   *used = true;
   return MATPOW_OK;
+}
+
+matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
+                           int64_t* dLog2, cudaStream_t s, bool* used) {
+  ChainJob j{dA, N, n, dOut, dLog2, {p->buf[0], p->buf[1], p->buf[2], p->buf[3]}, p->scales};
+  return tc_chain_launch(p, &j, 1, s, used);
 }
 
 }  // namespace mp

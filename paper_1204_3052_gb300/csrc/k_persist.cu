@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
           const uint32_t fb = full0 + 8 * s;
           ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
           const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-          const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
+          const int kx = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB)) * BK;
 #pragma unroll
           for (int k = 0; k < NSL; ++k) ptx::tma_load_2d(base + k * C::A_BYTES, ax + k, kx, m0, fb);
           const uint32_t bbase = base + NSL * C::A_BYTES;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
           break;
         }
         ptx::tc_fence_after();
-        const int kr = fxb::rot_kb(kb, KB, (ti.m0 + ti.n0) / 128);
+        const int kr = fxb::rot_kb(kb, KB, fxb::tile_rot(ti.m0, ti.n0, KB));
         float fac[1];
         fac[0] = fxb::pow2f(eA[h * KB + kr] + eB[kr] - 16 - ti.sx - ti.sy);
         fxb::fold<BN, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN), fac, BN);

@@ -364,7 +364,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         const uint32_t fb = full0 + 8 * s;
         ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
         const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
-        const int kx = fxb::rot_kb(kb, KB, (m0 + n0) / 128) * BK;
+        const int kx = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB)) * BK;
 #pragma unroll
         for (int k = 0; k < NSL; ++k) ptx::tma_load_2d(base + k * C::A_BYTES, ax[k], kx, m0, fb);
         const uint32_t bbase = base + NSL * C::A_BYTES;
@@ -454,7 +454,7 @@ __device__ __forceinline__ void fxb_cta(const GemmDesc& d, int t, const CUtensor
         break;
       }
       ptx::tc_fence_after();
-      const int kr = fxb::rot_kb(kb, KB, (m0 + n0) / 128);
+      const int kr = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB));
       float fac[WC / 64];
 #pragma unroll
       for (int g = 0; g < WC / 64; ++g)

@@ -44,8 +44,11 @@ __device__ __forceinline__ unsigned barrett(unsigned x, unsigned p, unsigned m) 
   return r >= p ? r - p : r;
 }
 
-__global__ void __launch_bounds__(tcm::THREADS, 1)
-    tc_modp_kernel(const __grid_constant__ TcPairParams P, unsigned* status) {
+// One 128 x 64 output tile t of product d; ax1/ax0: the high / low byte
+// slices of X as the A operand, by1/by0: those of Y as the B operand.
+__device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtensorMap* ax1,
+                                         const CUtensorMap* ax0, const CUtensorMap* by1,
+                                         const CUtensorMap* by0, unsigned* status) {
   using namespace tcm;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -60,11 +63,6 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int t = blockIdx.x;
-  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
-  if (which) t -= P.tiles0;
-  const TcProblem& pr = P.p[which];
-  const GemmDesc& d = pr.d;
   int tm, tn;
   tile_raster(t, (d.N + BM - 1) / BM, d.tiles_n, &tm, &tn);
   const int m0 = tm * BM, n0 = tn * BN;
@@ -90,10 +88,10 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
     ptx::tmem_relinquish();
   }
   if (warp == 0 && lane == 0) {
-    ptx::prefetch_tmap(&pr.ax[0]);
-    ptx::prefetch_tmap(&pr.ax[1]);
-    ptx::prefetch_tmap(&pr.by[0]);
-    ptx::prefetch_tmap(&pr.by[1]);
+    ptx::prefetch_tmap(ax1);
+    ptx::prefetch_tmap(ax0);
+    ptx::prefetch_tmap(by1);
+    ptx::prefetch_tmap(by0);
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -113,10 +111,10 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
         ptx::mbar_expect_tx(fb, STAGE_BYTES);
         const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
         const int kx = kb * BK;
-        ptx::tma_load_2d(base, &pr.ax[0], kx, m0, fb);            // x1
-        ptx::tma_load_2d(base + A_BYTES, &pr.ax[1], kx, m0, fb);  // x0
-        ptx::tma_load_2d(base + 2 * A_BYTES, &pr.by[0], n0, kx, fb);            // y1
-        ptx::tma_load_2d(base + 2 * A_BYTES + B_BYTES, &pr.by[1], n0, kx, fb);  // y0
+        ptx::tma_load_2d(base, ax1, kx, m0, fb);                          // x1
+        ptx::tma_load_2d(base + A_BYTES, ax0, kx, m0, fb);                // x0
+        ptx::tma_load_2d(base + 2 * A_BYTES, by1, n0, kx, fb);            // y1
+        ptx::tma_load_2d(base + 2 * A_BYTES + B_BYTES, by0, n0, kx, fb);  // y0
         ++issued;
       }
       for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
@@ -256,6 +254,32 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
 }
 
+__global__ void __launch_bounds__(tcm::THREADS, 1)
+    tc_modp_kernel(const __grid_constant__ TcPairParams P, unsigned* status) {
+  int t = blockIdx.x;
+  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
+  if (which) t -= P.tiles0;
+  const TcProblem& pr = P.p[which];
+  modp_cta(pr.d, t, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], status);
+}
+
+// Grouped launch (server): products from a device table, each buffer's four
+// TMA descriptors {x1, x0 as A; y1, y0 as B} from a device table at map_x
+// (A role: + 0, 1) and map_y (B role: + 2, 3).
+__global__ void __launch_bounds__(tcm::THREADS, 1)
+    tc_modp_group_kernel(const GemmDesc* __restrict__ descs, int count,
+                         const CUtensorMap* __restrict__ maps, unsigned* status) {
+  const int tb = blockIdx.x;
+  int lo = 0, hi = count - 1;  // last desc with tile_begin <= tb
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].tile_begin <= tb) lo = mid; else hi = mid - 1;
+  }
+  const GemmDesc& d = descs[lo];
+  modp_cta(d, tb - d.tile_begin, maps + d.map_x, maps + d.map_x + 1, maps + d.map_y + 2,
+           maps + d.map_y + 3, status);
+}
+
 // A (uint32, leading dimension N) -> byte slices (x >> 8, x & 255) as bfloat16
 // planes with leading dimension ld; entries >= p flag ST_BADINPUT.
 __global__ void prep_modp_slices_kernel(const unsigned* __restrict__ A, int N, int ld, unsigned p,
@@ -277,7 +301,18 @@ __global__ void prep_modp_slices_kernel(const unsigned* __restrict__ A, int N, i
 // ---------------------------------------------------------------------------
 
 cudaError_t tc_modp_init() {
-  return cudaFuncSetAttribute(tc_modp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcm::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc_modp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcm::SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_modp_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tcm::SMEM);
+  return e;
+}
+
+cudaError_t launch_modp_tc_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
+                                 unsigned* status, cudaStream_t s) {
+  if (tiles <= 0) return cudaSuccess;
+  tc_modp_group_kernel<<<tiles, tcm::THREADS, tcm::SMEM, s>>>(d_descs, count, (const CUtensorMap*)d_maps,
+                                                              status);
+  return cudaGetLastError();
 }
 
 int tc_modp_tile_n() { return tcm::BN; }

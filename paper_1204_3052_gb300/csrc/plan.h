@@ -101,6 +101,7 @@ struct matpow_plan_s {
   int chain_mode = 1;  // whole-chain kernel: 0 off, 1 with split-K where it fits, 2 without
   bool modp_tc = true;    // mod-p products on the tensor cores (64 < N <= 16384)
   bool persist = true;    // batched 64-column levels: persistent grouped kernel
+  bool naive = false;     // float powers by n - 1 products R <- R A (comparison method)
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
   // graphs
   std::vector<mp::GraphEntry> graphs;
@@ -139,6 +140,19 @@ bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box
 // (exact split; small and medium N).  *used = false when it does not apply.
 matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
                            int64_t* dLog2, cudaStream_t s, bool* used);
+// One power of a multi-power whole-chain launch: input, order, power, output,
+// its four stored-format buffers and its scale slots (2 + G(n)).
+struct ChainJob {
+  const float* A;
+  int N;
+  uint64_t n;
+  float* out;
+  int64_t* log2;
+  void* buf[4];
+  Scale* scales;
+};
+// Up to four independent powers (same tile width) in one cooperative launch.
+matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cudaStream_t s, bool* used);
 cudaError_t tc_chain_init(matpow_plan_s* p);
 // tensor-core mod-p products (k_tcmodp.cu)
 cudaError_t tc_modp_init();
@@ -146,6 +160,11 @@ int tc_modp_tile_n();
 cudaError_t launch_prep_modp_slices(const unsigned* A, int N, unsigned p, void* dst,
                                     unsigned* status, cudaStream_t s);
 matpow_status tc_modp_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s);
+// Grouped tensor-core mod-p level launch (server): one CTA per 128 x 64 tile of
+// every product in the device table; descriptors per buffer as for the exact
+// split with two slices (x1, x0 as A at map_x, y1, y0 as B at map_y + 2).
+cudaError_t launch_modp_tc_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
+                                 unsigned* status, cudaStream_t s);
 // Grouped exact-split level launch of the plan's batch (max_n: largest order
 // among the products).
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,

@@ -94,6 +94,7 @@ struct Req {
   std::vector<LevelOps> levels;
   size_t next_level = 0;
   bool tiny = false;
+  bool tcm = false;  // mod p on the tensor cores (byte-slice planes)
   bool prepared = false;
   uint64_t done_step = 0;
 };
@@ -143,8 +144,9 @@ static matpow_status sfail(matpow_server_s* s, matpow_status st, const char* msg
 }
 
 static size_t footprint(const matpow_server_s* s, const matpow_request& r) {
-  const int fmt = r.kind == 1 ? FMT_U32 : s->fmt;
-  return 4 * matrix_bytes(r.N, fmt);
+  if (r.kind == 1)  // uint32 (CUDA cores) or two byte-slice planes (tensor cores)
+    return 4 * std::max(matrix_bytes(r.N, FMT_U32), matrix_bytes(r.N, FMT_MODP));
+  return 4 * matrix_bytes(r.N, s->fmt);
 }
 
 static cudaEvent_t take_ev(matpow_server_s* s) {
@@ -182,8 +184,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64_t step) {
   std::vector<TinyDesc> tiny;
   std::vector<PrepDesc> prep;
-  std::vector<GemmDesc> gf, gw, gm;  // float (64-wide tiles), float (128-wide), mod p
-  int tiles_f = 0, tiles_w = 0, tiles_m = 0, maxn_f = 0;
+  std::vector<GemmDesc> gf, gw, gm, gt;  // float (64-wide tiles), float (128-wide), mod p (CUDA / tensor cores)
+  int tiles_f = 0, tiles_w = 0, tiles_m = 0, tiles_t = 0, maxn_f = 0;
   std::vector<Req*> modp_prep;
   for (Req* q : act) {
     if (q->state != 1) continue;
@@ -287,6 +289,18 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
           tiles_f += d.tiles_n * d.tiles_n;
           gf.push_back(d);
         }
+      } else if (q->tcm) {
+        d.ld = ld_for(r.N, FMT_MODP);
+        d.plane = plane_offset_elems(r.N, FMT_MODP);
+        d.mode = last ? OUT_USER_VALUE : OUT_INTERNAL;
+        d.p = r.p;
+        d.bn = tc_modp_tile_n();
+        d.tiles_n = (r.N + d.bn - 1) / d.bn;
+        d.map_x = 24 * q->chunk + 4 * op.xb;
+        d.map_y = 24 * q->chunk + 4 * op.yb;
+        d.tile_begin = tiles_t;
+        tiles_t += ((r.N + 127) / 128) * d.tiles_n;
+        gt.push_back(d);
       } else {
         d.ld = ld_for(r.N, FMT_U32);
         d.mode = last ? OUT_USER_VALUE : OUT_INTERNAL;
@@ -325,7 +339,8 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   // tile records of the 64-column float group (persistent kernel)
   std::vector<int4> trec;
   if (fmt_exact(s->fmt)) persist_tile_records(gf.data(), (int)gf.size(), fmt_slices(s->fmt), &trec);
-  const size_t o_td = align256(o_m + gm.size() * sizeof(GemmDesc));
+  const size_t o_mt = align256(o_m + gm.size() * sizeof(GemmDesc));
+  const size_t o_td = align256(o_mt + gt.size() * sizeof(GemmDesc));
   const size_t total = std::max<size_t>(align256(o_td + trec.size() * sizeof(int4)), 256);
   if (!ensure_tab(s, total)) return fail(nullptr, MATPOW_ENOMEM, "server: descriptor table");
   const int ti = s->tab_i;
@@ -338,6 +353,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   if (!gf.empty()) memcpy(h + o_f, gf.data(), gf.size() * sizeof(GemmDesc));
   if (!gw.empty()) memcpy(h + o_w, gw.data(), gw.size() * sizeof(GemmDesc));
   if (!gm.empty()) memcpy(h + o_m, gm.data(), gm.size() * sizeof(GemmDesc));
+  if (!gt.empty()) memcpy(h + o_mt, gt.data(), gt.size() * sizeof(GemmDesc));
   if (!trec.empty()) memcpy(h + o_td, trec.data(), trec.size() * sizeof(int4));
   cudaError_t e = cudaMemcpyAsync(dd, h, total, cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: upload");
@@ -362,8 +378,11 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   for (Req* q : modp_prep) {
     char* base = (char*)s->arena_mem + q->off;
     unsigned* st = s->status + (q->chunk + 1) * 32;
-    e = launch_modp_check_convert((const unsigned*)q->r.dA, q->r.N, q->r.p, (unsigned*)base, st,
-                                  s->stream);
+    if (q->tcm)
+      e = launch_prep_modp_slices((const unsigned*)q->r.dA, q->r.N, q->r.p, base, st, s->stream);
+    else
+      e = launch_modp_check_convert((const unsigned*)q->r.dA, q->r.N, q->r.p, (unsigned*)base, st,
+                                    s->stream);
     if (e == cudaSuccess && q->r.n == 1)
       e = cudaMemcpy2DAsync(q->r.dOut, (size_t)q->r.N * 4, base, (size_t)ld_for(q->r.N, FMT_U32) * 4,
                             (size_t)q->r.N * 4, q->r.N, cudaMemcpyDeviceToDevice, s->stream);
@@ -386,6 +405,11 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
   }
   if (!gm.empty()) {
     e = launch_modp_group((const GemmDesc*)(dd + o_m), (int)gm.size(), tiles_m, st0, s->stream);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p level");
+  }
+  if (!gt.empty()) {
+    e = launch_modp_tc_group((const GemmDesc*)(dd + o_mt), (int)gt.size(), tiles_t, s->d_maps, st0,
+                             s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p level");
   }
   cudaEvent_t ev = take_ev(s);
@@ -415,11 +439,13 @@ static void scheduler(matpow_server_s* s) {
         s->free_chunks.pop_back();
         q->state = 1;
         q->tiny = q->r.kind == 0 && q->r.N <= tiny_max_supported() && q->r.n >= 2;
+        // mod p on the tensor cores from N > 64 (as matpow_mod_p does)
+        q->tcm = q->r.kind == 1 && q->r.n >= 2 && q->r.N > 64 && q->r.N <= 16384;
         if (q->r.n >= 2) build_schedule(q->r.n, &q->levels);
-        if (fmt_exact(s->fmt) && q->r.kind == 0 && !q->tiny && q->r.n >= 2) {
+        if ((fmt_exact(s->fmt) && q->r.kind == 0 && !q->tiny && q->r.n >= 2) || q->tcm) {
           // TMA descriptors of the request's four buffers, uploaded in stream
           // order before its first product
-          const int nsl = fmt_slices(s->fmt);
+          const int nsl = q->tcm ? 2 : fmt_slices(s->fmt);
           CUtensorMap* hm = s->h_maps + 24 * q->chunk;
           const size_t mb = fp / 4;
           bool okm = true;
@@ -550,8 +576,9 @@ extern "C" matpow_status matpow_server_create(matpow_server_t* out, const matpow
   if (e == cudaSuccess) e = cudaMalloc(&s->status, sizeof(unsigned) * s->h_status.size());
   if (e == cudaSuccess) e = cudaMemset(s->status, 0, sizeof(unsigned) * s->h_status.size());
   if (e == cudaSuccess) e = tiny_attrs();
-  if (e == cudaSuccess && fmt_exact(s->fmt)) {
+  if (e == cudaSuccess) {  // tensor maps: exact-split float levels and tensor-core mod p
     e = tc_init(nullptr);
+    if (e == cudaSuccess) e = tc_modp_init();
     if (e == cudaSuccess) e = cudaMalloc(&s->d_maps, sizeof(CUtensorMap) * 24 * d->max_inflight);
     if (e == cudaSuccess) e = cudaMallocHost(&s->h_maps, sizeof(CUtensorMap) * 24 * d->max_inflight);
   }

@@ -136,3 +136,34 @@ def test_batched_graph_replay_follows_new_contents():
         assert torch.equal(lg, lr)
     plan.close()
     ref.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+def test_few_powers_run_side_by_side_in_one_chain(prec):
+    # up to four powers in the whole-chain range go to one cooperative launch;
+    # without split-K each tile's arithmetic is that of a single call (bits
+    # equal), with it the results stay within the oracle bound
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    Ns = [512, 100, 300, 65]
+    ns = [1024, 3, 77, 2 ** 20 + 1]
+    As = [wl.gaussian(N, 90 + i) for i, N in enumerate(Ns)]
+    dAs = [to_dev(a) for a in As]
+    for mode in (2, 1):
+        plan = mpw.Plan(512, prec)
+        plan.set_option(mpw.OPT_CHAIN, mode)
+        lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
+        before = plan.launch_count()
+        outs = plan.batched(dAs, ns, log2=lg)
+        plan.check()
+        assert plan.launch_count() - before == 1  # one cooperative launch
+        for i, (A, n) in enumerate(zip(As, ns)):
+            if mode == 2:
+                alone, alone_lg = plan.f32(dAs[i], n, mantissa=True)
+                plan.check()
+                assert torch.equal(alone, outs[i]) and int(alone_lg.item()) == int(lg[i].item()), (Ns[i], n)
+            if n <= 4096:
+                M, e, _ = oracle.matpow_f64(A, n)
+                err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
+                assert err <= gate(n, floor_for(prec, A, n, M, e)), (mode, Ns[i], n, err)
+        plan.close()

@@ -76,3 +76,29 @@ def test_modp_tensor_and_simt_agree_on_large_orders():
         assert torch.equal(a, b), (N, n, p)
     tc.close()
     sm.close()
+
+
+def test_walk_counts_mod_p(plan):
+    # graph walk counting: (A^n)[i, j] is the number of walks of length n from
+    # i to j in the graph with 0/1 adjacency A; counted here by dynamic
+    # programming over walk lengths with Python integers (exact, independent
+    # of the oracle), then reduced mod p
+    p = 65521
+    g = wl.rng(31)
+    for N, n in ((70, 9), (130, 25)):
+        A = (g.random((N, N)) < 0.1).astype(np.uint64)
+        src = [0, N // 2, N - 1]
+        got, st = run(plan, A, n, p)
+        assert st == 0
+        adj = [[j for j in range(N) if A[i, j]] for i in range(N)]
+        for s in src:
+            walks = [0] * N
+            walks[s] = 1
+            for _ in range(n):
+                nxt = [0] * N
+                for i, w in enumerate(walks):
+                    if w:
+                        for j in adj[i]:
+                            nxt[j] += w
+                walks = nxt
+            assert [int(v) for v in got[s]] == [w % p for w in walks], (N, n, s)

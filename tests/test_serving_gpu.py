@@ -115,3 +115,33 @@ def test_poll_unknown_ticket_and_eagain():
     server = mpw.Server(64, "fp32", hbm_budget_bytes=8 << 20, max_inflight=4)
     assert server.poll(12345) == mpw.EINVAL
     server.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x6"])
+def test_tensor_core_modp_requests_and_bad_entry(prec):
+    # mod-p requests above N = 64 run on the tensor cores (byte slices) inside
+    # the server's grouped levels; one bad entry fails only its own request
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    server = mpw.Server(512, prec, hbm_budget_bytes=64 << 20, max_inflight=8)
+    p = 65521
+    cases = [(100, 7), (257, 1000), (512, 2 ** 30 - 1), (130, 2)]
+    bad = wl.modp_uniform(100, p, 77)
+    bad[5, 9] = p
+    subs = []
+    for i, (N, n) in enumerate(cases):
+        A = wl.modp_uniform(N, p, 60 + i)
+        dA = to_dev(A.view(np.int32))
+        out = torch.empty_like(dA)
+        subs.append((A, n, dA, out, server.submit(dA, n, out, kind=1, p=p)))
+    dB = to_dev(bad.view(np.int32))
+    oB = torch.empty_like(dB)
+    tb = server.submit(dB, 33, oB, kind=1, p=p)
+    for A, n, dA, out, t in subs:
+        assert server.wait(t) == mpw.OK
+    assert server.wait(tb) == mpw.EINVAL
+    torch.cuda.synchronize()
+    for A, n, dA, out, t in subs:
+        want, _ = oracle.matpow_modp(A, n, p)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32).astype(np.uint64), want), (A.shape[0], n)
+    server.close()
