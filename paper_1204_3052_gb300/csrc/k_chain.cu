@@ -139,8 +139,9 @@ __device__ __forceinline__ void st_cluster_v4(uint32_t a, float x, float y, floa
                "f"(w)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t a) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(a) : "memory");
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(a), "r"(count)
+               : "memory");
 }
 // Bounded wait on a local mbarrier whose arrivals come from other CTAs of the
 // cluster (acquire at cluster scope).
@@ -224,12 +225,9 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   const unsigned G = gridDim.x;
   unsigned bar_no = 0;
   // split-K needs the launch's clusters of S; launched without them (each CTA
-  // its own cluster), the first CTA of each group of S computes the tile alone
-  // and the others only take part in the grid barriers
+  // its own cluster), every CTA computes whole tiles
   const bool clustered = S > 1 && cluster_nctarank() == (uint32_t)S;
-  const int rank = clustered ? (int)cluster_ctarank() : 0;
-  const bool idle = S > 1 && !clustered && (blockIdx.x % S) != 0;
-  const int SE = clustered ? S : 1;
+  const int crank = clustered ? (int)cluster_ctarank() : 0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -286,10 +284,22 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   uint32_t xph = 0;  // phase of xbar (leader)
   float T[BN];
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
-    const int t_all = blockIdx.x / S;
+    // this level's split: f CTAs of a cluster share a tile, the largest f
+    // (dividing S) with f x (tiles of the level) <= G; the cluster's S CTAs
+    // then work on S / f tiles
+    const int T_L = P.lvl_begin[L][P.nprob];
+    int f = 1;
+    if (clustered) {
+      f = S;
+      while (f > 1 && f * T_L > (int)G) f >>= 1;
+    }
+    const int sub = crank / f;
+    const int rank = crank - sub * f;  // rank within the tile's group; 0 leads
+    const int lead_rank = sub * f;     // cluster rank of the group's leader
+    const int t_all = clustered ? (int)(blockIdx.x / S) * (S / f) + sub : (int)blockIdx.x;
     int pi = 0;  // the power this CTA group works for at level L
     while (pi + 1 < P.nprob && t_all >= P.lvl_begin[L][pi + 1]) ++pi;
-    const bool has = !idle && t_all < P.lvl_begin[L][P.nprob];
+    const bool has = t_all < T_L;
     const ChainProblem& Q = P.pr[pi];
     const int local = has ? t_all - P.lvl_begin[L][pi] : 0;
     const int oi = local / Q.tiles_per_op;
@@ -298,7 +308,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
     const int N = Q.N;
     const int KB = (N + BK - 1) / BK;
     // this CTA's run of the tile's k-blocks (in the rotated visiting order)
-    const int i0 = rank * KB / SE, i1 = (rank + 1) * KB / SE;
+    const int i0 = rank * KB / f, i1 = (rank + 1) * KB / f;
     const int nkb = i1 - i0;
     const int tm = t / Q.tiles_n, tn = t - (t / Q.tiles_n) * Q.tiles_n;
     const int m0 = tm * BM, n0 = tn * BN;
@@ -413,13 +423,16 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
         const bool lead = rank == 0;
         if (!lead) {
           // push this partial tile into the leader's buffer, then arrive there
-          const uint32_t dst = mapa_rank(ptx::smem_u32(xbuf + (size_t)(rank - 1) * (BN / 4) * 128), 0);
+          // (weighted so that every split factor completes the leader's
+          // barrier, initialised for S - 1 pushing CTAs, in one phase)
+          const uint32_t dst =
+              mapa_rank(ptx::smem_u32(xbuf + (size_t)(rank - 1) * (BN / 4) * 128), (uint32_t)lead_rank);
 #pragma unroll
           for (int c = 0; c < BN / 4; ++c)
             st_cluster_v4(dst + (uint32_t)((c * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
                           T[4 * c + 3]);
-          mbar_arrive_remote(mapa_rank(xbar, 0));
-        } else if (clustered) {
+          mbar_arrive_remote(mapa_rank(xbar, (uint32_t)lead_rank), (uint32_t)((S - 1) / (f - 1)));
+        } else if (f > 1) {
           // the other CTAs' partial tiles, added in rank order
           if (!mbar_wait_cluster(xbar, xph, 2 * WAIT_NS)) {
             *abort_flag = 1;
@@ -428,7 +441,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           xph ^= 1;
           if (ok) {
 #pragma unroll 1
-            for (int r = 1; r < S; ++r) {
+            for (int r = 1; r < f; ++r) {
               const float4* src = xbuf + (size_t)(r - 1) * (BN / 4) * 128 + et;
 #pragma unroll
               for (int c = 0; c < BN / 4; ++c) {
@@ -623,21 +636,28 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
     G1 = std::max(G1, acc);
   }
   if (G1 > p->num_sms) return MATPOW_OK;
-  // split-K: 2 or 4 CTAs per tile when the SMs allow it (each keeps >= 1 k-block)
-  int S = 1;
+  // split-K: clusters of S = 2 or 4 CTAs; each level then splits its tiles
+  // over f | S CTAs, the largest f with f x (its tiles) <= G.  The grid is
+  // the smallest multiple of S covering S x (the largest level), capped by
+  // the SMs; at least one level must be able to split, or S = 1.
+  int S = 1, G = G1;
   if (p->chain_mode == 1 && BN == 64) {
+    int minT = 1 << 30;
+    for (int L = 0; L < nlevels; ++L) minT = std::min(minT, (int)P.lvl_begin[L][nj]);
     const int smax = nsl == 3 ? 2 : 4;
     for (int c = smax; c >= 2; c /= 2) {
-      if (G1 * c > p->num_sms || c > minKB) continue;
+      if (c > minKB) continue;
+      const int g = std::min(c * G1, p->num_sms / c * c);
+      if (g < G1 || 2 * minT > g) continue;  // no level could split
       const int mc = nsl == 3 ? chain_max_clusters<64, 3, 2>()
                      : c == 4 ? chain_max_clusters<64, 2, 4>() : chain_max_clusters<64, 2, 2>();
-      if (mc >= G1) {
+      if (mc >= g / c) {
         S = c;
+        G = g;
         break;
       }
     }
   }
-  const int G = G1 * S;
 
   int prep = 0;
   cudaError_t e = cudaSuccess;
@@ -695,12 +715,12 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
   cudaEvent_t ev;
   timed_begin(p, s, &ev);
   if (nsl == 3)
-    e = S == 2 ? chain_launch<64, 3, 2>(&P, G, s) : chain_launch<64, 3, 1>(&P, G1, s);
+    e = S == 2 ? chain_launch<64, 3, 2>(&P, G, s) : chain_launch<64, 3, 1>(&P, G, s);
   else if (BN == 64)
     e = S == 4 ? chain_launch<64, 2, 4>(&P, G, s)
-        : S == 2 ? chain_launch<64, 2, 2>(&P, G, s) : chain_launch<64, 2, 1>(&P, G1, s);
+        : S == 2 ? chain_launch<64, 2, 2>(&P, G, s) : chain_launch<64, 2, 1>(&P, G, s);
   else
-    e = chain_launch<128, 2, 1>(&P, G1, s);
+    e = chain_launch<128, 2, 1>(&P, G, s);
   if (e != cudaSuccess && S > 1) {
     // a cooperative launch with clusters was refused: run without split-K
     cudaGetLastError();
