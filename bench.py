@@ -42,6 +42,14 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 # the summaries under profiles/ give the command.  Reset to None whenever the
 # kernel changes.
 TRAFFIC = {
+    ("single512", "bf16x6"): (1.18e6, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
+                                      "tc_chain_split_kernel<64, 3, 2>, one launch per step "
+                                      "(profiles/tc_chain_kernel_single512.md)"),
+    ("batched4096", "bf16x6"): (9.14e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
+                                        "the 12 level launches of one step "
+                                        "(profiles/tc_fxb_persist_kernel_batched512.md)"),
+    ("modp2048", "bf16x3"): (2.69e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "
+                                     "launches of one step (profiles/tc_modp_kernel_modp2048.md)"),
     ("large8192", "bf16x3"): (3.04e9, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
                                       "tc_fxb_kernel<128, 2> at full size (profiles/tc_fxb_kernel_large8192.md)"),
 }
@@ -663,6 +671,9 @@ def run_modp(args, wk, world, rank, local):
             "frac": achieved / peaks["bf16_tflops"], "traffic": None, "kernel": "tc_modp_kernel",
             "peak_source": peak_src + " bf16 burst", "counted": "4 bfloat16 byte-slice products per term",
             "launches_timed": kl, "avg_launch_us": kms * 1e3 / max(kl, 1)}
+    tr = TRAFFIC.get((args.workload, args.precision))
+    if tr:
+        roof["traffic"], roof["traffic_source"] = tr
     if rank != 0:
         return
     cb = cpu_sample_modp(wk, args.cpu_budget) if world == 1 and not args.no_cpu else None
@@ -844,6 +855,9 @@ def run_batched(args, wk, world, rank, local):
             "peak_source": peak_src + " bf16 burst", "launches_timed": kl,
             "avg_launch_us": kms * 1e3 / max(kl, 1),
             "tiny_chain_share_ms": tms / 2, "level_kernels_ms": kms / 2}
+    tr = TRAFFIC.get((args.workload, args.precision))
+    if tr:
+        roof["traffic"], roof["traffic_source"] = tr
     if rank != 0:
         return
     cb = None
