@@ -88,6 +88,22 @@ __device__ __forceinline__ void slice_n(float v, int e, float (&a)[NSL]) {
   }
 }
 
+// The slice products of one 16-deep k-step into the NSL accumulators at TMEM
+// column t0 (accumulator w at t0 + w BN collects a_i b_j with i + j = w).
+// The B slice planes lie next to each other at the MMA's 64-column chunk
+// stride, so the products that share an A slice go out as one wider MMA:
+// a_i [b_0 | ... | b_(NSL-1-i)] with N = (NSL - i) BN, written to
+// accumulators i .. NSL - 1.  acc = 0 on the k-block's first k-step (the
+// first MMA then initialises every accumulator).  The sums are exact
+// integers, so grouping the products this way changes no result.
+template <int BN, int NSL>
+__device__ __forceinline__ void slice_mmas(uint32_t t0, const uint64_t (&ad)[NSL], uint64_t bd0, uint32_t acc) {
+  static_assert(NSL * BN <= 256, "MMA N");
+#pragma unroll
+  for (int i = 0; i < NSL; ++i)
+    ptx::mma_f16(t0 + (uint32_t)(i * BN), ad[i], bd0, idesc_bf16(128, (NSL - i) * BN), i == 0 ? acc : 1u);
+}
+
 // Named barrier 1 over the NT epilogue threads (warps 4.. of the CTA).
 template <int NT = 128>
 __device__ __forceinline__ void epi_bar() {

@@ -344,7 +344,6 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
         }
       } else if (warp == 1) {
         if (lane == 0) {
-          constexpr uint32_t idesc = idesc_bf16(BM, BN);
           for (int kb = i0; kb < i1; ++kb) {
             const int g = kb_base + kb - i0;
             const int buf = g & 1;
@@ -370,15 +369,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
                 bd[i] = ptx::smem_desc(b0 + i * C::B_BYTES + 2048 * k, 8192, 1024);
               }
               const uint32_t acc = k == 0 ? 0u : 1u;
-              // accumulator w collects the products a_i b_j with i + j = w
-              ptx::mma_f16(t0, ad[0], bd[0], idesc, acc);
-              ptx::mma_f16(t0 + BN, ad[0], bd[1], idesc, acc);
-              ptx::mma_f16(t0 + BN, ad[1], bd[0], idesc, 1);
-              if (NSL == 3) {
-                ptx::mma_f16(t0 + 2 * BN, ad[0], bd[NSL - 1], idesc, acc);
-                ptx::mma_f16(t0 + 2 * BN, ad[1], bd[1], idesc, 1);
-                ptx::mma_f16(t0 + 2 * BN, ad[NSL - 1], bd[0], idesc, 1);
-              }
+              fxb::slice_mmas<BN, NSL>(t0, ad, bd[0], acc);
             }
             ptx::mma_commit(empty0 + 8 * s);
             ptx::mma_commit(accfull0 + 8 * buf);

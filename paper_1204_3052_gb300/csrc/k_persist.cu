@@ -182,7 +182,6 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
       int KB = blockIdx.x < tiles_total ? recs[blockIdx.x].x >> 24 : 0;
       for (int tb = blockIdx.x; tb < tiles_total && !*abort_flag; tb += G) {
         // the next tile's depth, loaded while this tile's MMAs are issued
@@ -212,15 +211,7 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
               bd[i] = ptx::smem_desc(b0 + i * C::B_BYTES + 2048 * k, 8192, 1024);
             }
             const uint32_t acc = k == 0 ? 0u : 1u;
-            // accumulator w collects the products a_i b_j with i + j = w
-            ptx::mma_f16(t0, ad[0], bd[0], idesc, acc);
-            ptx::mma_f16(t0 + BN, ad[0], bd[1], idesc, acc);
-            ptx::mma_f16(t0 + BN, ad[1], bd[0], idesc, 1);
-            if (NSL == 3) {
-              ptx::mma_f16(t0 + 2 * BN, ad[0], bd[NSL - 1], idesc, acc);
-              ptx::mma_f16(t0 + 2 * BN, ad[1], bd[1], idesc, 1);
-              ptx::mma_f16(t0 + 2 * BN, ad[NSL - 1], bd[0], idesc, 1);
-            }
+            fxb::slice_mmas<BN, NSL>(t0, ad, bd[0], acc);
           }
           ptx::mma_commit(empty0 + 8 * s);
           ptx::mma_commit(accfull0 + 8 * buf);
