@@ -124,7 +124,7 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      constexpr uint32_t idesc2 = idesc_bf16(BM, 2 * BN);
       for (int kb = 0; kb < KB; ++kb) {
         const int ch = kb / CHUNK_KB;
         const int buf = ch & 1;
@@ -143,19 +143,17 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
         ptx::tc_fence_after();
         const uint32_t a1 = ptx::smem_u32(smem + s * STAGE_BYTES);
         const uint32_t a0 = a1 + A_BYTES;
-        const uint32_t b1 = a1 + 2 * A_BYTES;
-        const uint32_t b0 = b1 + B_BYTES;
+        const uint32_t b1 = a1 + 2 * A_BYTES;  // y1, then y0 at + B_BYTES (one 64-column chunk)
 #pragma unroll
         for (int k = 0; k < BK / 16; ++k) {
           const uint64_t ad1 = ptx::smem_desc(a1 + 32 * k, 16, 1024);
           const uint64_t ad0 = ptx::smem_desc(a0 + 32 * k, 16, 1024);
           const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
-          const uint64_t bd0 = ptx::smem_desc(b0 + 2048 * k, 8192, 1024);
           const uint32_t acc = (first && k == 0) ? 0u : 1u;
-          ptx::mma_f16(tH, ad1, bd1, idesc, acc);               // H  = x1 y1
-          ptx::mma_f16(tH + BN, ad1, bd0, idesc, acc);          // M1 = x1 y0
-          ptx::mma_f16(tH + 2 * BN, ad0, bd1, idesc, acc);      // M2 = x0 y1
-          ptx::mma_f16(tH + 3 * BN, ad0, bd0, idesc, acc);      // L  = x0 y0
+          // the y1 and y0 planes lie next to each other at the MMA's 64-column
+          // chunk stride: x1 [y1 | y0] -> H | M1 and x0 [y1 | y0] -> M2 | L
+          ptx::mma_f16(tH, ad1, bd1, idesc2, acc);
+          ptx::mma_f16(tH + 2 * BN, ad0, bd1, idesc2, acc);
         }
         ptx::mma_commit(empty0 + 8 * s);
         if (last) ptx::mma_commit(accfull0 + 8 * buf);
