@@ -46,7 +46,10 @@ namespace chain {
 constexpr int BM = 128, BK = 64, THREADS = 256, CHUNK_KB = 4;
 constexpr int MAX_LEVELS = 64;
 constexpr uint64_t WAIT_NS = 2000000000ull;
-constexpr int SMEM_MAX = 227 * 1024;
+// dynamic shared memory: the 227 KB per CTA less the per-level work table
+// (static shared memory, WORK_BYTES)
+constexpr int WORK_BYTES = 24 * MAX_LEVELS;
+constexpr int SMEM_MAX = 227 * 1024 - WORK_BYTES;
 template <int BN, int NSL, int S>
 struct Cfg {
   static constexpr int NG = BN / fxb::BLK;
@@ -194,6 +197,15 @@ __device__ __forceinline__ uint32_t cluster_nctarank() {
   return r;
 }
 
+// One CTA's assignment at one level (24 bytes).
+struct LevelWork {
+  chain::Op op;
+  short pi;  // power, or -1: no tile at this level
+  short f;   // CTAs per tile at this level
+  short t, m0, n0, N;
+};
+static_assert(sizeof(LevelWork) * chain::MAX_LEVELS <= chain::WORK_BYTES, "work table");
+
 template <int BN, int NSL, int S>
 __device__ __forceinline__ void chain_body(const ChainParams& P) {
   using namespace chain;
@@ -243,6 +255,44 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
+  // this CTA's work at every level (tile, power, split), from the launch
+  // tables in parameter space, once: one thread per level
+  __shared__ LevelWork s_work[chain::MAX_LEVELS];
+  for (int L = threadIdx.x; L < P.nlevels; L += blockDim.x) {
+    // the level's split: f CTAs of a cluster share a tile, the largest f
+    // (dividing S) with f x (tiles of the level) <= G; the cluster's S CTAs
+    // then work on S / f tiles
+    const int T_L = P.lvl_begin[L][P.nprob];
+    int f = 1;
+    if (clustered) {
+      f = S;
+      while (f > 1 && f * T_L > (int)G) f >>= 1;
+    }
+    const int t_all = clustered ? (int)(blockIdx.x / S) * (S / f) + crank / f : (int)blockIdx.x;
+    LevelWork w;
+    w.f = (short)f;
+    w.pi = -1;
+    w.t = 0;
+    w.m0 = w.n0 = 0;
+    w.N = (short)P.pr[0].N;
+    w.op = P.pr[0].ops[2 * L];
+    if (t_all < T_L) {
+      int pi = 0;  // the power this CTA group works for at level L
+      while (pi + 1 < P.nprob && t_all >= P.lvl_begin[L][pi + 1]) ++pi;
+      const ChainProblem& Q = P.pr[pi];
+      const int local = t_all - P.lvl_begin[L][pi];
+      const int oi = local / Q.tiles_per_op;
+      const int t = local - oi * Q.tiles_per_op;
+      const int tm = t / Q.tiles_n, tn = t - tm * Q.tiles_n;
+      w.pi = (short)pi;
+      w.t = (short)t;
+      w.op = Q.ops[2 * L + oi];
+      w.N = (short)Q.N;
+      w.m0 = (short)(tm * BM);
+      w.n0 = (short)(tn * BN);
+    }
+    s_work[L] = w;
+  }
   // every CTA of the cluster has started and initialised its barriers before
   // any remote store or arrival
   if (clustered) cluster_sync_all();
@@ -284,34 +334,22 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   uint32_t xph = 0;  // phase of xbar (leader)
   float T[BN];
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
-    // this level's split: f CTAs of a cluster share a tile, the largest f
-    // (dividing S) with f x (tiles of the level) <= G; the cluster's S CTAs
-    // then work on S / f tiles
-    const int T_L = P.lvl_begin[L][P.nprob];
-    int f = 1;
-    if (clustered) {
-      f = S;
-      while (f > 1 && f * T_L > (int)G) f >>= 1;
-    }
+    // this CTA's work at level L, worked out at kernel start
+    const LevelWork W = s_work[L];
+    const int f = W.f;
     const int sub = crank / f;
     const int rank = crank - sub * f;  // rank within the tile's group; 0 leads
     const int lead_rank = sub * f;     // cluster rank of the group's leader
-    const int t_all = clustered ? (int)(blockIdx.x / S) * (S / f) + sub : (int)blockIdx.x;
-    int pi = 0;  // the power this CTA group works for at level L
-    while (pi + 1 < P.nprob && t_all >= P.lvl_begin[L][pi + 1]) ++pi;
-    const bool has = t_all < T_L;
-    const ChainProblem& Q = P.pr[pi];
-    const int local = has ? t_all - P.lvl_begin[L][pi] : 0;
-    const int oi = local / Q.tiles_per_op;
-    const int t = local - oi * Q.tiles_per_op;
-    const chain::Op op = Q.ops[2 * L + oi];
-    const int N = Q.N;
+    const bool has = W.pi >= 0;
+    const ChainProblem& Q = P.pr[has ? W.pi : 0];
+    const int t = W.t;
+    const chain::Op op = W.op;
+    const int N = W.N;
     const int KB = (N + BK - 1) / BK;
     // this CTA's run of the tile's k-blocks (in the rotated visiting order)
     const int i0 = rank * KB / f, i1 = (rank + 1) * KB / f;
     const int nkb = i1 - i0;
-    const int tm = t / Q.tiles_n, tn = t - (t / Q.tiles_n) * Q.tiles_n;
-    const int m0 = tm * BM, n0 = tn * BN;
+    const int m0 = W.m0, n0 = W.n0;
     const int q = warp - 4;
     const int row = m0 + 32 * q + lane;
 
@@ -456,23 +494,24 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
               if (t == 0 && q == 0 && lane == 0 && Q.out_log2) *Q.out_log2 = Ec;
               if (row < N) {
                 float* O = Q.out + (size_t)row * N;
+                if constexpr (BN == 64) {  // 16-byte stores where the rows allow
+                  store_row_f32<BN>(T, O, n0, N, Q.out_log2 != nullptr, Ec, P.status, Q.out);
+                } else {
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                  const int c = n0 + j;
-                  if (c < N) O[c] = Q.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+                  for (int j = 0; j < BN; ++j) {
+                    const int c = n0 + j;
+                    if (c < N) O[c] = Q.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
+                  }
                 }
               }
             }
           } else {
             if (t == 0 && q == 0 && lane == 0) Q.scales[op.sc].E = Ec;
-            if (ok) {  // the ring is idle here: all k-blocks of this tile were consumed
-              const CUtensorMap* cm[NSL];
-#pragma unroll
-              for (int k = 0; k < NSL; ++k) cm[k] = &Q.amap[op.cb][k];
-              fxb::store_slices_tma<BN, 128, NSL>(T, 32 * q + lane, m0, n0, q, lane, N, 0, BN / 64, smem,
-                                                  cm, Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered,
-                                                  q == 0 && lane == 0, n0);
-            }
+            if (ok)  // 16-byte stores straight from registers (the next level's
+                     // copies read them after the grid barrier)
+              fxb::store_slices<BN, 128, NSL>(T, row, m0, n0, q, lane, N, Q.ld, (__nv_bfloat16*)Q.slices[op.cb],
+                                              Q.plane, Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered);
+            __threadfence();  // this thread's stores are visible GPU-wide before the barrier
             fence_proxy_async_global();
           }
         }
