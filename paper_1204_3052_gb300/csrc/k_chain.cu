@@ -206,6 +206,45 @@ struct LevelWork {
 };
 static_assert(sizeof(LevelWork) * chain::MAX_LEVELS <= chain::WORK_BYTES, "work table");
 
+// The end of a tile's level work by the NT epilogue threads that own its rows
+// (q_first: the first of their warps): one verdict over them, then the user
+// output (final product) or the next operand's block exponents and slices.
+template <int BN, int NSL, int NT>
+__device__ __forceinline__ void chain_finish(float (&T)[BN], bool ok, volatile int* epi_ok,
+                                             volatile int* abort_flag, int q, int lane, int row, int t, int m0,
+                                             int n0, int N, const ChainProblem& Q, const chain::Op& op,
+                                             long long Ec, unsigned* status, float* ered, int q_first) {
+  fxb::epi_bar<NT>();
+  if (q == q_first && lane == 0) *epi_ok = ok && !*abort_flag;
+  fxb::epi_bar<NT>();
+  ok = *epi_ok != 0;
+  if (op.last) {
+    if (ok) {
+      if (t == 0 && q == 0 && lane == 0 && Q.out_log2) *Q.out_log2 = Ec;
+      if (row < N) {
+        float* O = Q.out + (size_t)row * N;
+        if constexpr (BN == 64) {  // 16-byte stores where the rows allow
+          store_row_f32<BN>(T, O, n0, N, Q.out_log2 != nullptr, Ec, status, Q.out);
+        } else {
+#pragma unroll
+          for (int j = 0; j < BN; ++j) {
+            const int c = n0 + j;
+            if (c < N) O[c] = Q.out_log2 ? T[j] : final_value(T[j], Ec, status);
+          }
+        }
+      }
+    }
+  } else {
+    if (t == 0 && q == 0 && lane == 0) Q.scales[op.sc].E = Ec;
+    if (ok)  // 16-byte stores straight from registers (the next level's copies
+             // read them after the grid barrier)
+      fxb::store_slices<BN, NT, NSL>(T, row, m0, n0, q, lane, N, Q.ld, (__nv_bfloat16*)Q.slices[op.cb], Q.plane,
+                                     Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered);
+    __threadfence();  // this thread's stores are visible GPU-wide before the barrier
+    fence_proxy_async_global();
+  }
+}
+
 template <int BN, int NSL, int S>
 __device__ __forceinline__ void chain_body(const ChainParams& P) {
   using namespace chain;
@@ -449,8 +488,42 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
         }
         const int et = 32 * q + lane;  // epilogue thread = tile row
-        const bool lead = rank == 0;
-        if (!lead) {
+        // f = 2: the two CTAs of the tile each finish one 64-row block row
+        // (warps q with q / 2 = rank) and send the other rows to the partner;
+        // f = 4: the group's first CTA gathers the other three partial tiles
+        const bool rows2 = f == 2;
+        const bool mine = rows2 ? (q >> 1) == rank : rank == 0;
+        if (rows2) {
+          if (!mine) {
+            // this row belongs to the partner's block row: push it there
+            // (weighted: 64 pushing threads complete the barrier, which is
+            // initialised for (S - 1) x 128 arrivals)
+            const uint32_t prt = (uint32_t)(lead_rank + 1 - rank);
+            const uint32_t dst = mapa_rank(ptx::smem_u32(xbuf), prt);
+#pragma unroll
+            for (int c = 0; c < BN / 4; ++c)
+              st_cluster_v4(dst + (uint32_t)((c * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
+                            T[4 * c + 3]);
+            mbar_arrive_remote(mapa_rank(xbar, prt), (uint32_t)(2 * (S - 1)));
+          } else {
+            if (!mbar_wait_cluster(xbar, xph, 2 * WAIT_NS)) {
+              *abort_flag = 1;
+              ok = false;
+            }
+            if (ok) {
+              const float4* src = xbuf + et;
+#pragma unroll
+              for (int c = 0; c < BN / 4; ++c) {
+                const float4 v = src[c * 128];
+                T[4 * c] += v.x;
+                T[4 * c + 1] += v.y;
+                T[4 * c + 2] += v.z;
+                T[4 * c + 3] += v.w;
+              }
+            }
+          }
+          xph ^= 1;  // both CTAs' barriers complete once per such level
+        } else if (!mine) {
           // push this partial tile into the leader's buffer, then arrive there
           // (weighted so that every split factor completes the leader's
           // barrier, initialised for S - 1 pushing CTAs, in one phase)
@@ -483,37 +556,13 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
             }
           }
         }
-        if (lead) {
-          // one verdict for all four epilogue warps (they share named barriers below)
-          fxb::epi_bar();
-          if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
-          fxb::epi_bar();
-          ok = *epi_ok != 0;
-          if (op.last) {
-            if (ok) {
-              if (t == 0 && q == 0 && lane == 0 && Q.out_log2) *Q.out_log2 = Ec;
-              if (row < N) {
-                float* O = Q.out + (size_t)row * N;
-                if constexpr (BN == 64) {  // 16-byte stores where the rows allow
-                  store_row_f32<BN>(T, O, n0, N, Q.out_log2 != nullptr, Ec, P.status, Q.out);
-                } else {
-#pragma unroll
-                  for (int j = 0; j < BN; ++j) {
-                    const int c = n0 + j;
-                    if (c < N) O[c] = Q.out_log2 ? T[j] : final_value(T[j], Ec, P.status);
-                  }
-                }
-              }
-            }
-          } else {
-            if (t == 0 && q == 0 && lane == 0) Q.scales[op.sc].E = Ec;
-            if (ok)  // 16-byte stores straight from registers (the next level's
-                     // copies read them after the grid barrier)
-              fxb::store_slices<BN, 128, NSL>(T, row, m0, n0, q, lane, N, Q.ld, (__nv_bfloat16*)Q.slices[op.cb],
-                                              Q.plane, Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered);
-            __threadfence();  // this thread's stores are visible GPU-wide before the barrier
-            fence_proxy_async_global();
-          }
+        if (mine) {
+          if (rows2)  // two warps (one block row) share the named barriers
+            chain_finish<BN, NSL, 64>(T, ok, epi_ok, abort_flag, q, lane, row, t, m0, n0, N, Q, op, Ec,
+                                      P.status, ered, 2 * rank);
+          else
+            chain_finish<BN, NSL, 128>(T, ok, epi_ok, abort_flag, q, lane, row, t, m0, n0, N, Q, op, Ec,
+                                       P.status, ered, 0);
         }
       }
       kb_base += nkb;  // ring and accumulator counters advance only with work done
