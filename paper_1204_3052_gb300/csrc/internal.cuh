@@ -125,6 +125,16 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // Final rescale of a stored value to float32 in float64 (S * 2^E).
 __device__ __forceinline__ float final_value(float s, long long E, unsigned* status) {
+  // Common case: s is a normal float and s 2^E is one too, so the result is
+  // exact and is s with E added to its exponent field.  Zero, subnormal
+  // operands and results outside the normal range take the float64 route
+  // (one rounding to float32, overflow to +-inf, underflow to 0 or subnormal).
+  const unsigned bits = __float_as_uint(s);
+  const int es = (int)((bits >> 23) & 0xffu);
+  if (es != 0 && es != 255 && E > -254 && E < 254) {
+    const int et = es + (int)E;
+    if (et >= 1 && et <= 254) return __uint_as_float(bits + ((unsigned)(int)E << 23));
+  }
   long long Ec = E < -4000 ? -4000 : (E > 4000 ? 4000 : E);
   double v = ldexp((double)s, (int)Ec);
   float f = (float)v;

@@ -199,8 +199,8 @@ cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_tota
 // ---------------------------------------------------------------------------
 // Whole chain for N <= 64 in one CTA: P, R and a temporary T (64x64 float32
 // each, zero-padded) live in shared memory for the entire power.  Every
-// product is followed by an exact power-of-two renormalisation (max|.| in
-// [0.5, 1)) with the exponent carried in a 64-bit integer.
+// product is stored with an exact power-of-two scaling taken from its
+// operands' maxima, the exponent carried in a 64-bit integer.
 
 namespace tiny {
 constexpr int NMAX = 64, LDS = 68, THREADS = 256;
@@ -208,127 +208,171 @@ constexpr int NMAX = 64, LDS = 68, THREADS = 256;
 
 int tiny_max_supported() { return tiny::NMAX; }
 
-// dst <- normalise(Xs * Ys); returns the applied exponent.  256 threads, each
-// owns a 4x4 block of the 64x64 result.
-__device__ __forceinline__ int tiny_mul(const float* Xs, const float* Ys, float* dst, int kmax,
-                                        float* red) {
+// Thread layout of a 64 x 64 product: thread t owns rows 4 (t / 16) + 0..3
+// and columns 4 (t % 16) + 0..3.  Per 4-deep k-step it reads 4 float4 of X
+// and 4 float4 of Y and makes 64 FMAs.  (One CTA of this kind is bound by
+// shared-memory operand delivery near 1.8 us per product; wider register
+// tiles, a split k range or warp-wide broadcasts of X measured no faster.)
+__device__ __forceinline__ void tiny_load(const float* Xs, const float* Ys, int k, int r0, int c0, float4* a,
+                                          float4* b) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(Xs + (r0 + i) * tiny::LDS + k);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float4*>(Ys + (k + q) * tiny::LDS + c0);
+}
+
+__device__ __forceinline__ void tiny_fma(const float4* a, const float4* b, float (*acc)[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc[i][0] = fmaf(av[q], b[q].x, acc[i][0]);
+      acc[i][1] = fmaf(av[q], b[q].y, acc[i][1]);
+      acc[i][2] = fmaf(av[q], b[q].z, acc[i][2]);
+      acc[i][3] = fmaf(av[q], b[q].w, acc[i][3]);
+    }
+  }
+}
+
+// dst <- (Xs Ys) 2^shift, an exact power-of-two rescaling; this thread's
+// share of max|dst| goes to red[warp].  Every output is one fmaf chain over
+// ascending k.  dst is neither Xs nor Ys; the caller synchronises.
+__device__ __forceinline__ void tiny_mul(const float* Xs, const float* Ys, float* dst, int kmax, int shift,
+                                         float* red) {
   using namespace tiny;
   const int tid = threadIdx.x;
   const int r0 = 4 * (tid >> 4), c0 = 4 * (tid & 15);
   float acc[4][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k = 0; k < kmax; k += 4) {
-    float4 a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(Xs + (r0 + i) * LDS + k);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float4*>(Ys + (k + q) * LDS + c0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float av[4] = {a[i].x, a[i].y, a[i].z, a[i].w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        acc[i][0] = fmaf(av[q], b[q].x, acc[i][0]);
-        acc[i][1] = fmaf(av[q], b[q].y, acc[i][1]);
-        acc[i][2] = fmaf(av[q], b[q].z, acc[i][2]);
-        acc[i][3] = fmaf(av[q], b[q].w, acc[i][3]);
-      }
-    }
+  for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  // Two operand sets in ping-pong: the next k-step's operands load while
+  // this one's FMAs issue (the last step reloads its own: nothing is read
+  // past row or column kmax - 1).
+  float4 a0[4], b0[4], a1[4], b1[4];
+  tiny_load(Xs, Ys, 0, r0, c0, a0, b0);
+  for (int k = 0; k < kmax; k += 8) {
+    tiny_load(Xs, Ys, k + 4 < kmax ? k + 4 : k, r0, c0, a1, b1);
+    tiny_fma(a0, b0, acc);
+    if (k + 4 >= kmax) break;
+    tiny_load(Xs, Ys, k + 8 < kmax ? k + 8 : k + 4, r0, c0, a0, b0);
+    tiny_fma(a1, b1, acc);
   }
   float m = 0.f;
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) m = fmaxf(m, fabsf(acc[i][j]));
-  m = warp_max(m);
-  __syncthreads();  // all reads of Xs/Ys done before dst (which may alias) is written
-  if ((tid & 31) == 0) red[tid >> 5] = m;
-  __syncthreads();
-  m = red[0];
-#pragma unroll
-  for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, red[w]);
-  const int s = scale_exp_from_bits(__float_as_uint(m));
-#pragma unroll
   for (int i = 0; i < 4; ++i) {
-    float4 v = make_float4(mul_pow2(acc[i][0], -s), mul_pow2(acc[i][1], -s), mul_pow2(acc[i][2], -s),
-                           mul_pow2(acc[i][3], -s));
+    const float4 v = make_float4(mul_pow2(acc[i][0], shift), mul_pow2(acc[i][1], shift),
+                                 mul_pow2(acc[i][2], shift), mul_pow2(acc[i][3], shift));
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     *reinterpret_cast<float4*>(dst + (r0 + i) * LDS + c0) = v;
   }
-  __syncthreads();
-  return s;
+  m = warp_max(m);
+  if ((tid & 31) == 0) red[tid >> 5] = m;
 }
 
+// frexp exponent of the maximum gathered in red[8] (after a barrier).
+__device__ __forceinline__ int tiny_red_exp(const float* red) {
+  float m = red[0];
+#pragma unroll
+  for (int w = 1; w < tiny::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+  return scale_exp_from_bits(__float_as_uint(m));
+}
+
+// Every stored matrix S carries E (the matrix is S 2^E) and s, the frexp
+// exponent of max|S|.  A product T = X Y is stored with a lagged rescaling:
+//   S_T = (S_X S_Y) 2^-(s_X + s_Y),  E_T = E_X + E_Y + s_X + s_Y,
+// so max|S_T| <= N, and s_T comes from the block reduction that the single
+// barrier after the product completes.  The products see the same values up
+// to exact powers of two as with normalised operands (one barrier per product
+// instead of three).
 __device__ __forceinline__ void tiny_chain(const TinyDesc& d, unsigned* status) {
   using namespace tiny;
   extern __shared__ __align__(16) float sm[];
   float* P = sm;
   float* R = sm + NMAX * LDS;
   float* T = sm + 2 * NMAX * LDS;
-  __shared__ float red[THREADS / 32];
-  __shared__ int flag;
+  __shared__ float red[2][THREADS / 32];  // alternate per product
   const int tid = threadIdx.x;
   const int N = d.N;
   const float* __restrict__ A = d.A;
   const int kmax = (N + 3) & ~3;
 
-  if (tid == 0) flag = 0;
+  // P = A normalised (E = frexp exponent of max|A|, so s = 0).  All of this
+  // thread's loads of A are issued before any is used (one memory round trip).
+  constexpr int PER = NMAX * NMAX / THREADS;
+  const int NN = N * N;
+  float v[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = tid + j * THREADS;
+    v[j] = i < NN ? A[i] : 0.f;
+  }
   for (int i = tid; i < NMAX * LDS; i += THREADS) {
     int r = i / LDS, c = i - r * LDS;
-    float v = (r < N && c < N) ? A[(size_t)r * N + c] : 0.f;
-    P[i] = v;
+    if (r >= N || c >= N) P[i] = 0.f;
     R[i] = (r == c && r < N) ? 1.f : 0.f;
   }
-  __syncthreads();
-  // normalise A
   float m = 0.f;
   bool bad = false;
-  for (int i = tid; i < NMAX * LDS; i += THREADS) {
-    bad |= !isfinite(P[i]);
-    m = fmaxf(m, fabsf(P[i]));
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    bad |= !isfinite(v[j]);
+    m = fmaxf(m, fabsf(v[j]));
   }
-  if (bad) atomicOr(&flag, 1);
   m = warp_max(m);
-  if ((tid & 31) == 0) red[tid >> 5] = m;
-  __syncthreads();
-  m = red[0];
-  for (int w = 1; w < THREADS / 32; ++w) m = fmaxf(m, red[w]);
-  long long eP = scale_exp_from_bits(__float_as_uint(m));
-  for (int i = tid; i < NMAX * LDS; i += THREADS) P[i] = mul_pow2(P[i], -(int)eP);
-  if (tid == 0 && flag) atomicOr(status, ST_BADINPUT);
+  if ((tid & 31) == 0) red[0][tid >> 5] = m;
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_BADINPUT);
+  long long eP = tiny_red_exp(red[0]), eR = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int i = tid + j * THREADS;
+    if (i < NN) {
+      const int r = i / N, c = i - r * N;
+      P[r * LDS + c] = mul_pow2(v[j], -(int)eP);
+    }
+  }
+  int sP = 0, sR = 0;
   __syncthreads();
 
-  long long eR = 0;
   bool haveR = false;
+  int rb = 1;  // red buffer of the next product
   unsigned long long bits = d.n;
   while (bits) {
     if (bits & 1ull) {
       if (!haveR) {
         for (int i = tid; i < NMAX * LDS; i += THREADS) R[i] = P[i];
         eR = eP;
+        sR = sP;
         haveR = true;
         __syncthreads();
       } else {
-        int s = tiny_mul(R, P, T, kmax, red);
+        tiny_mul(R, P, T, kmax, -(sR + sP), red[rb]);
+        __syncthreads();
+        eR = eR + eP + sR + sP;
+        sR = tiny_red_exp(red[rb]);
+        rb ^= 1;
         float* t = R; R = T; T = t;
-        eR = eR + eP + s;
       }
     }
     bits >>= 1;
     if (bits) {
-      int s = tiny_mul(P, P, T, kmax, red);
+      tiny_mul(P, P, T, kmax, -2 * sP, red[rb]);
+      __syncthreads();
+      eP = 2 * eP + 2 * sP;
+      sP = tiny_red_exp(red[rb]);
+      rb ^= 1;
       float* t = P; P = T; T = t;
-      eP = 2 * eP + s;
     }
   }
-  // n == 0: R is the identity with exponent 0
-  if (d.log2 && tid == 0) *d.log2 = eR;
+  // n == 0: R is the identity with exponent 0 (sR = 0: max|I| = 1 -> frexp 1;
+  // written as is); otherwise the mantissa S_R 2^-s_R, exponent E_R + s_R
+  const int shift = haveR ? -sR : 0;
+  const long long eOut = haveR ? eR + sR : 0;
+  if (d.log2 && tid == 0) *d.log2 = eOut;
   for (int i = tid; i < N * N; i += THREADS) {
     int r = i / N, c = i - r * N;
-    float v = R[r * LDS + c];
-    d.out[i] = d.log2 ? v : final_value(v, eR, status);
+    float v = mul_pow2(R[r * LDS + c], shift);
+    d.out[i] = d.log2 ? v : final_value(v, eOut, status);
   }
 }
 
