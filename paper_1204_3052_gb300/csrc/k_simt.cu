@@ -270,11 +270,94 @@ __device__ __forceinline__ void tiny_mul(const float* Xs, const float* Ys, float
   if ((tid & 31) == 0) red[tid >> 5] = m;
 }
 
-// frexp exponent of the maximum gathered in red[8] (after a barrier).
+// ---- four-CTA cluster form of the same chain (single powers): each CTA of a
+// 2 x 2 cluster computes one 32 x 32 quadrant of every product and stores it
+// into all four CTAs' copies of the result through distributed shared memory.
+namespace tinyc {
+constexpr int C = 4;
+__device__ __forceinline__ uint32_t ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of the four CTAs executes the same sequence of these barriers
+// (once after the set-up and once per product), so none waits for a thread
+// that never arrives.
+__device__ __forceinline__ void barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t peer(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_v2(uint32_t a, float x, float y) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ void st_f32(uint32_t a, float x) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(x) : "memory");
+}
+}  // namespace tinyc
+
+// Quadrant (rq, cq) of dst <- (Xs Ys) 2^shift in every CTA of the cluster;
+// thread t owns rows rq + 2 (t / 16) + 0..1 and columns cq + 2 (t % 16) + 0..1
+// (one fmaf chain over ascending k per output, as in tiny_mul, so both forms
+// give identical bits).  Each warp's max|.| goes to red[8 rank + warp] of
+// every CTA.  The caller runs the cluster barrier after the call.
+__device__ __forceinline__ void tinyc_mul(const float* Xs, const float* Ys, float* dst, int kmax, int shift,
+                                          float* red, uint32_t rank) {
+  using namespace tiny;
+  const int tid = threadIdx.x;
+  const int r = 32 * (int)(rank >> 1) + 2 * (tid >> 4), c = 32 * (int)(rank & 1) + 2 * (tid & 15);
+  float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  for (int k = 0; k < kmax; k += 4) {
+    const float4 a0 = *reinterpret_cast<const float4*>(Xs + r * LDS + k);
+    const float4 a1 = *reinterpret_cast<const float4*>(Xs + (r + 1) * LDS + k);
+    float2 b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = *reinterpret_cast<const float2*>(Ys + (k + q) * LDS + c);
+    const float av[2][4] = {{a0.x, a0.y, a0.z, a0.w}, {a1.x, a1.y, a1.z, a1.w}};
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[i][0] = fmaf(av[i][q], b[q].x, acc[i][0]);
+        acc[i][1] = fmaf(av[i][q], b[q].y, acc[i][1]);
+      }
+  }
+  float m = 0.f;
+  float v[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    v[i][0] = mul_pow2(acc[i][0], shift);
+    v[i][1] = mul_pow2(acc[i][1], shift);
+    m = fmaxf(m, fmaxf(fabsf(v[i][0]), fabsf(v[i][1])));
+  }
+  *reinterpret_cast<float2*>(dst + r * LDS + c) = make_float2(v[0][0], v[0][1]);
+  *reinterpret_cast<float2*>(dst + (r + 1) * LDS + c) = make_float2(v[1][0], v[1][1]);
+#pragma unroll
+  for (uint32_t p = 1; p < (uint32_t)tinyc::C; ++p) {
+    const uint32_t q = (rank + p) % tinyc::C;
+    tinyc::st_v2(tinyc::peer(dst + r * LDS + c, q), v[0][0], v[0][1]);
+    tinyc::st_v2(tinyc::peer(dst + (r + 1) * LDS + c, q), v[1][0], v[1][1]);
+  }
+  m = warp_max(m);
+  if ((tid & 31) == 0) {
+    red[8 * rank + (tid >> 5)] = m;
+#pragma unroll
+    for (uint32_t p = 1; p < (uint32_t)tinyc::C; ++p)
+      tinyc::st_f32(tinyc::peer(red + 8 * rank + (tid >> 5), (rank + p) % tinyc::C), m);
+  }
+}
+
+// frexp exponent of the maximum gathered in red[W] (after a barrier).
+template <int W>
 __device__ __forceinline__ int tiny_red_exp(const float* red) {
   float m = red[0];
 #pragma unroll
-  for (int w = 1; w < tiny::THREADS / 32; ++w) m = fmaxf(m, red[w]);
+  for (int w = 1; w < W; ++w) m = fmaxf(m, red[w]);
   return scale_exp_from_bits(__float_as_uint(m));
 }
 
@@ -285,14 +368,17 @@ __device__ __forceinline__ int tiny_red_exp(const float* red) {
 // barrier after the product completes.  The products see the same values up
 // to exact powers of two as with normalised operands (one barrier per product
 // instead of three).
+template <bool CL>
 __device__ __forceinline__ void tiny_chain(const TinyDesc& d, unsigned* status) {
   using namespace tiny;
+  constexpr int W = CL ? 8 * tinyc::C : THREADS / 32;  // maxima gathered per product
   extern __shared__ __align__(16) float sm[];
   float* P = sm;
   float* R = sm + NMAX * LDS;
   float* T = sm + 2 * NMAX * LDS;
-  __shared__ float red[2][THREADS / 32];  // alternate per product
+  __shared__ float red[2][W];  // alternate per product
   const int tid = threadIdx.x;
+  const uint32_t rank = CL ? tinyc::ctarank() : 0u;
   const int N = d.N;
   const float* __restrict__ A = d.A;
   const int kmax = (N + 3) & ~3;
@@ -321,8 +407,8 @@ __device__ __forceinline__ void tiny_chain(const TinyDesc& d, unsigned* status) 
   }
   m = warp_max(m);
   if ((tid & 31) == 0) red[0][tid >> 5] = m;
-  if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_BADINPUT);
-  long long eP = tiny_red_exp(red[0]), eR = 0;
+  if (__syncthreads_or(bad) && tid == 0 && rank == 0) atomicOr(status, ST_BADINPUT);
+  long long eP = tiny_red_exp<THREADS / 32>(red[0]), eR = 0;
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
     const int i = tid + j * THREADS;
@@ -332,7 +418,10 @@ __device__ __forceinline__ void tiny_chain(const TinyDesc& d, unsigned* status) 
     }
   }
   int sP = 0, sR = 0;
-  __syncthreads();
+  if (CL)
+    tinyc::barrier();  // every CTA has started and set up before any remote store
+  else
+    __syncthreads();
 
   bool haveR = false;
   int rb = 1;  // red buffer of the next product
@@ -346,20 +435,30 @@ __device__ __forceinline__ void tiny_chain(const TinyDesc& d, unsigned* status) 
         haveR = true;
         __syncthreads();
       } else {
-        tiny_mul(R, P, T, kmax, -(sR + sP), red[rb]);
-        __syncthreads();
+        if (CL) {
+          tinyc_mul(R, P, T, kmax, -(sR + sP), red[rb], rank);
+          tinyc::barrier();
+        } else {
+          tiny_mul(R, P, T, kmax, -(sR + sP), red[rb]);
+          __syncthreads();
+        }
         eR = eR + eP + sR + sP;
-        sR = tiny_red_exp(red[rb]);
+        sR = tiny_red_exp<W>(red[rb]);
         rb ^= 1;
         float* t = R; R = T; T = t;
       }
     }
     bits >>= 1;
     if (bits) {
-      tiny_mul(P, P, T, kmax, -2 * sP, red[rb]);
-      __syncthreads();
+      if (CL) {
+        tinyc_mul(P, P, T, kmax, -2 * sP, red[rb], rank);
+        tinyc::barrier();
+      } else {
+        tiny_mul(P, P, T, kmax, -2 * sP, red[rb]);
+        __syncthreads();
+      }
       eP = 2 * eP + 2 * sP;
-      sP = tiny_red_exp(red[rb]);
+      sP = tiny_red_exp<W>(red[rb]);
       rb ^= 1;
       float* t = P; P = T; T = t;
     }
@@ -368,36 +467,50 @@ __device__ __forceinline__ void tiny_chain(const TinyDesc& d, unsigned* status) 
   // written as is); otherwise the mantissa S_R 2^-s_R, exponent E_R + s_R
   const int shift = haveR ? -sR : 0;
   const long long eOut = haveR ? eR + sR : 0;
-  if (d.log2 && tid == 0) *d.log2 = eOut;
-  for (int i = tid; i < N * N; i += THREADS) {
+  if (d.log2 && tid == 0 && rank == 0) *d.log2 = eOut;
+  // the cluster's CTAs write row blocks of 16 (no remote store follows the
+  // last barrier, so a CTA may exit while the others still write)
+  const int rbeg = CL ? 16 * (int)rank : 0, rend = CL ? min(N, rbeg + 16) : N;
+  for (int i = rbeg * N + tid; i < rend * N; i += THREADS) {
     int r = i / N, c = i - r * N;
     float v = mul_pow2(R[r * LDS + c], shift);
     d.out[i] = d.log2 ? v : final_value(v, eOut, status);
   }
 }
 
+__global__ void __cluster_dims__(tinyc::C, 1, 1) __launch_bounds__(tiny::THREADS, 1)
+    tiny_cluster_kernel(const TinyDesc d, unsigned* status) {
+  tiny_chain<true>(d, status);
+}
+
 __global__ void __launch_bounds__(tiny::THREADS, 1) tiny_one_kernel(const TinyDesc d, unsigned* status) {
-  tiny_chain(d, status);
+  tiny_chain<false>(d, status);
 }
 
 __global__ void __launch_bounds__(tiny::THREADS, 1)
     tiny_group_kernel(const TinyDesc* __restrict__ descs, unsigned* status) {
   TinyDesc d = descs[blockIdx.x];
-  tiny_chain(d, status);
+  tiny_chain<false>(d, status);
 }
 
 static constexpr int kTinySmem = 3 * tiny::NMAX * tiny::LDS * (int)sizeof(float);
 
 cudaError_t tiny_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(tiny_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(tiny_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kTinySmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tiny_one_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTinySmem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(tiny_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               kTinySmem);
 }
 
 cudaError_t launch_tiny_one(const TinyDesc& d, unsigned* status, cudaStream_t s) {
-  tiny_one_kernel<<<1, tiny::THREADS, kTinySmem, s>>>(d, status);
+  // Up to N = 32 a product is cheaper than the cluster's exchange and barrier.
+  if (d.N > 32)
+    tiny_cluster_kernel<<<tinyc::C, tiny::THREADS, kTinySmem, s>>>(d, status);
+  else
+    tiny_one_kernel<<<1, tiny::THREADS, kTinySmem, s>>>(d, status);
   return cudaGetLastError();
 }
 

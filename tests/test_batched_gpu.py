@@ -167,3 +167,30 @@ def test_few_powers_run_side_by_side_in_one_chain(prec):
                 err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
                 assert err <= gate(n, floor_for(prec, A, n, M, e)), (mode, Ns[i], n, err)
         plan.close()
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 17, 32, 33, 40, 63, 64])
+def test_tiny_single_forms_match_group_kernel_bitwise(N):
+    # orders up to 64: a single call runs the whole chain in one CTA (N <= 32)
+    # or in a four-CTA cluster that exchanges quadrants through distributed
+    # shared memory; a batch runs one CTA per matrix.  All three form every
+    # output as the same fmaf chain, so the bits agree.
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    ns = [2, 3, 100, (1 << 20) + 5]
+    As = [wl.gaussian(N, 40 + N), wl.stochastic_exact(N, 41 + N)]
+    plan = mpw.Plan(64, "fp32")
+    for A in As:
+        dA = to_dev(A)
+        lg = torch.zeros(len(ns), dtype=torch.int64, device="cuda")
+        outs = plan.batched([dA] * len(ns), ns, log2=lg)
+        plan.check()
+        for i, n in enumerate(ns):
+            alone, alone_lg = plan.f32(dA, n, mantissa=True)
+            plan.check()
+            assert torch.equal(alone, outs[i]) and int(alone_lg.item()) == int(lg[i].item()), (N, n)
+            if n <= 100:
+                M, e, _ = oracle.matpow_f64(A, n)
+                err = oracle.rel_frobenius(alone.cpu().numpy(), int(alone_lg.item()), M, e)
+                assert err <= gate(n, floor_for("fp32", A, n, M, e)), (N, n, err)
+    plan.close()
