@@ -542,6 +542,12 @@ def run_ours(args, wk, world, rank, local):
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "simt_gemm" if kind == mpw.KERNEL_SIMT else "tiny_chain",
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+        if kind == mpw.KERNEL_TINY:
+            # the chain is a dependent sequence of products on the SMs of one
+            # CTA (N <= 32) or one four-CTA cluster: their share of the peak
+            sms = 4 if N > 32 else 1
+            roof["sms_used"] = sms
+            roof["frac_of_sms_used"] = achieved / (peak * sms / 152)
     roof["launches_timed"] = kl
     roof["avg_launch_us"] = kms * 1e3 / max(kl, 1)
     tr = TRAFFIC.get((args.workload, prec))

@@ -12,7 +12,7 @@
 // with Barrett reductions; a non-final product writes c's byte slices straight
 // into the next product's operand planes.
 //
-// CTA: 384 threads.  Warp 0 TMA, warp 1 MMA (4 MMAs per 16-deep step), warp 2
+// CTA: 384 threads.  Warp 0 TMA, warp 1 MMA (2 MMAs per 16-deep step), warp 2
 // TMEM (2 buffers x 4 accumulators x 64 columns = 512), warps 4-11 epilogue
 // (lane quadrant w % 4, column half (w - 4) / 4).  Every wait is bounded.
 #include <cuda.h>
@@ -44,11 +44,22 @@ __device__ __forceinline__ unsigned barrett(unsigned x, unsigned p, unsigned m) 
   return r >= p ? r - p : r;
 }
 
-// One 128 x 64 output tile t of product d; ax1/ax0: the high / low byte
-// slices of X as the A operand, by1/by0: those of Y as the B operand.
-__device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtensorMap* ax1,
-                                         const CUtensorMap* ax0, const CUtensorMap* by1,
-                                         const CUtensorMap* by0, unsigned* status) {
+// One output tile: its product, the operands' TMA descriptors (ax1/ax0: the
+// high / low byte slices of X as the A operand, by1/by0: those of Y as the B
+// operand) and its index within the product.
+struct ModpTile {
+  const GemmDesc* d;
+  const CUtensorMap *ax1, *ax0, *by1, *by0;
+  int t;
+};
+
+// Tiles blockIdx.x, blockIdx.x + gridDim.x, ... of the launch's `total`
+// 128 x 64 output tiles (tile_of(i) -> ModpTile).  The producer, MMA and
+// epilogue roles run through the same tile sequence with running k-block and
+// chunk counters, so with a grid below `total` (persistent) the next tile's
+// loads and products proceed while the epilogue finishes the last one.
+template <class TileOf>
+__device__ __forceinline__ void modp_tiles(int total, TileOf tile_of, unsigned* status) {
   using namespace tcm;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -61,14 +72,7 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
   const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
   const uint32_t accempty0 = ptx::smem_u32(bars + 2 * STAGES + 2);
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int tm, tn;
-  tile_raster(t, (d.N + BM - 1) / BM, d.tiles_n, &tm, &tn);
-  const int m0 = tm * BM, n0 = tn * BN;
-  const int N = d.N;
-  const int KB = (N + BK - 1) / BK;
-  const int NCH = (KB + CHUNK_KB - 1) / CHUNK_KB;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -87,11 +91,12 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
     ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
     ptx::tmem_relinquish();
   }
-  if (warp == 0 && lane == 0) {
-    ptx::prefetch_tmap(ax1);
-    ptx::prefetch_tmap(ax0);
-    ptx::prefetch_tmap(by1);
-    ptx::prefetch_tmap(by0);
+  if (warp == 0 && lane == 0 && (int)blockIdx.x < total) {
+    const ModpTile f = tile_of((int)blockIdx.x);
+    ptx::prefetch_tmap(f.ax1);
+    ptx::prefetch_tmap(f.ax0);
+    ptx::prefetch_tmap(f.by1);
+    ptx::prefetch_tmap(f.by0);
   }
   ptx::tc_fence_before();
   __syncthreads();
@@ -100,63 +105,82 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % STAGES;
-        if (!ptx::mbar_wait(empty0 + 8 * s, ((kb / STAGES) & 1) ^ 1, abort_flag, WAIT_NS)) {
-          *abort_flag = 1;
-          break;
+      int g = 0;  // k-blocks issued so far (all tiles)
+      bool ok = true;
+      for (int i = blockIdx.x; ok && i < total; i += gridDim.x) {
+        const ModpTile f = tile_of(i);
+        int tm, tn;
+        tile_raster(f.t, (f.d->N + BM - 1) / BM, f.d->tiles_n, &tm, &tn);
+        const int m0 = tm * BM, n0 = tn * BN;
+        const int KB = (f.d->N + BK - 1) / BK;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!ptx::mbar_wait(empty0 + 8 * s, ((g / STAGES) & 1) ^ 1, abort_flag, WAIT_NS)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + 8 * s;
+          ptx::mbar_expect_tx(fb, STAGE_BYTES);
+          const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
+          const int kx = kb * BK;
+          ptx::tma_load_2d(base, f.ax1, kx, m0, fb);                          // x1
+          ptx::tma_load_2d(base + A_BYTES, f.ax0, kx, m0, fb);                // x0
+          ptx::tma_load_2d(base + 2 * A_BYTES, f.by1, n0, kx, fb);            // y1
+          ptx::tma_load_2d(base + 2 * A_BYTES + B_BYTES, f.by0, n0, kx, fb);  // y0
         }
-        const uint32_t fb = full0 + 8 * s;
-        ptx::mbar_expect_tx(fb, STAGE_BYTES);
-        const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
-        const int kx = kb * BK;
-        ptx::tma_load_2d(base, ax1, kx, m0, fb);                          // x1
-        ptx::tma_load_2d(base + A_BYTES, ax0, kx, m0, fb);                // x0
-        ptx::tma_load_2d(base + 2 * A_BYTES, by1, n0, kx, fb);            // y1
-        ptx::tma_load_2d(base + 2 * A_BYTES + B_BYTES, by0, n0, kx, fb);  // y0
-        ++issued;
       }
-      for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb) {
+      // no copy may still be writing shared memory when the CTA exits
+      for (int k = g - STAGES < 0 ? 0 : g - STAGES; k < g; ++k) {
         int dummy = 0;
-        ptx::mbar_wait(full0 + 8 * (kb % STAGES), (kb / STAGES) & 1, &dummy, WAIT_NS);
+        ptx::mbar_wait(full0 + 8 * (k % STAGES), (k / STAGES) & 1, &dummy, WAIT_NS);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       constexpr uint32_t idesc2 = idesc_bf16(BM, 2 * BN);
-      for (int kb = 0; kb < KB; ++kb) {
-        const int ch = kb / CHUNK_KB;
-        const int buf = ch & 1;
-        const bool first = (kb % CHUNK_KB) == 0;
-        const bool last = (kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1;
-        const uint32_t tH = tmem + (uint32_t)(buf * 4 * BN);
-        if (first && !ptx::mbar_wait(accempty0 + 8 * buf, ((ch >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
-          *abort_flag = 1;
-          break;
-        }
-        const int s = kb % STAGES;
-        if (!ptx::mbar_wait(full0 + 8 * s, (kb / STAGES) & 1, abort_flag, WAIT_NS)) {
-          *abort_flag = 1;
-          break;
-        }
-        ptx::tc_fence_after();
-        const uint32_t a1 = ptx::smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t a0 = a1 + A_BYTES;
-        const uint32_t b1 = a1 + 2 * A_BYTES;  // y1, then y0 at + B_BYTES (one 64-column chunk)
+      int g = 0, gc = 0;  // k-blocks and chunks consumed so far (all tiles)
+      bool ok = true;
+      for (int i = blockIdx.x; ok && i < total; i += gridDim.x) {
+        const ModpTile f = tile_of(i);
+        const int KB = (f.d->N + BK - 1) / BK;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const bool first = (kb % CHUNK_KB) == 0;
+          const bool last = (kb % CHUNK_KB) == CHUNK_KB - 1 || kb == KB - 1;
+          const int buf = gc & 1;
+          const uint32_t tH = tmem + (uint32_t)(buf * 4 * BN);
+          if (first && !ptx::mbar_wait(accempty0 + 8 * buf, ((gc >> 1) & 1) ^ 1, abort_flag, WAIT_NS)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          const int s = g % STAGES;
+          if (!ptx::mbar_wait(full0 + 8 * s, (g / STAGES) & 1, abort_flag, WAIT_NS)) {
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t a1 = ptx::smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t a0 = a1 + A_BYTES;
+          const uint32_t b1 = a1 + 2 * A_BYTES;  // y1, then y0 at + B_BYTES (one 64-column chunk)
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ad1 = ptx::smem_desc(a1 + 32 * k, 16, 1024);
-          const uint64_t ad0 = ptx::smem_desc(a0 + 32 * k, 16, 1024);
-          const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
-          const uint32_t acc = (first && k == 0) ? 0u : 1u;
-          // the y1 and y0 planes lie next to each other at the MMA's 64-column
-          // chunk stride: x1 [y1 | y0] -> H | M1 and x0 [y1 | y0] -> M2 | L
-          ptx::mma_f16(tH, ad1, bd1, idesc2, acc);
-          ptx::mma_f16(tH + 2 * BN, ad0, bd1, idesc2, acc);
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t ad1 = ptx::smem_desc(a1 + 32 * k, 16, 1024);
+            const uint64_t ad0 = ptx::smem_desc(a0 + 32 * k, 16, 1024);
+            const uint64_t bd1 = ptx::smem_desc(b1 + 2048 * k, 8192, 1024);
+            const uint32_t acc = (first && k == 0) ? 0u : 1u;
+            // the y1 and y0 planes lie next to each other at the MMA's 64-column
+            // chunk stride: x1 [y1 | y0] -> H | M1 and x0 [y1 | y0] -> M2 | L
+            ptx::mma_f16(tH, ad1, bd1, idesc2, acc);
+            ptx::mma_f16(tH + 2 * BN, ad0, bd1, idesc2, acc);
+          }
+          ptx::mma_commit(empty0 + 8 * s);
+          if (last) {
+            ptx::mma_commit(accfull0 + 8 * buf);
+            ++gc;
+          }
         }
-        ptx::mma_commit(empty0 + 8 * s);
-        if (last) ptx::mma_commit(accfull0 + 8 * buf);
       }
       ptx::mma_commit(drainb);
       int dummy = 0;
@@ -165,44 +189,51 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
   } else if (warp >= 4) {
     const int q = warp & 3;
     const int cs = (warp - 4) >> 2;
-    const int row = m0 + 32 * q + lane;
-    const int nw = n0 + cs * WC;
-    unsigned Ht[WC], Mt[WC], Lt[WC];
-#pragma unroll
-    for (int j = 0; j < WC; ++j) Ht[j] = Mt[j] = Lt[j] = 0u;
+    int gc = 0;  // chunks drained so far (all tiles)
     bool ok = true;
-    for (int ch = 0; ch < NCH; ++ch) {
-      const int buf = ch & 1;
-      int dummy = 0;
-      if (!ptx::mbar_wait(accfull0 + 8 * buf, (ch >> 1) & 1, &dummy, 2 * WAIT_NS)) {
-        *abort_flag = 1;
-        ok = false;
-        break;
+    for (int i = blockIdx.x; ok && i < total; i += gridDim.x) {
+      const ModpTile f = tile_of(i);
+      const GemmDesc& d = *f.d;
+      const int N = d.N;
+      int tm, tn;
+      tile_raster(f.t, (N + BM - 1) / BM, d.tiles_n, &tm, &tn);
+      const int row = tm * BM + 32 * q + lane;
+      const int nw = tn * BN + cs * WC;
+      const int NCH = ((N + BK - 1) / BK + CHUNK_KB - 1) / CHUNK_KB;
+      unsigned Ht[WC], Mt[WC], Lt[WC];
+#pragma unroll
+      for (int j = 0; j < WC; ++j) Ht[j] = Mt[j] = Lt[j] = 0u;
+      for (int ch = 0; ch < NCH; ++ch, ++gc) {
+        const int buf = gc & 1;
+        if (!ptx::mbar_wait(accfull0 + 8 * buf, (gc >> 1) & 1, abort_flag, 2 * WAIT_NS)) {
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 4 * BN + cs * WC);
+        uint32_t r[32];
+        ptx::tmem_ld_32x32b_x32(tq, r);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < WC; ++j) Ht[j] += (unsigned)__uint_as_float(r[j]);
+        ptx::tmem_ld_32x32b_x32(tq + BN, r);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
+        ptx::tmem_ld_32x32b_x32(tq + 2 * BN, r);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
+        ptx::tmem_ld_32x32b_x32(tq + 3 * BN, r);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < WC; ++j) Lt[j] += (unsigned)__uint_as_float(r[j]);
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
       }
-      ptx::tc_fence_after();
-      const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 4 * BN + cs * WC);
-      uint32_t r[32];
-      ptx::tmem_ld_32x32b_x32(tq, r);
-      ptx::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < WC; ++j) Ht[j] += (unsigned)__uint_as_float(r[j]);
-      ptx::tmem_ld_32x32b_x32(tq + BN, r);
-      ptx::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
-      ptx::tmem_ld_32x32b_x32(tq + 2 * BN, r);
-      ptx::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
-      ptx::tmem_ld_32x32b_x32(tq + 3 * BN, r);
-      ptx::tmem_ld_wait();
-#pragma unroll
-      for (int j = 0; j < WC; ++j) Lt[j] += (unsigned)__uint_as_float(r[j]);
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
-    }
-    if (ok && !*abort_flag && row < N) {
+      if (!ok || *abort_flag || row >= N) continue;
       const unsigned pm = d.p;
       const unsigned bm = (unsigned)(0x100000000ull / pm);
       const unsigned c16 = (unsigned)((1ull << 16) % pm), c8 = 256u % pm;
@@ -252,30 +283,39 @@ __device__ __forceinline__ void modp_cta(const GemmDesc& d, int t, const CUtenso
   if (threadIdx.x == 0 && *abort_flag) atomicOr(status, ST_TIMEOUT);
 }
 
+// Products of one level (one or two of the same order), persistent: grid =
+// min(tiles, SMs).
 __global__ void __launch_bounds__(tcm::THREADS, 1)
-    tc_modp_kernel(const __grid_constant__ TcPairParams P, unsigned* status) {
-  int t = blockIdx.x;
-  const int which = (P.count > 1 && t >= P.tiles0) ? 1 : 0;
-  if (which) t -= P.tiles0;
-  const TcProblem& pr = P.p[which];
-  modp_cta(pr.d, t, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], status);
+    tc_modp_kernel(const __grid_constant__ TcPairParams P, int total, unsigned* status) {
+  modp_tiles(
+      total,
+      [&](int i) {
+        const int which = (P.count > 1 && i >= P.tiles0) ? 1 : 0;
+        const TcProblem& pr = P.p[which];
+        return ModpTile{&pr.d, &pr.ax[0], &pr.ax[1], &pr.by[0], &pr.by[1], which ? i - P.tiles0 : i};
+      },
+      status);
 }
 
 // Grouped launch (server): products from a device table, each buffer's four
 // TMA descriptors {x1, x0 as A; y1, y0 as B} from a device table at map_x
-// (A role: + 0, 1) and map_y (B role: + 2, 3).
+// (A role: + 0, 1) and map_y (B role: + 2, 3).  One CTA per tile.
 __global__ void __launch_bounds__(tcm::THREADS, 1)
     tc_modp_group_kernel(const GemmDesc* __restrict__ descs, int count,
-                         const CUtensorMap* __restrict__ maps, unsigned* status) {
-  const int tb = blockIdx.x;
-  int lo = 0, hi = count - 1;  // last desc with tile_begin <= tb
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (descs[mid].tile_begin <= tb) lo = mid; else hi = mid - 1;
-  }
-  const GemmDesc& d = descs[lo];
-  modp_cta(d, tb - d.tile_begin, maps + d.map_x, maps + d.map_x + 1, maps + d.map_y + 2,
-           maps + d.map_y + 3, status);
+                         const CUtensorMap* __restrict__ maps, int total, unsigned* status) {
+  modp_tiles(
+      total,
+      [&](int tb) {
+        int lo = 0, hi = count - 1;  // last desc with tile_begin <= tb
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (descs[mid].tile_begin <= tb) lo = mid; else hi = mid - 1;
+        }
+        const GemmDesc& d = descs[lo];
+        return ModpTile{&d, maps + d.map_x, maps + d.map_x + 1, maps + d.map_y + 2, maps + d.map_y + 3,
+                        tb - d.tile_begin};
+      },
+      status);
 }
 
 // A (uint32, leading dimension N) -> byte slices (x >> 8, x & 255) as bfloat16
@@ -309,7 +349,7 @@ cudaError_t launch_modp_tc_group(const GemmDesc* d_descs, int count, int tiles, 
                                  unsigned* status, cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
   tc_modp_group_kernel<<<tiles, tcm::THREADS, tcm::SMEM, s>>>(d_descs, count, (const CUtensorMap*)d_maps,
-                                                              status);
+                                                              tiles, status);
   return cudaGetLastError();
 }
 
@@ -342,7 +382,8 @@ matpow_status tc_modp_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStrea
       return fail(p, MATPOW_ECUDA, "cuTensorMapEncodeTiled failed (N=%d)", d.N);
   }
   P.tiles0 = g.count > 1 ? g.d[1].tile_begin : g.tiles_total;
-  tc_modp_kernel<<<g.tiles_total, tcm::THREADS, tcm::SMEM, s>>>(P, p->status);
+  const int grid = g.tiles_total < p->num_sms ? g.tiles_total : p->num_sms;
+  tc_modp_kernel<<<grid, tcm::THREADS, tcm::SMEM, s>>>(P, g.tiles_total, p->status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(p, e, "tc_modp_kernel launch");
   return MATPOW_OK;
