@@ -48,8 +48,10 @@ TRAFFIC = {
     ("batched4096", "bf16x6"): (9.33e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
                                         "the 12 level launches of one step "
                                         "(profiles/tc_fxb_persist_kernel_batched512.md)"),
-    ("modp2048", "bf16x3"): (2.69e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "
+    ("modp2048", "bf16x3"): (2.68e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "
                                      "launches of one step (profiles/tc_modp_kernel_modp2048.md)"),
+    ("stoch64", "fp32"): (5.66e4, "ncu dram__bytes_read.sum + dram__bytes_write.sum of tiny_cluster_kernel, "
+                             "one launch (profiles/tiny_cluster_kernel_stoch64.md)"),
     ("large8192", "bf16x3"): (3.04e9, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
                                       "tc_fxb_kernel<128, 2> at full size (profiles/tc_fxb_kernel_large8192.md)"),
 }
