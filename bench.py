@@ -427,7 +427,9 @@ def run_ours(args, wk, world, rank, local):
 
     A_host = make_input(wk)
     A = torch.from_numpy(A_host).to(dev)
-    outs = [torch.empty_like(A) for _ in ns]
+    # the powers' results side by side in one allocation (one copy back per step)
+    out_all = torch.empty((len(ns),) + tuple(A.shape), dtype=torch.float32, device=dev)
+    outs = [out_all[i] for i in range(len(ns))]
     lgs = torch.zeros(len(ns), dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -485,15 +487,14 @@ def run_ours(args, wk, world, rank, local):
 
     # ---- end to end through the C-ABI with host buffers
     A_pin = torch.from_numpy(A_host).pin_memory()
-    outs_pin = [torch.empty(A_host.shape, dtype=torch.float32).pin_memory() for _ in ns]
+    out_pin = torch.empty(tuple(out_all.shape), dtype=torch.float32).pin_memory()
     lg_pin = torch.zeros(len(ns), dtype=torch.int64).pin_memory()
     e2e_steps = max(args.steps, 3)
     with torch.cuda.stream(stream):
         def e2e_step():
             A.copy_(A_pin, non_blocking=True)
             step(stream)
-            for i in range(len(ns)):
-                outs_pin[i].copy_(outs[i], non_blocking=True)
+            out_pin.copy_(out_all, non_blocking=True)
             lg_pin.copy_(lgs, non_blocking=True)
         for _ in range(2):
             e2e_step()
@@ -775,8 +776,15 @@ def run_batched(args, wk, world, rank, local):
     Ns = [int(x) for x in bd.Ns]
     ns = [int(x) for x in bd.ns]
     hostA = [wl.gaussian(N, int(sd)) for N, sd in zip(Ns, bd.seeds)]
-    dA = [torch.from_numpy(a).to(dev) for a in hostA]
-    outs = [torch.empty_like(a) for a in dA]
+    # the batch packed into one allocation per direction, as a caller that
+    # stages it with one copy would hold it; the API takes one pointer per matrix
+    offs = np.cumsum([0] + [N * N for N in Ns])
+    dbuf = torch.empty(int(offs[-1]), dtype=torch.float32, device=dev)
+    obuf = torch.empty_like(dbuf)
+    dA = [dbuf[int(o):int(o) + N * N].view(N, N) for o, N in zip(offs[:-1], Ns)]
+    outs = [obuf[int(o):int(o) + N * N].view(N, N) for o, N in zip(offs[:-1], Ns)]
+    hbuf = np.concatenate([a.reshape(-1) for a in hostA])
+    dbuf.copy_(torch.from_numpy(hbuf))
     lg = torch.zeros(len(dA), dtype=torch.int64, device=dev)
     flop_step = sum(gemm_count(n) * 2.0 * N ** 3 for N, n in zip(Ns, ns))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -822,16 +830,14 @@ def run_batched(args, wk, world, rank, local):
             errs["N%d_n%d" % (Ns[i], ns[i])] = oracle.rel_frobenius(
                 outs[i].cpu().numpy(), int(lg[i].item()), M, e)
     # end to end: inputs from pinned host memory, results back, inside the timed region
-    pinA = [torch.from_numpy(a).pin_memory() for a in hostA]
-    pinO = [torch.empty(a.shape, dtype=torch.float32).pin_memory() for a in hostA]
+    pinA = torch.from_numpy(hbuf).pin_memory()
+    pinO = torch.empty(obuf.shape, dtype=torch.float32).pin_memory()
     pinL = torch.zeros(len(dA), dtype=torch.int64).pin_memory()
     with torch.cuda.stream(stream):
         def e2e_step():
-            for a, b in zip(dA, pinA):
-                a.copy_(b, non_blocking=True)
+            dbuf.copy_(pinA, non_blocking=True)
             step(stream)
-            for a, b in zip(pinO, outs):
-                a.copy_(b, non_blocking=True)
+            pinO.copy_(obuf, non_blocking=True)
             pinL.copy_(lg, non_blocking=True)
         e2e_step()
         torch.cuda.synchronize()

@@ -299,7 +299,8 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
 
 // Grouped launch (server): products from a device table, each buffer's four
 // TMA descriptors {x1, x0 as A; y1, y0 as B} from a device table at map_x
-// (A role: + 0, 1) and map_y (B role: + 2, 3).  One CTA per tile.
+// (A role: + 0, 1) and map_y (B role: + 2, 3).  Persistent like the level
+// launch when the grid is below the tile count.
 __global__ void __launch_bounds__(tcm::THREADS, 1)
     tc_modp_group_kernel(const GemmDesc* __restrict__ descs, int count,
                          const CUtensorMap* __restrict__ maps, int total, unsigned* status) {
@@ -346,10 +347,11 @@ cudaError_t tc_modp_init() {
 }
 
 cudaError_t launch_modp_tc_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
-                                 unsigned* status, cudaStream_t s) {
+                                 int num_sms, unsigned* status, cudaStream_t s) {
   if (tiles <= 0) return cudaSuccess;
-  tc_modp_group_kernel<<<tiles, tcm::THREADS, tcm::SMEM, s>>>(d_descs, count, (const CUtensorMap*)d_maps,
-                                                              tiles, status);
+  const int grid = num_sms > 0 && tiles > num_sms ? num_sms : tiles;
+  tc_modp_group_kernel<<<grid, tcm::THREADS, tcm::SMEM, s>>>(d_descs, count, (const CUtensorMap*)d_maps,
+                                                             tiles, status);
   return cudaGetLastError();
 }
 

@@ -164,7 +164,7 @@ matpow_status tc_modp_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStrea
 // every product in the device table; descriptors per buffer as for the exact
 // split with two slices (x1, x0 as A at map_x, y1, y0 as B at map_y + 2).
 cudaError_t launch_modp_tc_group(const GemmDesc* d_descs, int count, int tiles, const void* d_maps,
-                                 unsigned* status, cudaStream_t s);
+                                 int num_sms, unsigned* status, cudaStream_t s);
 // Grouped exact-split level launch of the plan's batch (max_n: largest order
 // among the products).
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,

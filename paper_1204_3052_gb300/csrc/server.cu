@@ -408,8 +408,8 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p level");
   }
   if (!gt.empty()) {
-    e = launch_modp_tc_group((const GemmDesc*)(dd + o_mt), (int)gt.size(), tiles_t, s->d_maps, st0,
-                             s->stream);
+    e = launch_modp_tc_group((const GemmDesc*)(dd + o_mt), (int)gt.size(), tiles_t, s->d_maps, s->num_sms,
+                             st0, s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p level");
   }
   cudaEvent_t ev = take_ev(s);
