@@ -1,16 +1,21 @@
 // Exact products over the integers mod p on the tensor cores.
 //
-// A residue x in [0, p), p <= 65536, is stored as two byte slices
-// x = 256 x1 + x0 (x1, x0 in [0, 255], exact in bfloat16).  For C = X Y mod p
-// (arXiv 1204.3052 Sec. 4.1's product, inside Sec. 4.3's chain) the tensor
-// cores form, per 256-deep chunk of k,
+// A residue x in [0, p), p <= 65536, is stored as two balanced byte digits
+// of its centred representative x' (x or x - p, |x'| <= p / 2):
+// x' = 256 x1 + x0 with x0 in [-128, 127], x1 in [-128, 128], both exact in
+// bfloat16.  For C = X Y mod p (arXiv 1204.3052 Sec. 4.1's product, inside
+// Sec. 4.3's chain) the tensor cores form, per 256-deep chunk of k,
 //     H  = sum x1 y1,   M1 = sum x1 y0,   M2 = sum x0 y1,   L = sum x0 y0,
-// each a sum of at most 256 products <= 255^2, i.e. below 2^24: the float32
-// TMEM accumulators hold them exactly.  The epilogue warps add the chunk sums
-// into 32-bit integer totals (exact for N <= 32768), and at the end
+// each a sum of at most 256 products of magnitude <= 2^14, i.e. within
+// +-2^22: the float32 TMEM accumulators hold them exactly, and adding
+// 1.5 * 2^23 turns each into its integer in the low bits of the float (one
+// float add and one integer add per value instead of a float-to-integer
+// conversion).  The epilogue warps keep 32-bit totals (within +-2^28 for
+// N <= 16384), and at the end
 //     c = (H * 2^16 + (M1 + M2) * 2^8 + L) mod p
-// with Barrett reductions; a non-final product writes c's byte slices straight
-// into the next product's operand planes.
+// with Barrett reductions of the totals shifted by a multiple of p; a
+// non-final product writes c's digits straight into the next product's
+// operand planes.
 //
 // CTA: 384 threads.  Warp 0 TMA, warp 1 MMA (2 MMAs per 16-deep step), warp 2
 // TMEM (2 buffers x 4 accumulators x 64 columns = 512), warps 4-11 epilogue
@@ -43,6 +48,20 @@ __device__ __forceinline__ unsigned barrett(unsigned x, unsigned p, unsigned m) 
   unsigned r = x - q * p;
   return r >= p ? r - p : r;
 }
+
+// Balanced byte digits (d1, d0) of the centred representative of x in [0, p).
+__device__ __forceinline__ void modp_digits(unsigned x, unsigned p, int* d1, int* d0) {
+  const int xc = x > (p >> 1) ? (int)x - (int)p : (int)x;
+  const int lo = ((xc + 128) & 255) - 128;
+  *d1 = (xc - lo) >> 8;  // xc - lo is a multiple of 256
+  *d0 = lo;
+}
+
+// An exact integer-valued float v with |v| <= 2^22, plus 1.5 * 2^23, has the
+// bits 0x4B400000 + v: totals of these bit patterns minus count * 0x4B400000
+// (mod 2^32) are the exact integer totals.
+constexpr float kMagic = 12582912.0f;
+constexpr unsigned kMagicBits = 0x4B400000u;
 
 // One output tile: its product, the operands' TMA descriptors (ax1/ax0: the
 // high / low byte slices of X as the A operand, by1/by0: those of Y as the B
@@ -216,19 +235,19 @@ __device__ __forceinline__ void modp_tiles(int total, TileOf tile_of, unsigned* 
         ptx::tmem_ld_32x32b_x32(tq, r);
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < WC; ++j) Ht[j] += (unsigned)__uint_as_float(r[j]);
+        for (int j = 0; j < WC; ++j) Ht[j] += __float_as_uint(__uint_as_float(r[j]) + kMagic);
         ptx::tmem_ld_32x32b_x32(tq + BN, r);
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
+        for (int j = 0; j < WC; ++j) Mt[j] += __float_as_uint(__uint_as_float(r[j]) + kMagic);
         ptx::tmem_ld_32x32b_x32(tq + 2 * BN, r);
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < WC; ++j) Mt[j] += (unsigned)__uint_as_float(r[j]);
+        for (int j = 0; j < WC; ++j) Mt[j] += __float_as_uint(__uint_as_float(r[j]) + kMagic);
         ptx::tmem_ld_32x32b_x32(tq + 3 * BN, r);
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < WC; ++j) Lt[j] += (unsigned)__uint_as_float(r[j]);
+        for (int j = 0; j < WC; ++j) Lt[j] += __float_as_uint(__uint_as_float(r[j]) + kMagic);
         ptx::tc_fence_before();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
@@ -237,10 +256,14 @@ __device__ __forceinline__ void modp_tiles(int total, TileOf tile_of, unsigned* 
       const unsigned pm = d.p;
       const unsigned bm = (unsigned)(0x100000000ull / pm);
       const unsigned c16 = (unsigned)((1ull << 16) % pm), c8 = 256u % pm;
-      unsigned res[WC];
+      // totals within +-2^29; off: a multiple of p in [2^30, 2^30 + p)
+      const unsigned off = pm * ((1u << 30) / pm + ((1u << 30) % pm ? 1u : 0u));
+      const unsigned b1 = (unsigned)NCH * kMagicBits, b2 = 2u * b1;
+      unsigned* res = Ht;  // c overwrites the H totals
 #pragma unroll
       for (int j = 0; j < WC; ++j) {
-        const unsigned h = barrett(Ht[j], pm, bm), m = barrett(Mt[j], pm, bm), l = barrett(Lt[j], pm, bm);
+        const unsigned h = barrett(Ht[j] - b1 + off, pm, bm), m = barrett(Mt[j] - b2 + off, pm, bm),
+                       l = barrett(Lt[j] - b1 + off, pm, bm);
         const unsigned v = barrett(h * c16, pm, bm) + barrett(m * c8, pm, bm) + l;  // < 3p
         res[j] = barrett(v, pm, bm);
       }
@@ -256,9 +279,11 @@ __device__ __forceinline__ void modp_tiles(int total, TileOf tile_of, unsigned* 
             uint32_t w1[4], w0[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-              const unsigned a = res[8 * g8 + 2 * h], b = res[8 * g8 + 2 * h + 1];
-              __nv_bfloat162 hi = __floats2bfloat162_rn((float)(a >> 8), (float)(b >> 8));
-              __nv_bfloat162 lo = __floats2bfloat162_rn((float)(a & 255u), (float)(b & 255u));
+              int a1, a0, b1d, b0d;
+              modp_digits(res[8 * g8 + 2 * h], pm, &a1, &a0);
+              modp_digits(res[8 * g8 + 2 * h + 1], pm, &b1d, &b0d);
+              __nv_bfloat162 hi = __floats2bfloat162_rn((float)a1, (float)b1d);
+              __nv_bfloat162 lo = __floats2bfloat162_rn((float)a0, (float)b0d);
               w1[h] = *reinterpret_cast<uint32_t*>(&hi);
               w0[h] = *reinterpret_cast<uint32_t*>(&lo);
             }
@@ -319,8 +344,8 @@ __global__ void __launch_bounds__(tcm::THREADS, 1)
       status);
 }
 
-// A (uint32, leading dimension N) -> byte slices (x >> 8, x & 255) as bfloat16
-// planes with leading dimension ld; entries >= p flag ST_BADINPUT.
+// A (uint32, leading dimension N) -> balanced byte digits (x1, x0) as
+// bfloat16 planes with leading dimension ld; entries >= p flag ST_BADINPUT.
 __global__ void prep_modp_slices_kernel(const unsigned* __restrict__ A, int N, int ld, unsigned p,
                                         __nv_bfloat16* dst, long long plane, unsigned* status) {
   const size_t total = (size_t)N * ld;
@@ -331,8 +356,10 @@ __global__ void prep_modp_slices_kernel(const unsigned* __restrict__ A, int N, i
     const int c = (int)(i - r * ld);
     const unsigned v = c < N ? A[r * N + c] : 0u;
     bad |= v >= p;
-    dst[i] = __float2bfloat16_rn((float)(v >> 8));
-    dst[plane + i] = __float2bfloat16_rn((float)(v & 255u));
+    int d1, d0;
+    modp_digits(v < p ? v : 0u, p, &d1, &d0);
+    dst[i] = __float2bfloat16_rn((float)d1);
+    dst[plane + i] = __float2bfloat16_rn((float)d0);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, ST_BADINPUT);
 }
