@@ -370,3 +370,30 @@ def test_split_k_chain_matches_oracle_and_unsplit_chain(prec, N):
         assert d <= 1e-5 * n ** 0.5 * (30 if prec == "bf16x3" else 1), (N, n, d)
     split.close()
     whole.close()
+
+
+@pytest.mark.parametrize("N", [12, 80])
+@pytest.mark.parametrize("prec", PRECS)
+def test_value_mode_rounds_like_float64_rescale(plans, prec, N):
+    # The float32 result is mantissa * 2^E rounded once to float32: exact when
+    # it stays normal, one round-to-nearest into the subnormals, +-inf past
+    # the top.  Diagonal matrices put the cube of every entry at a chosen
+    # power of two near the bottom or the top of the float32 range; value
+    # mode must equal the same call's mantissa form rescaled in float64.
+    targets = {
+        "low": [-149.7, -149.2, -148.6, -147.1, -140.3, -131.9, -126.4, -125.9, -133.3, -145.5],
+        "high": [126.2, 126.9, 127.4, 127.9, 128.1, 129.5, 124.7, 127.99, 125.3, 127.01],
+    }
+    for side, ts in targets.items():
+        t = np.array([ts[i % len(ts)] for i in range(N)])
+        sign = np.where(np.arange(N) % 3 == 1, -1.0, 1.0)
+        A = np.diag(sign * np.exp2(t / 3.0)).astype(np.float32)
+        mant, e = run(plans[prec], A, 3)
+        val, _ = run(plans[prec], A, 3, mantissa=False)
+        with np.errstate(over="ignore", under="ignore"):
+            want = np.ldexp(mant, e).astype(np.float32).astype(np.float64)
+        assert np.array_equal(val, want, equal_nan=False), (side, prec, N)
+        if side == "low":
+            assert np.any((val != 0) & (np.abs(val) < 2.0 ** -126)), "no subnormal result exercised"
+        else:
+            assert np.any(np.isinf(val)) and np.any(np.isfinite(val) & (val != 0)), "range edge not exercised"
