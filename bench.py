@@ -42,13 +42,13 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 # the summaries under profiles/ give the command.  Reset to None whenever the
 # kernel changes.
 TRAFFIC = {
-    ("single512", "bf16x6"): (1.23e6, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
+    ("single512", "bf16x6"): (1.18e6, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
                                       "tc_chain_split_kernel<64, 3, 2>, one launch per step "
                                       "(profiles/tc_chain_kernel_single512.md)"),
-    ("batched4096", "bf16x6"): (9.33e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
+    ("batched4096", "bf16x6"): (9.35e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
                                         "the 12 level launches of one step "
                                         "(profiles/tc_fxb_persist_kernel_batched512.md)"),
-    ("modp2048", "bf16x3"): (2.68e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "
+    ("modp2048", "bf16x3"): (2.70e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "
                                      "launches of one step (profiles/tc_modp_kernel_modp2048.md)"),
     ("stoch64", "fp32"): (5.66e4, "ncu dram__bytes_read.sum + dram__bytes_write.sum of tiny_cluster_kernel, "
                              "one launch (profiles/tiny_cluster_kernel_stoch64.md)"),
