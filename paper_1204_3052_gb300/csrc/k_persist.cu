@@ -15,9 +15,13 @@
 // The host gives one 16-byte record per tile (product, depth, origin, the
 // two tensor-map indices), so the producer and MMA warps read one record
 // per tile and prefetch the next.
-//   warps 4-7  fold finished k-blocks into float32 registers, then write the
-//           next operand's slices with plain global stores (no staging in
-//           the ring, which the next tile is already filling)
+//   warps 4-11  fold finished k-blocks into float32 registers, then write
+//           the next operand's slices with plain global stores (no staging
+//           in the ring, which the next tile is already filling); warp w
+//           takes TMEM lane quadrant w % 4 and the tile's column half
+//           (w - 4) / 4, so two warps per scheduler share the epilogue work
+//           (with one warp per quadrant the MMA warp waited on the epilogue
+//           for 43 % of its time with three slices)
 //
 // The arithmetic per tile is that of tc_fxb_group_kernel: the same k-block
 // order, the same fold, the same slicing, so the results are bit-for-bit the
@@ -36,7 +40,9 @@
 namespace mp {
 namespace persist {
 
-constexpr int BM = 128, BN = 64, BK = 64, THREADS = 256;
+constexpr int BM = 128, BN = 64, BK = 64, THREADS = 384;
+constexpr int EW = 8;      // epilogue warps (4..11)
+constexpr int WC = BN / 2; // columns per epilogue thread
 constexpr int KB_MAX = 64;  // N <= 4096
 constexpr int EXPB = 4;     // tiles staged ahead by warp 3 (one per group of 8 lanes)
 constexpr uint64_t WAIT_NS = 2000000000ull;
@@ -108,11 +114,11 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
     }
     for (int b = 0; b < NBUF; ++b) {
       ptx::mbar_init(accfull0 + 8 * b, 1);
-      ptx::mbar_init(accempty0 + 8 * b, 4);  // one arrival per epilogue warp
+      ptx::mbar_init(accempty0 + 8 * b, EW);  // one arrival per epilogue warp
     }
     for (int b = 0; b < EXPB; ++b) {
       ptx::mbar_init(expfull0 + 8 * b, 8);     // the 8 lanes of one group of warp 3
-      ptx::mbar_init(expempty0 + 8 * b, 128);  // every epilogue thread
+      ptx::mbar_init(expempty0 + 8 * b, 32 * EW);  // every epilogue thread
     }
     ptx::mbar_init(drainb, 1);
     *abort_flag = 0;
@@ -270,9 +276,11 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
       ptx::mbar_arrive(expfull0 + 8 * e);  // release: this lane's writes are visible
     }
   } else if (warp >= 4) {
-    const int q = warp - 4;
-    const int h = q >> 1;
-    float T[BN];
+    const int q = warp & 3;          // TMEM lane quadrant: rows 32 q .. 32 q + 31
+    const int h = q >> 1;            // the tile's 64-row block row
+    const int ch = (warp - 4) >> 2;  // columns 32 ch .. 32 ch + 31
+    const bool lead = warp == 4 && lane == 0;
+    float T[WC];
     for (int lt = 0;; ++lt) {
       const int tb = blockIdx.x + lt * G;
       if (tb >= tiles_total) break;
@@ -291,10 +299,11 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
       void* outp = d.out;
       long long* out_log2 = d.out_log2;
       const int row = ti.m0 + 32 * q + lane;
+      const int c0 = ti.n0 + WC * ch;
       const int* eA = expbuf + e * C::EXP_INTS;
       const int* eB = eA + 2 * KB_MAX;
 #pragma unroll
-      for (int j = 0; j < BN; ++j) T[j] = 0.f;
+      for (int j = 0; j < WC; ++j) T[j] = 0.f;
       for (int kb = 0; kb < KB; ++kb, ++gk) {
         const int buf = gk % NBUF;
         if (!ptx::mbar_wait(accfull0 + 8 * buf, (gk / NBUF) & 1, &dummy, 2 * WAIT_NS)) {
@@ -303,33 +312,89 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
         }
         ptx::tc_fence_after();
         const int kr = fxb::rot_kb(kb, KB, fxb::tile_rot(ti.m0, ti.n0, KB));
-        float fac[1];
-        fac[0] = fxb::pow2f(eA[h * KB + kr] + eB[kr] - 16 - ti.sx - ti.sy);
-        fxb::fold<BN, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN), fac, BN);
+        const float f = fxb::pow2f(eA[h * KB + kr] + eB[kr] - 16 - ti.sx - ti.sy);
+        // the fold of fxb::fold on this thread's 32 columns: accumulator w at
+        // column offset w * BN of the k-block's set
+        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN + WC * ch);
+        uint32_t rm[32], rc[32];
+        ptx::tmem_ld_32x32b_x32(tq, rm);
+        ptx::tmem_ld_32x32b_x32(tq + BN, rc);
+        if (NSL == 3) {
+          uint32_t rd[32];
+          ptx::tmem_ld_32x32b_x32(tq + 2 * BN, rd);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            rc[j] = __float_as_uint(fmaf(__uint_as_float(rd[j]), 0.00390625f, __uint_as_float(rc[j])));
+        } else {
+          ptx::tmem_ld_wait();
+        }
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
+        if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);  // the set is in registers
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          T[j] = fmaf(fmaf(__uint_as_float(rc[j]), 0.00390625f, __uint_as_float(rm[j])), f, T[j]);
       }
       ptx::mbar_arrive(expempty0 + 8 * e);  // this tile's exponents and record are no longer read
-      // one verdict for the four epilogue warps (they share named barrier 1)
-      fxb::epi_bar<128>();
-      if (q == 0 && lane == 0) *epi_ok = ok && !*abort_flag;
-      fxb::epi_bar<128>();
+      // one verdict for the epilogue warps (they share named barrier 1)
+      fxb::epi_bar<32 * EW>();
+      if (lead) *epi_ok = ok && !*abort_flag;
+      fxb::epi_bar<32 * EW>();
       if (!*epi_ok) {
         *abort_flag = 1;
         break;
       }
       const bool first = ti.m0 == 0 && ti.n0 == 0;  // tile 0 of its product
       if (mode == OUT_INTERNAL) {
-        if (first && q == 0 && lane == 0) scales[sc].E = ti.Ec;
-        fxb::store_slices<BN, 128, NSL>(T, row, ti.m0, ti.n0, q, lane, N, ld, (__nv_bfloat16*)Cp, plane,
-                                        (int*)((char*)Cp + fxb::bexp_offset(N, ld, NSL)),
-                                        &scales[sc].maxbits, red);
+        if (first && lead) scales[sc].E = ti.Ec;
+        // block maximum of the 64 x 64 block (rows of quadrants 2h, 2h + 1,
+        // both column halves), its exponent, then this thread's slices
+        float m = 0.f;
+#pragma unroll
+        for (int j = 0; j < WC; ++j) m = fmaxf(m, fabsf(T[j]));
+        m = warp_max(m);
+        if (lane == 0) red[2 * q + ch] = m;
+        fxb::epi_bar<32 * EW>();
+        const float bm = fmaxf(fmaxf(red[4 * h], red[4 * h + 1]), fmaxf(red[4 * h + 2], red[4 * h + 3]));
+        const int ex = fxb::frexp_exp(bm);
+        const int nb = fxb::nblocks(N);
+        const int I = ti.m0 / fxb::BLK + h, J = ti.n0 / fxb::BLK;
+        if ((q & 1) == 0 && ch == 0 && lane == 0 && I < nb && J < nb) {
+          ((int*)((char*)Cp + fxb::bexp_offset(N, ld, NSL)))[I * nb + J] = ex;
+          if (bm > 0.f) atomicMax(&scales[sc].maxbits, __float_as_uint(bm));
+        }
+        if (row < N) {
+          // 16-byte groups of 8 columns; a group that starts below N ends
+          // within the row's padding to ld (a multiple of 8), which no
+          // product reads, and its columns past N hold exact zeros
+          __nv_bfloat16* p1 = (__nv_bfloat16*)Cp + (size_t)row * ld + c0;
+#pragma unroll
+          for (int g8 = 0; g8 < WC / 8; ++g8) {
+            if (c0 + 8 * g8 < N) {
+              uint32_t w[NSL][4];
+#pragma unroll
+              for (int hh = 0; hh < 4; ++hh) {
+                float x0[NSL], x1[NSL];
+                fxb::slice_n<NSL>(T[8 * g8 + 2 * hh], ex, x0);
+                fxb::slice_n<NSL>(T[8 * g8 + 2 * hh + 1], ex, x1);
+#pragma unroll
+                for (int k = 0; k < NSL; ++k) {
+                  __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
+                  w[k][hh] = *reinterpret_cast<uint32_t*>(&v2);
+                }
+              }
+#pragma unroll
+              for (int k = 0; k < NSL; ++k)
+                *reinterpret_cast<uint4*>(p1 + k * plane + 8 * g8) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
+            }
+          }
+        }
+        fxb::epi_bar<32 * EW>();  // red may be reused
       } else {
-        if (first && q == 0 && lane == 0 && mode == OUT_USER_MANT && out_log2) *out_log2 = ti.Ec;
+        if (first && lead && mode == OUT_USER_MANT && out_log2) *out_log2 = ti.Ec;
         if (row < N)
-          store_row_f32<BN>(T, (float*)outp + (size_t)row * N, ti.n0, N, mode == OUT_USER_MANT, ti.Ec, status,
-                            outp);
+          store_row_f32<WC>(T, (float*)outp + (size_t)row * N, c0, N, mode == OUT_USER_MANT, ti.Ec, status, outp);
       }
     }
   }
