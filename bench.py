@@ -45,7 +45,7 @@ TRAFFIC = {
     ("single512", "bf16x6"): (1.18e6, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
                                       "tc_chain_split_kernel<64, 3, 2>, one launch per step "
                                       "(profiles/tc_chain_kernel_single512.md)"),
-    ("batched4096", "bf16x6"): (9.35e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
+    ("batched4096", "bf16x6"): (9.63e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
                                         "the 12 level launches of one step "
                                         "(profiles/tc_fxb_persist_kernel_batched512.md)"),
     ("modp2048", "bf16x3"): (2.70e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "

@@ -212,9 +212,22 @@ matpow_status matpow_batched(matpow_plan_t plan, int count, const float* const* 
 /*
  * Wait for the work enqueued on `stream` and return the first deferred
  * device status of the plan since the last matpow_sync (MATPOW_OK,
- * MATPOW_ERANGE, MATPOW_EINVAL for an entry >= p), then clear it.
+ * MATPOW_ERANGE, MATPOW_EINVAL for an entry >= p, MATPOW_ETIMEDOUT when a
+ * kernel's bounded wait gave up), then clear it.
  */
 matpow_status matpow_sync(matpow_plan_t plan, void* stream);
+
+/*
+ * Error-path self-test.  Launches one CTA that waits on a shared-memory
+ * mbarrier that no thread ever arrives at, with the bounded wait every
+ * tensor-core kernel of the library uses, given a budget of `budget_ns`
+ * nanoseconds of the GPU's global timer (1000 <= budget_ns <= 10^10, else
+ * MATPOW_EINVAL).  The wait gives up, the kernel records the timeout in the
+ * plan's status word and returns; matpow_sync() then returns
+ * MATPOW_ETIMEDOUT and the plan and the CUDA context stay usable.
+ * Asynchronous.  For tests of the timeout path.
+ */
+matpow_status matpow_selftest_wait_timeout(matpow_plan_t plan, uint64_t budget_ns, void* stream);
 
 /* G(n) = floor(log2 n) + popcount(n) - 1 (0 for n <= 1): products that A^n takes. */
 int matpow_gemm_count(uint64_t n);

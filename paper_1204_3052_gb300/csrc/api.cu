@@ -686,6 +686,16 @@ extern "C" matpow_status matpow_mod_p(matpow_plan_t p, const uint32_t* dA, int N
   });
 }
 
+extern "C" matpow_status matpow_selftest_wait_timeout(matpow_plan_t p, uint64_t budget_ns, void* stream) {
+  if (!p) return fail(nullptr, MATPOW_EINVAL, "matpow_selftest_wait_timeout: plan is NULL");
+  if (budget_ns < 1000ull || budget_ns > 10000000000ull)
+    return fail(p, MATPOW_EINVAL, "matpow_selftest_wait_timeout: budget_ns must be in [1e3, 1e10]");
+  DeviceGuard dg(p->device);
+  CK(p, launch_selftest_wait((unsigned long long)budget_ns, p->status, (cudaStream_t)stream));
+  p->launches++;
+  return MATPOW_OK;
+}
+
 extern "C" matpow_status matpow_sync(matpow_plan_t p, void* stream) {
   if (!p) return fail(nullptr, MATPOW_EINVAL, "matpow_sync: plan is NULL");
   DeviceGuard dg(p->device);

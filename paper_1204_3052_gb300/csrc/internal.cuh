@@ -193,6 +193,7 @@ struct TinyDesc {
   int N;
   int pad_;
 };
+cudaError_t launch_selftest_wait(unsigned long long budget_ns, unsigned* status, cudaStream_t s);
 cudaError_t launch_tiny_one(const TinyDesc& d, unsigned* status, cudaStream_t s);
 cudaError_t launch_tiny_group(const TinyDesc* d_descs, int count, unsigned* status, cudaStream_t s);
 int tiny_max_supported();

@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace mp {
 
@@ -203,6 +204,27 @@ cudaError_t launch_prep_absmax_group(const PrepDesc* d, int count, int blocks, S
 cudaError_t launch_prep_convert_group(const PrepDesc* d, int count, int blocks, Scale* scales,
                                       cudaStream_t s) {
   prep_convert_group_kernel<<<blocks, 256, 0, s>>>(d, count, scales);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Error-path self-test: a bounded wait on an mbarrier that nothing arrives at.
+__global__ void selftest_wait_kernel(unsigned long long budget_ns, unsigned* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int abort_flag;
+  const uint32_t b = ptx::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    ptx::mbar_init(b, 1);
+    abort_flag = 0;
+    ptx::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !ptx::mbar_wait(b, 0, (volatile int*)&abort_flag, budget_ns))
+    atomicOr(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_selftest_wait(unsigned long long budget_ns, unsigned* status, cudaStream_t s) {
+  selftest_wait_kernel<<<1, 32, 0, s>>>(budget_ns, status);
   return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ EXPORTS = [
     "matpow_plan_set_option", "matpow_f32", "matpow_mod_p", "matpow_batched", "matpow_sync",
     "matpow_gemm_count", "matpow_kernel_time", "matpow_launch_count", "matpow_server_create",
     "matpow_submit", "matpow_poll", "matpow_server_latencies", "matpow_server_destroy",
-    "matpow_f32_noalloc",
+    "matpow_f32_noalloc", "matpow_selftest_wait_timeout",
 ]
 
 
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "matpow_server_latencies": (i64, [vp, ctypes.POINTER(ctypes.c_double), i64]),
             "matpow_server_destroy": (i32, [vp]),
             "matpow_f32_noalloc": (i32, [vp, i32, u64, vp, vp, vp]),
+            "matpow_selftest_wait_timeout": (i32, [vp, u64, vp]),
         }
         for name, (res, args) in protos.items():
             fn = getattr(lib, name)
@@ -186,6 +187,10 @@ def matpow_batched(plan: int, As: Sequence, Ns: Sequence[int], ns: Sequence[int]
 
 def matpow_sync(plan: int, stream=None) -> int:
     return load().matpow_sync(plan, _stream(stream))
+
+
+def matpow_selftest_wait_timeout(plan: int, budget_ns: int, stream=None) -> int:
+    return load().matpow_selftest_wait_timeout(plan, int(budget_ns), _stream(stream))
 
 
 def matpow_gemm_count(n: int) -> int:
