@@ -32,6 +32,12 @@ Functions and the passage each follows:
   |a1| <= 256, |a2| <= 128.  ``fixed_slices_n(X, block, k)`` continues the
   same recurrence to k slices (a_(j+1) = rint(256 * remainder)), so
   X ~ 2^(s-8k) sum_j 256^(k-1-j) a_j.
+* ``expm_f64(A)``: the matrix exponential e^A in float64 from the series
+  definition by scaling and squaring (Moler and Van Loan 2003, method 3):
+  e^A = (sum_k B^k / k!)^(2^s), B = A / 2^s, ||B||_1 <= 1/2, 18 terms.
+  ``expm_fp32_ps(A)``: the float32 yardstick of the GPU evaluation (degree-11
+  Taylor polynomial in Paterson-Stockmeyer form, float32 products); parity
+  unpinned.
 * ``emu_sqmul(A, n, precision)``: the square-and-multiply chain with the
   operand rounding of a tensor-core precision emulated on the CPU ("bf16":
   one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi of floating
@@ -389,3 +395,70 @@ def emu_sqmul(A, n: int, precision: str):
         if bits:
             P, ep = norm(_emu_product(P, P, precision), 2 * ep)
     return R, er
+
+
+# ---------------------------------------------------------------------------
+# The matrix exponential e^A (the "scaling and squaring" use of the same
+# squaring chain; Moler and Van Loan, "Nineteen dubious ways to compute the
+# exponential of a matrix, twenty-five years later", SIAM Review 45 (2003),
+# method 3).  Not part of arXiv 1204.3052, which means A^n by "matrix
+# exponentiation"; this is the other common meaning, built on the same core.
+
+def expm_scaling(A, theta: float):
+    """s = max(0, ceil(log2(||A||_1 / theta))): the number of squarings that
+    brings ||A / 2^s||_1 to at most theta (1-norm: the largest column sum)."""
+    A = np.asarray(A, dtype=np.float64)
+    nrm = float(np.max(np.sum(np.abs(A), axis=0))) if A.size else 0.0
+    if not math.isfinite(nrm):
+        raise ValueError("non-finite input")
+    if nrm <= theta:
+        return 0
+    return max(0, math.ceil(math.log2(nrm / theta)))
+
+
+def expm_f64(A, terms: int = 18):
+    """e^A in float64 from its definition, the exponential series
+    e^B = sum_k B^k / k!, applied to B = A / 2^s with ||B||_1 <= 1/2 (the
+    terms past B^18 / 18! are below 2^-53 relative), then
+    e^A = (e^B)^(2^s) by s squarings.  The series is summed by Horner's rule,
+    T <- I + B T / k for k = terms .. 1; every product is the plain triple
+    loop (gemm_f64)."""
+    A = np.asarray(A, dtype=np.float64)
+    N = _square(A)
+    s = expm_scaling(A, 0.5)
+    B = np.ldexp(A, -s)
+    I = np.eye(N)
+    T = I.copy()
+    for k in range(terms, 0, -1):
+        T = I + gemm_f64(B, T) / k
+    for _ in range(s):
+        T = gemm_f64(T, T)
+    return T
+
+
+def expm_fp32_ps(A):
+    """The float32-class yardstick of the GPU method (parity unpinned): s
+    squarings for ||A / 2^s||_1 <= 1, the degree-11 Taylor polynomial of
+    B = A / 2^s in Paterson-Stockmeyer form
+        T = P0 + B^4 (P1 + B^4 P2),  Pj = sum_{i<4} B^i / (4j + i)!,
+    with B^2, B^3, B^4 and the two outer products rounded to float32 (numpy
+    float32 matmul) and the sums formed in float64 then rounded to float32,
+    and T^(2^s) by float32 squarings.  Returns (M, e): e^A ~ M 2^e."""
+    A = np.asarray(A, dtype=np.float64)
+    N = _square(A)
+    s = expm_scaling(A, 1.0)
+    B = np.ldexp(A, -s).astype(np.float32)
+    B2 = np.matmul(B, B)
+    B3 = np.matmul(B2, B)
+    B4 = np.matmul(B2, B2)
+    I = np.eye(N)
+    P = []
+    for j in range(3):
+        c = [1.0 / math.factorial(4 * j + i) for i in range(4)]
+        P.append((c[0] * I + c[1] * B.astype(np.float64) + c[2] * B2.astype(np.float64)
+                  + c[3] * B3.astype(np.float64)).astype(np.float32))
+    Q = np.matmul(B4, P[2])
+    P1 = (P[1].astype(np.float64) + Q).astype(np.float32)
+    R = np.matmul(B4, P1)
+    T = (P[0].astype(np.float64) + R).astype(np.float32)
+    return fp32_sqmul(T, 1 << s) if s > 0 else (T, 0)
