@@ -185,6 +185,27 @@ matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, float* dOut
                                  int64_t* dLog2Scale, void* stream);
 
 /*
+ * The matrix exponential e^A of a float32 matrix.  (The paper's "matrix
+ * exponentiation" is A^n; e^A is the other common meaning, computed here on
+ * the same squaring chain by scaling and squaring: Moler and Van Loan,
+ * SIAM Review 45 (2003), method 3.)
+ *   s = max(0, ceil(log2 ||A||_1)) squarings (||A||_1: the largest column
+ *   sum), B = A 2^-s, T = the degree-11 Taylor polynomial of e^B in
+ *   Paterson-Stockmeyer form, T = P0 + B^4 (P1 + B^4 P2) (five products on
+ *   the plan's product path: B^2, B^3, B^4 and the two outer ones), and
+ *   e^A = T^(2^s) by matpow_f32 (s squarings).
+ *   dA, dOut, dLog2Scale   as in matpow_f32; dOut may alias dA.
+ * Reads ||A||_1 back to the host (it fixes s), so the call waits for the
+ * stream up to that point; not for use inside a stream capture.  A
+ * non-finite entry or ||A||_1 > 2^62 returns MATPOW_EINVAL.  The first call
+ * on a plan allocates 7 max_n^2 float32 of scratch (MATPOW_ENOMEM if that
+ * fails).  Accuracy: float32 class, the error growing with s (each squaring
+ * doubles the relative error of the dominant eigenvalues).
+ */
+matpow_status matpow_expm(matpow_plan_t plan, const float* dA, int N, float* dOut, int64_t* dLog2Scale,
+                          void* stream);
+
+/*
  * A^n mod p for integer A (exact; the same square-and-multiply over Z/pZ).
  *   dA     device, N*N uint32 with every entry in [0, p); read only.
  *   p      modulus, 2 <= p <= 65536.

@@ -36,8 +36,9 @@ Functions and the passage each follows:
   definition by scaling and squaring (Moler and Van Loan 2003, method 3):
   e^A = (sum_k B^k / k!)^(2^s), B = A / 2^s, ||B||_1 <= 1/2, 18 terms.
   ``expm_fp32_ps(A)``: the float32 yardstick of the GPU evaluation (degree-11
-  Taylor polynomial in Paterson-Stockmeyer form, float32 products); parity
-  unpinned.
+  Taylor polynomial in Paterson-Stockmeyer form, float32 products), and
+  ``expm_emu_ps(A, precision)`` the same with emulated tensor-core operand
+  rounding; parity unpinned.
 * ``emu_sqmul(A, n, precision)``: the square-and-multiply chain with the
   operand rounding of a tensor-core precision emulated on the CPU ("bf16":
   one bfloat16 product; "bf16x3": hi*hi + hi*lo + lo*hi of floating
@@ -436,7 +437,16 @@ def expm_f64(A, terms: int = 18):
     return T
 
 
-def expm_fp32_ps(A):
+def expm_emu_ps(A, precision: str):
+    """``expm_fp32_ps`` with every product's operands rounded as a tensor-core
+    precision would round them (``_emu_product``; the squarings by
+    ``emu_sqmul``): the error yardstick of the lower-precision paths on the
+    same evaluation (parity unpinned).  Returns (M, e)."""
+    return expm_fp32_ps(A, lambda X, Y: _emu_product(X, Y, precision),
+                        lambda T, n: emu_sqmul(T, n, precision))
+
+
+def expm_fp32_ps(A, mul=None, power=None):
     """The float32-class yardstick of the GPU method (parity unpinned): s
     squarings for ||A / 2^s||_1 <= 1, the degree-11 Taylor polynomial of
     B = A / 2^s in Paterson-Stockmeyer form
@@ -444,21 +454,23 @@ def expm_fp32_ps(A):
     with B^2, B^3, B^4 and the two outer products rounded to float32 (numpy
     float32 matmul) and the sums formed in float64 then rounded to float32,
     and T^(2^s) by float32 squarings.  Returns (M, e): e^A ~ M 2^e."""
+    mul = mul or np.matmul
+    power = power or fp32_sqmul
     A = np.asarray(A, dtype=np.float64)
     N = _square(A)
     s = expm_scaling(A, 1.0)
     B = np.ldexp(A, -s).astype(np.float32)
-    B2 = np.matmul(B, B)
-    B3 = np.matmul(B2, B)
-    B4 = np.matmul(B2, B2)
+    B2 = mul(B, B)
+    B3 = mul(B2, B)
+    B4 = mul(B2, B2)
     I = np.eye(N)
     P = []
     for j in range(3):
         c = [1.0 / math.factorial(4 * j + i) for i in range(4)]
         P.append((c[0] * I + c[1] * B.astype(np.float64) + c[2] * B2.astype(np.float64)
                   + c[3] * B3.astype(np.float64)).astype(np.float32))
-    Q = np.matmul(B4, P[2])
+    Q = mul(B4, P[2])
     P1 = (P[1].astype(np.float64) + Q).astype(np.float32)
-    R = np.matmul(B4, P1)
+    R = mul(B4, P1)
     T = (P[0].astype(np.float64) + R).astype(np.float32)
-    return fp32_sqmul(T, 1 << s) if s > 0 else (T, 0)
+    return power(T, 1 << s) if s > 0 else (T, 0)

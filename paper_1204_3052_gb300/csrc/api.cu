@@ -218,6 +218,7 @@ extern "C" matpow_status matpow_plan_destroy(matpow_plan_t p) {
   for (auto& ev : p->event_pool) cudaEventDestroy(ev);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->ws) cudaFree(p->ws);
+  if (p->expm_ws) cudaFree(p->expm_ws);
   batch_free(p);
   tc_free(p);
   if (p->h_status) cudaFreeHost(p->h_status);
@@ -579,6 +580,60 @@ static matpow_status enqueue_modp(matpow_plan_s* p, const uint32_t* dA, int N, u
     timed_end(p, s, ev, MATPOW_KERNEL_MODP, 2.0 * N * (double)N * N * g.count);
     p->launches++;
   }
+  return MATPOW_OK;
+}
+
+matpow_status mp::enqueue_product_f32(matpow_plan_s* p, const float* X, const float* Y, int N, float* out,
+                                      cudaStream_t s) {
+  const int fmt = plan_float_fmt(p);
+  const long long plane = plane_offset_elems(N, fmt);
+  CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * 4, s));
+  if (fmt_exact(fmt)) {
+    CK(p, launch_prep_fxb(X, N, fmt, p->buf[0], &p->scales[1], p->status, s));
+    CK(p, launch_prep_fxb(Y, N, fmt, p->buf[1], &p->scales[2], p->status, s));
+    p->launches += 2;
+  } else {
+    CK(p, launch_absmax_f32(X, N, &p->scales[0], p->status, s));
+    CK(p, launch_convert_f32(X, N, &p->scales[0], &p->scales[1], fmt, p->buf[0], plane, s));
+    CK(p, cudaMemsetAsync(&p->scales[0], 0, sizeof(Scale), s));  // slot 0 again for Y's maximum
+    CK(p, launch_absmax_f32(Y, N, &p->scales[0], p->status, s));
+    CK(p, launch_convert_f32(Y, N, &p->scales[0], &p->scales[2], fmt, p->buf[1], plane, s));
+    p->launches += 4;
+  }
+  GemmPair g{};
+  g.count = 1;
+  GemmDesc& d = g.d[0];
+  d.X = p->buf[0];
+  d.Y = p->buf[1];
+  d.C = nullptr;
+  d.out = out;
+  d.out_log2 = nullptr;
+  d.plane = plane;
+  d.N = N;
+  d.ld = ld_for(N, fmt);
+  d.sx = 1;
+  d.sy = 2;
+  d.sc = 3;
+  d.mode = OUT_USER_VALUE;
+  d.tile_begin = 0;
+  cudaEvent_t ev;
+  const double flop = 2.0 * N * (double)N * N;
+  timed_begin(p, s, &ev);
+  if (p->prec != MATPOW_FP32_SIMT) {
+    int nt = 0;
+    matpow_status st = tc_fill_desc(p, &d, &nt);
+    if (st != MATPOW_OK) return st;
+    g.tiles_total = nt;
+    st = tc_launch_pair(p, g, s);
+    if (st != MATPOW_OK) return st;
+    timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
+  } else {
+    d.tiles_n = tiles_for(N, simt_tile_edge());
+    g.tiles_total = d.tiles_n * d.tiles_n;
+    CK(p, launch_simt_pair(g, p->scales, p->status, s));
+    timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
+  }
+  p->launches++;
   return MATPOW_OK;
 }
 

@@ -103,6 +103,7 @@ struct matpow_plan_s {
   bool persist = true;    // batched 64-column levels: persistent grouped kernel
   bool naive = false;     // float powers by n - 1 products R <- R A (comparison method)
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
+  float* expm_ws = nullptr;  // matpow_expm scratch: 7 max_n^2 float32 + a word, on first use
   // graphs
   std::vector<mp::GraphEntry> graphs;
   uint64_t graph_clock = 0;
@@ -140,6 +141,10 @@ bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box
 // (exact split; small and medium N).  *used = false when it does not apply.
 matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
                            int64_t* dLog2, cudaStream_t s, bool* used);
+// C = X Y of two float32 N x N matrices (N > tiny_max), value-mode float32
+// output, through the plan's product path (uses buffers 0, 1, scale slots 0-3).
+matpow_status enqueue_product_f32(matpow_plan_s* p, const float* X, const float* Y, int N, float* out,
+                                  cudaStream_t s);
 // One power of a multi-power whole-chain launch: input, order, power, output,
 // its four stored-format buffers and its scale slots (2 + G(n)).
 struct ChainJob {

@@ -38,7 +38,7 @@ EXPORTS = [
     "matpow_plan_set_option", "matpow_f32", "matpow_mod_p", "matpow_batched", "matpow_sync",
     "matpow_gemm_count", "matpow_kernel_time", "matpow_launch_count", "matpow_server_create",
     "matpow_submit", "matpow_poll", "matpow_server_latencies", "matpow_server_destroy",
-    "matpow_f32_noalloc", "matpow_selftest_wait_timeout",
+    "matpow_f32_noalloc", "matpow_selftest_wait_timeout", "matpow_expm",
 ]
 
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "matpow_server_destroy": (i32, [vp]),
             "matpow_f32_noalloc": (i32, [vp, i32, u64, vp, vp, vp]),
             "matpow_selftest_wait_timeout": (i32, [vp, u64, vp]),
+            "matpow_expm": (i32, [vp, vp, i32, vp, vp, vp]),
         }
         for name, (res, args) in protos.items():
             fn = getattr(lib, name)
@@ -187,6 +188,10 @@ def matpow_batched(plan: int, As: Sequence, Ns: Sequence[int], ns: Sequence[int]
 
 def matpow_sync(plan: int, stream=None) -> int:
     return load().matpow_sync(plan, _stream(stream))
+
+
+def matpow_expm(plan: int, A, N: int, out, log2_scale=None, stream=None) -> int:
+    return load().matpow_expm(plan, _ptr(A), N, _ptr(out), _ptr(log2_scale), _stream(stream))
 
 
 def matpow_selftest_wait_timeout(plan: int, budget_ns: int, stream=None) -> int:
@@ -276,6 +281,16 @@ class Plan:
             out = torch.empty_like(A)
         lg = torch.zeros(1, dtype=torch.int64, device=A.device) if mantissa else None
         _check(matpow_f32(self.h, A, N, n, out, lg, stream), self.h)
+        return (out, lg) if mantissa else out
+
+    def expm(self, A, out=None, mantissa: bool = False, stream=None):
+        """e^A (float32).  Returns out, or (out, log2 tensor) with mantissa=True."""
+        import torch
+        N = A.shape[0]
+        if out is None:
+            out = torch.empty_like(A)
+        lg = torch.zeros(1, dtype=torch.int64, device=A.device) if mantissa else None
+        _check(matpow_expm(self.h, A, N, out, lg, stream), self.h)
         return (out, lg) if mantissa else out
 
     def mod_p(self, A, n: int, p: int, out=None, stream=None):
