@@ -82,6 +82,9 @@ WORKLOADS = {
                      prec="bf16x6", gen="gaussian",
                      desc="N in {128,256,512} N(0,1/N) float32, n in {64,256,1024}, seed 0: "
                           "square-and-multiply vs the naive n-1 product method on the GPU"),
+    # the matrix exponential on the same kernels (scaling and squaring)
+    "expm512": dict(kind="expm", N=512, scale=4.0, ns=[], prec="bf16x6", gen="gaussian",
+                    desc="e^A of a single N=512 4 N(0,1/N) float32 matrix (||A||_1 ~ 70: 7 squarings), seed 0"),
     # a smaller batch of the same mix (profiling case: a few hundred MB on the device)
     "batched512": dict(kind="batched", count=512, n_max=4096, N=256, ns=[], prec="bf16x6",
                        desc="batched: 512 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
@@ -248,6 +251,37 @@ def cpu_sample_modp(wk, budget_s):
                                         "x %d (%.1f s)" % (reps, dt)}
 
 
+def expm_input(wk):
+    from paper_1204_3052_gb300 import workloads as wl
+    return (wl.gaussian(wk["N"], 0) * wk["scale"]).astype(np.float32)
+
+
+def expm_flop(A) -> float:
+    """Algorithmic flop of e^A by the library's method: (5 + s) products of
+    2N^3 (B^2, B^3, B^4, two Paterson-Stockmeyer products, s squarings)."""
+    import oracle
+    return (5 + oracle.expm_scaling(A, 1.0)) * 2.0 * A.shape[0] ** 3
+
+
+def cpu_sample_expm(wk, budget_s):
+    """The float64 oracle e^A of the workload's matrix, repeated for about
+    budget_s; e^A per second times the library method's algorithmic flop."""
+    import oracle
+    A = expm_input(wk)
+    cores = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.expm_f64(A)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or reps >= 100:
+            break
+    return {"value": reps * expm_flop(A) / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": "float64 scaling and squaring of the exponential series (triple-loop products), "
+                      "N=%d x %d (%.1f s)" % (wk["N"], reps, dt)}
+
+
 def cpu_sample_list(items, budget_s):
     """Oracle over (A, n, p) items in order until ~budget_s; effective TFLOP/s."""
     import oracle
@@ -296,6 +330,11 @@ def config_for(args, wk, world):
         cfg.update(p=wk["p"], gemms_per_step=sum(gemm_count(n) for n in wk["ns"]),
                    l2="flushed between timed steps (256 MB write)")
         cfg["precision"] = "exact mod p (byte-sliced bfloat16 tensor-core products)"
+    elif wk.get("kind") == "expm":
+        import oracle
+        s = oracle.expm_scaling(expm_input(wk), 1.0)
+        cfg.update(squarings=s, gemms_per_step=5 + s, l2="flushed between timed steps (256 MB write)",
+                   api="matpow_expm")
     else:
         cfg.update(gemms_per_step=sum(gemm_count(n) for n in wk["ns"]),
                    l2="flushed between timed steps (256 MB write)",
@@ -318,6 +357,8 @@ def run_reference(args, wk, world, rank):
             cb = cpu_sample_list(reference_items(wk), args.ref_budget)
         elif wk.get("kind") == "modp":
             cb = cpu_sample_modp(wk, args.ref_budget)
+        elif wk.get("kind") == "expm":
+            cb = cpu_sample_expm(wk, args.ref_budget)
         elif wk.get("kind") == "naive":
             cb = cpu_sample(dict(wk, ns=wk["ns_list"]), budget_s=args.ref_budget)
         else:
@@ -694,6 +735,129 @@ def run_modp(args, wk, world, rank, local):
             "e2e": {"value": e2e_steps * flop_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                     "h2d_bytes_per_step": int(A_host.nbytes),
                     "d2h_bytes_per_step": int(A_host.nbytes * len(ns))},
+            "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb}
+    print(json.dumps(line))
+
+
+def run_expm(args, wk, world, rank, local):
+    """e^A through matpow_expm (scaling and squaring on the product and
+    squaring kernels)."""
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_src = load_peaks()
+    N = wk["N"]
+    A_host = expm_input(wk)
+    flop_step = expm_flop(A_host)
+    A = torch.from_numpy(A_host).to(dev)
+    out = torch.empty_like(A)
+    lg = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    plan = mpw.Plan(N, args.precision, device=local)
+
+    def step(s):
+        st = mpw.matpow_expm(plan.h, A, N, out, lg, s)
+        if st != 0:
+            mpw._check(st, plan.h)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step(stream)
+        plan.check(stream)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = plan.launch_count()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step(stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        barrier(world)
+        clocks = sampler.stop()
+        launches = plan.launch_count() - launches0
+        st = plan.sync(stream)
+    t_ms = max_over_ranks(world, sum(a.elapsed_time(b) for a, b in evs), dev)
+    value = world * args.steps * flop_step / (t_ms * 1e-3) / 1e12
+    errs = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        want = oracle.expm_f64(A_host)
+        got = np.ldexp(out.cpu().numpy().astype(np.float64), int(lg.item()))
+        s = oracle.expm_scaling(A_host, 1.0)
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        errs = {"rel_frobenius": err, "stated": 2e-5 * (s + 1), "within_2e-5_(s+1)": err <= 2e-5 * (s + 1)}
+    # e2e: host input in, result (mantissa and exponent) out, through the C-ABI
+    A_pin = torch.from_numpy(A_host).pin_memory()
+    out_pin = torch.empty(A_host.shape, dtype=torch.float32).pin_memory()
+    lg_pin = torch.zeros(1, dtype=torch.int64).pin_memory()
+    e2e_steps = max(args.steps, 3)
+    with torch.cuda.stream(stream):
+        def e2e_step():
+            A.copy_(A_pin, non_blocking=True)
+            step(stream)
+            out_pin.copy_(out, non_blocking=True)
+            lg_pin.copy_(lg, non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(world, e0.elapsed_time(e1), dev)
+    # tensor-core kernels (products and squarings): per-launch CUDA-event time
+    plan.set_option(mpw.OPT_TIMING, 1)
+    kind = mpw.KERNEL_TC if args.precision != "fp32" else mpw.KERNEL_SIMT
+    with torch.cuda.stream(stream):
+        plan.kernel_time(kind, reset=True)
+        for _ in range(max(args.steps, 3)):
+            flush.zero_()
+            step(stream)
+        torch.cuda.synchronize()
+        kl, kms, kflop = plan.kernel_time(kind, reset=True)
+    plan.set_option(mpw.OPT_TIMING, 0)
+    plan.close()
+    products = PRODUCTS[args.precision]
+    if kind == mpw.KERNEL_TC:
+        achieved = kflop * products / (kms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["bf16_tflops"], "traffic": None,
+                "kernel": "tc_chain kernels and tc_fxb_kernel (powers, products, squarings)",
+                "peak_source": peak_src + " bf16 burst", "counted": "%d bfloat16 product(s) per term" % products}
+    else:
+        smax = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * smax * 1e6 / 1e12
+        achieved = kflop / (kms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "simt_gemm",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+    roof["launches_timed"] = kl
+    roof["avg_launch_us"] = kms * 1e3 / max(kl, 1)
+    roof["kernel_share_of_step"] = kms / max(args.steps, 3) / (t_ms / args.steps)
+    if rank != 0:
+        return
+    cb = cpu_sample_expm(wk, args.cpu_budget) if world == 1 and not args.no_cpu else None
+    line = {"metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision],
+            "data": "synthetic", "config": config_for(args, wk, world),
+            "rel_frobenius_vs_f64": errs, "status": st, "wall_s_timed": wall, "clocks": clocks,
+            "e2e": {"value": e2e_steps * flop_step / (e2e_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": int(A_host.nbytes), "d2h_bytes_per_step": int(A_host.nbytes) + 8},
             "gpu_launches": launches, "roofline": roof, "cpu_baseline": cb}
     print(json.dumps(line))
 
@@ -1098,6 +1262,8 @@ def main():
         run_serving(args, wk, world, rank, local)
     elif wk.get("kind") == "modp":
         run_modp(args, wk, world, rank, local)
+    elif wk.get("kind") == "expm":
+        run_expm(args, wk, world, rank, local)
     elif wk.get("kind") == "naive":
         run_naive(args, wk, world, rank, local)
     else:

@@ -186,7 +186,7 @@ extern "C" matpow_status matpow_plan(matpow_plan_t* out, int max_n, matpow_preci
   if (e == cudaSuccess) e = tc_chain_init(p);
   if (e == cudaSuccess) e = tc_modp_init();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMallocHost(&p->h_status, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_status, 4 * sizeof(unsigned));  // status, expm norm
   cudaSetDevice(prev);
   if (e != cudaSuccess) {
     matpow_plan_destroy(p);
@@ -219,6 +219,7 @@ extern "C" matpow_status matpow_plan_destroy(matpow_plan_t p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->ws) cudaFree(p->ws);
   if (p->expm_ws) cudaFree(p->expm_ws);
+  if (p->expm_ev) cudaEventDestroy(p->expm_ev);
   batch_free(p);
   tc_free(p);
   if (p->h_status) cudaFreeHost(p->h_status);

@@ -9,8 +9,8 @@
 //   B  = A 2^-s                             (exact), so ||B||_1 <= 1
 //   T  = sum_{k <= 11} B^k / k!             (truncation < 1/12! ~ 2e-9 relative)
 //      = P0 + B^4 (P1 + B^4 P2),  Pj = sum_{i < 4} B^i / (4j + i)!
-//        (Paterson and Stockmeyer 1973: five products B^2, B^3, B^4 and two
-//        outer ones instead of ten in Horner's rule)
+//        (Paterson and Stockmeyer 1973: B^2, B^3, B^4 -- one matpow_batched
+//        call -- and two outer products instead of ten in Horner's rule)
 //   e^A = T^(2^s)                           (matpow_f32: s squarings)
 #include <cuda_runtime.h>
 
@@ -32,34 +32,46 @@ namespace {
 
 constexpr int kMats = 7;  // B, B^2, B^3, B^4, P0, P1, P2 (later Q, P1 + Q, R, T)
 
-// Largest column sum of |A| (float64 sums); a non-finite entry makes it NaN
-// or inf, whose bits exceed every finite value's.
-__global__ void expm_norm1_kernel(const float* __restrict__ A, int N, unsigned* out) {
+// Column sums of |A| in float64: block (x, y) adds rows 64 y .. 64 y + 63 of
+// columns 256 x .. 256 x + 255 into colsum (zeroed before).
+constexpr int kNormRows = 64;
+__global__ void expm_colsum_kernel(const float* __restrict__ A, int N, double* colsum) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
+  const int i0 = blockIdx.y * kNormRows, i1 = min(N, i0 + kNormRows);
   double s = 0.0;
-  for (int i = 0; i < N; ++i) s += fabs((double)A[(size_t)i * N + j]);
-  const float f = (float)s;
-  atomicMax(out, isnan(f) ? 0x7fffffffu : __float_as_uint(f));
+  for (int i = i0; i < i1; ++i) s += fabs((double)A[(size_t)i * N + j]);
+  atomicAdd(&colsum[j], s);
 }
 
-__global__ void expm_scale_kernel(const float* __restrict__ A, float* __restrict__ B, size_t n, int k) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    B[i] = mul_pow2(A[i], k);
+// ||A||_1 = the largest column sum, as float bits; a non-finite entry makes a
+// sum NaN or inf, whose bits (0x7fffffff for NaN) exceed every finite value's.
+__global__ void expm_colmax_kernel(const double* __restrict__ colsum, int N, unsigned* out) {
+  unsigned m = 0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const float f = (float)colsum[j];
+    m = max(m, isnan(f) ? 0x7fffffffu : __float_as_uint(f));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 struct Coef {
   double c[12];  // 1 / k!, k = 0 .. 11
 };
 
-// Pj = c[4j] I + c[4j+1] B + c[4j+2] B^2 + c[4j+3] B^3, summed in float64.
-__global__ void expm_combo_kernel(const float* __restrict__ B, const float* __restrict__ B2,
-                                  const float* __restrict__ B3, float* P0, float* P1, float* P2, int N,
-                                  const Coef co) {
+// B^k = M_k 2^(E_k - k s) from the powers of A in mantissa form (exact
+// power-of-two rescaling, in float64); Pj = c[4j] I + c[4j+1] B + c[4j+2] B^2
+// + c[4j+3] B^3 summed in float64; B^4 written over M_4 as float32.
+__global__ void expm_combo_kernel(const float* __restrict__ A, const float* __restrict__ M2,
+                                  const float* __restrict__ M3, float* M4, const long long* __restrict__ E,
+                                  int sq, float* P0, float* P1, float* P2, int N, const Coef co) {
   const size_t n = (size_t)N * N;
+  const int e2 = (int)(E[0] - 2LL * sq), e3 = (int)(E[1] - 3LL * sq), e4 = (int)(E[2] - 4LL * sq);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const double d = (i / N == i % N) ? 1.0 : 0.0;
-    const double b = B[i], b2 = B2[i], b3 = B3[i];
+    const double b = ldexp((double)A[i], -sq), b2 = ldexp((double)M2[i], e2), b3 = ldexp((double)M3[i], e3);
+    M4[i] = (float)ldexp((double)M4[i], e4);
     float* P[3] = {P0, P1, P2};
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -124,50 +136,70 @@ extern "C" matpow_status matpow_expm(matpow_plan_t p, const float* dA, int N, fl
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nn = (size_t)N * N, cap = (size_t)p->max_n * p->max_n;
   if (!p->expm_ws) {
-    cudaError_t e = cudaMalloc(&p->expm_ws, kMats * cap * sizeof(float) + 256);
+    const size_t bytes = kMats * cap * sizeof(float) + 16 + sizeof(double) * (size_t)p->max_n + 256;
+    cudaError_t e = cudaMalloc(&p->expm_ws, bytes);
     if (e != cudaSuccess) {
       p->expm_ws = nullptr;
-      return fail(p, MATPOW_ENOMEM, "matpow_expm: scratch of %zu bytes", kMats * cap * sizeof(float) + 256);
+      return fail(p, MATPOW_ENOMEM, "matpow_expm: scratch of %zu bytes", bytes);
     }
+  }
+  if (!p->expm_ev) {
+    CK(p, cudaEventCreateWithFlags(&p->expm_ev, cudaEventDisableTiming));
   }
   float* M[kMats];
   for (int i = 0; i < kMats; ++i) M[i] = p->expm_ws + (size_t)i * cap;
-  unsigned* dnorm = (unsigned*)(p->expm_ws + (size_t)kMats * cap);
+  double* colsum = (double*)(((uintptr_t)(p->expm_ws + (size_t)kMats * cap) + 15) & ~(uintptr_t)15);
+  long long* E = (long long*)(colsum + p->max_n);  // exponents of A^2, A^3, A^4
+  unsigned* dnorm = (unsigned*)(E + 4);
 
-  // s from ||A||_1 (read back: it fixes the number of squarings)
+  // ||A||_1 on the device; its read-back (it fixes s) overlaps the powers
+  // A^2, A^3, A^4, which do not depend on s (B^k = A^k 2^(-k s))
+  CK(p, cudaMemsetAsync(colsum, 0, sizeof(double) * N, s));
   CK(p, cudaMemsetAsync(dnorm, 0, sizeof(unsigned), s));
-  expm_norm1_kernel<<<(N + 127) / 128, 128, 0, s>>>(dA, N, dnorm);
+  expm_colsum_kernel<<<dim3((N + 255) / 256, (N + kNormRows - 1) / kNormRows), 256, 0, s>>>(dA, N, colsum);
   CK(p, cudaGetLastError());
-  p->launches++;
-  unsigned hbits = 0;
-  CK(p, cudaMemcpyAsync(&hbits, dnorm, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  CK(p, cudaStreamSynchronize(s));
+  expm_colmax_kernel<<<1, 256, 0, s>>>(colsum, N, dnorm);
+  CK(p, cudaGetLastError());
+  p->launches += 2;
+  unsigned* hbits = p->h_status + 1;  // pinned word next to the status read-back
+  CK(p, cudaMemcpyAsync(hbits, dnorm, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(p, cudaEventRecord(p->expm_ev, s));
+  {
+    const float* as[3] = {dA, dA, dA};
+    const int ns3[3] = {N, N, N};
+    const uint64_t ks[3] = {2, 3, 4};
+    float* outs[3] = {M[1], M[2], M[3]};
+    matpow_status st = matpow_batched(p, 3, as, ns3, ks, outs, (int64_t*)E, stream);
+    if (st != MATPOW_OK) return st;
+  }
+  CK(p, cudaEventSynchronize(p->expm_ev));
   float nrm;
-  std::memcpy(&nrm, &hbits, sizeof nrm);
-  if (!std::isfinite(nrm)) return fail(p, MATPOW_EINVAL, "matpow_expm: non-finite input");
+  std::memcpy(&nrm, hbits, sizeof nrm);
+  if (!std::isfinite(nrm)) {
+    // the powers already enqueued flag the same input; that flag belongs to
+    // this call's EINVAL, not to the next matpow_sync
+    CK(p, cudaStreamSynchronize(s));
+    CK(p, cudaMemsetAsync(p->status, 0, sizeof(unsigned), s));
+    CK(p, cudaStreamSynchronize(s));
+    return fail(p, MATPOW_EINVAL, "matpow_expm: non-finite input");
+  }
   int sq = 0;
   if (nrm > 1.0f) sq = (int)std::ceil(std::log2((double)nrm));
   while (sq > 0 && std::ldexp((double)nrm, -(sq - 1)) <= 1.0) --sq;  // smallest s with ||A|| 2^-s <= 1
   while (std::ldexp((double)nrm, -sq) > 1.0) ++sq;
   if (sq > 62) return fail(p, MATPOW_EINVAL, "matpow_expm: ||A||_1 = %g is beyond 2^62", (double)nrm);
 
-  // B = A 2^-s; B^2, B^3, B^4; the three Pj
-  expm_scale_kernel<<<grid_for(nn), 256, 0, s>>>(dA, M[0], nn, -sq);
-  CK(p, cudaGetLastError());
-  p->launches++;
-  matpow_status st;
-  if ((st = product(p, M[0], M[0], N, M[1], s)) != MATPOW_OK) return st;  // B^2
-  if ((st = product(p, M[1], M[0], N, M[2], s)) != MATPOW_OK) return st;  // B^3
-  if ((st = product(p, M[1], M[1], N, M[3], s)) != MATPOW_OK) return st;  // B^4
+  // B^4 and the three Pj
   Coef co;
   double f = 1.0;
   for (int k = 0; k < 12; ++k) {
     if (k > 0) f *= k;
     co.c[k] = 1.0 / f;
   }
-  expm_combo_kernel<<<grid_for(nn), 256, 0, s>>>(M[0], M[1], M[2], M[4], M[5], M[6], N, co);
+  expm_combo_kernel<<<grid_for(nn), 256, 0, s>>>(dA, M[1], M[2], M[3], E, sq, M[4], M[5], M[6], N, co);
   CK(p, cudaGetLastError());
   p->launches++;
+  matpow_status st;
   // T = P0 + B^4 (P1 + B^4 P2)
   if ((st = product(p, M[3], M[6], N, M[0], s)) != MATPOW_OK) return st;  // Q = B^4 P2
   expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[5], M[0], M[5], nn);     // P1 + Q

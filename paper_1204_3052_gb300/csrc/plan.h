@@ -103,7 +103,8 @@ struct matpow_plan_s {
   bool persist = true;    // batched 64-column levels: persistent grouped kernel
   bool naive = false;     // float powers by n - 1 products R <- R A (comparison method)
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
-  float* expm_ws = nullptr;  // matpow_expm scratch: 7 max_n^2 float32 + a word, on first use
+  float* expm_ws = nullptr;  // matpow_expm scratch: 7 max_n^2 float32 + column sums, on first use
+  cudaEvent_t expm_ev = nullptr;  // matpow_expm: the norm's read-back has landed
   // graphs
   std::vector<mp::GraphEntry> graphs;
   uint64_t graph_clock = 0;
