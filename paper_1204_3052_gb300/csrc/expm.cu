@@ -32,9 +32,9 @@ namespace {
 
 constexpr int kMats = 7;  // B, B^2, B^3, B^4, P0, P1, P2 (later Q, P1 + Q, R, T)
 
-// Column sums of |A| in float64: block (x, y) adds rows 64 y .. 64 y + 63 of
+// Column sums of |A| in float64: block (x, y) adds rows 16 y .. 16 y + 15 of
 // columns 256 x .. 256 x + 255 into colsum (zeroed before).
-constexpr int kNormRows = 64;
+constexpr int kNormRows = 16;
 __global__ void expm_colsum_kernel(const float* __restrict__ A, int N, double* colsum) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
@@ -57,25 +57,32 @@ __global__ void expm_colmax_kernel(const double* __restrict__ colsum, int N, uns
 }
 
 struct Coef {
-  double c[12];  // 1 / k!, k = 0 .. 11
+  float c[12];  // 1 / k!, k = 0 .. 11, rounded to float32
 };
 
+// x 2^k for the exponents of this kernel (k >= -500): exact while the result
+// is normal; below 2^-250 relative the term is negligible and becomes 0.
+__device__ __forceinline__ float scale_pow2(float x, long long k) {
+  if (k < -250) return 0.f;
+  return mul_pow2(x, (int)k);
+}
+
 // B^k = M_k 2^(E_k - k s) from the powers of A in mantissa form (exact
-// power-of-two rescaling, in float64); Pj = c[4j] I + c[4j+1] B + c[4j+2] B^2
-// + c[4j+3] B^3 summed in float64; B^4 written over M_4 as float32.
+// power-of-two rescaling); Pj = c[4j] I + c[4j+1] B + c[4j+2] B^2 +
+// c[4j+3] B^3 by float32 fmaf (largest power first); B^4 written over M_4.
 __global__ void expm_combo_kernel(const float* __restrict__ A, const float* __restrict__ M2,
                                   const float* __restrict__ M3, float* M4, const long long* __restrict__ E,
                                   int sq, float* P0, float* P1, float* P2, int N, const Coef co) {
   const size_t n = (size_t)N * N;
-  const int e2 = (int)(E[0] - 2LL * sq), e3 = (int)(E[1] - 3LL * sq), e4 = (int)(E[2] - 4LL * sq);
+  const long long e2 = E[0] - 2LL * sq, e3 = E[1] - 3LL * sq, e4 = E[2] - 4LL * sq;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double d = (i / N == i % N) ? 1.0 : 0.0;
-    const double b = ldexp((double)A[i], -sq), b2 = ldexp((double)M2[i], e2), b3 = ldexp((double)M3[i], e3);
-    M4[i] = (float)ldexp((double)M4[i], e4);
+    const float d = (i / N == i % N) ? 1.f : 0.f;
+    const float b = mul_pow2(A[i], -sq), b2 = scale_pow2(M2[i], e2), b3 = scale_pow2(M3[i], e3);
+    M4[i] = scale_pow2(M4[i], e4);
     float* P[3] = {P0, P1, P2};
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      P[j][i] = (float)(co.c[4 * j] * d + co.c[4 * j + 1] * b + co.c[4 * j + 2] * b2 + co.c[4 * j + 3] * b3);
+      P[j][i] = fmaf(co.c[4 * j + 3], b3, fmaf(co.c[4 * j + 2], b2, fmaf(co.c[4 * j + 1], b, co.c[4 * j] * d)));
   }
 }
 
@@ -194,7 +201,7 @@ extern "C" matpow_status matpow_expm(matpow_plan_t p, const float* dA, int N, fl
   double f = 1.0;
   for (int k = 0; k < 12; ++k) {
     if (k > 0) f *= k;
-    co.c[k] = 1.0 / f;
+    co.c[k] = (float)(1.0 / f);
   }
   expm_combo_kernel<<<grid_for(nn), 256, 0, s>>>(dA, M[1], M[2], M[3], E, sq, M[4], M[5], M[6], N, co);
   CK(p, cudaGetLastError());
