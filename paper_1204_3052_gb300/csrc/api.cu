@@ -690,6 +690,11 @@ static matpow_status run_maybe_graph(matpow_plan_s* p, const GraphKey& key, cuda
   return MATPOW_OK;
 }
 
+matpow_status mp::run_graph_or_direct(matpow_plan_s* p, const GraphKey& key, cudaStream_t s,
+                                      const std::function<matpow_status(cudaStream_t)>& enqueue) {
+  return run_maybe_graph(p, key, s, enqueue);
+}
+
 struct DeviceGuard {
   int prev = 0;
   explicit DeviceGuard(int dev) {

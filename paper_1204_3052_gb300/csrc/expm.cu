@@ -116,6 +116,38 @@ matpow_status product(matpow_plan_s* p, const float* X, const float* Y, int N, f
   return enqueue_product_f32(p, X, Y, N, out, s);
 }
 
+// B^4, P0 .. P2, T = P0 + B^4 (P1 + B^4 P2), e^A = T^(2^sq) on stream s.
+matpow_status expm_tail(matpow_plan_s* p, const float* dA, int N, float* const* M, const long long* E, int sq,
+                        float* dOut, int64_t* dLog2Scale, cudaStream_t s) {
+  const size_t nn = (size_t)N * N;
+  // B^4 and the three Pj
+  Coef co;
+  double f = 1.0;
+  for (int k = 0; k < 12; ++k) {
+    if (k > 0) f *= k;
+    co.c[k] = (float)(1.0 / f);
+  }
+  expm_combo_kernel<<<grid_for(nn), 256, 0, s>>>(dA, M[1], M[2], M[3], E, sq, M[4], M[5], M[6], N, co);
+  CK(p, cudaGetLastError());
+  p->launches++;
+  matpow_status st;
+  // T = P0 + B^4 (P1 + B^4 P2)
+  if ((st = product(p, M[3], M[6], N, M[0], s)) != MATPOW_OK) return st;  // Q = B^4 P2
+  expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[5], M[0], M[5], nn);     // P1 + Q
+  CK(p, cudaGetLastError());
+  if ((st = product(p, M[3], M[5], N, M[1], s)) != MATPOW_OK) return st;  // R
+  expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[4], M[1], M[2], nn);     // T = P0 + R
+  CK(p, cudaGetLastError());
+  p->launches += 2;
+  // e^A = T^(2^s)
+  if (sq == 0) {
+    CK(p, launch_copy(M[2], dOut, N, (long long*)dLog2Scale, s));
+    p->launches++;
+    return MATPOW_OK;
+  }
+  return matpow_f32(p, M[2], N, 1ull << sq, dOut, dLog2Scale, s);
+}
+
 }  // namespace
 }  // namespace mp
 
@@ -196,30 +228,9 @@ extern "C" matpow_status matpow_expm(matpow_plan_t p, const float* dA, int N, fl
   while (std::ldexp((double)nrm, -sq) > 1.0) ++sq;
   if (sq > 62) return fail(p, MATPOW_EINVAL, "matpow_expm: ||A||_1 = %g is beyond 2^62", (double)nrm);
 
-  // B^4 and the three Pj
-  Coef co;
-  double f = 1.0;
-  for (int k = 0; k < 12; ++k) {
-    if (k > 0) f *= k;
-    co.c[k] = (float)(1.0 / f);
-  }
-  expm_combo_kernel<<<grid_for(nn), 256, 0, s>>>(dA, M[1], M[2], M[3], E, sq, M[4], M[5], M[6], N, co);
-  CK(p, cudaGetLastError());
-  p->launches++;
-  matpow_status st;
-  // T = P0 + B^4 (P1 + B^4 P2)
-  if ((st = product(p, M[3], M[6], N, M[0], s)) != MATPOW_OK) return st;  // Q = B^4 P2
-  expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[5], M[0], M[5], nn);     // P1 + Q
-  CK(p, cudaGetLastError());
-  if ((st = product(p, M[3], M[5], N, M[1], s)) != MATPOW_OK) return st;  // R
-  expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[4], M[1], M[2], nn);     // T = P0 + R
-  CK(p, cudaGetLastError());
-  p->launches += 2;
-  // e^A = T^(2^s)
-  if (sq == 0) {
-    CK(p, launch_copy(M[2], dOut, N, (long long*)dLog2Scale, s));
-    p->launches++;
-    return MATPOW_OK;
-  }
-  return matpow_f32(p, M[2], N, 1ull << sq, dOut, dLog2Scale, stream);
+  // the rest depends only on s and the pointers: one CUDA graph per s
+  GraphKey key{2, dA, dOut, dLog2Scale, N, (uint64_t)sq, 0};
+  return run_graph_or_direct(p, key, s, [&](cudaStream_t st) {
+    return expm_tail(p, dA, N, M, E, sq, dOut, dLog2Scale, st);
+  });
 }

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 #include <utility>
 #include <vector>
@@ -27,7 +28,7 @@ struct LevelOps {
 void build_schedule(uint64_t n, std::vector<LevelOps>* levels);
 
 struct GraphKey {
-  int kind;  // 0 float, 1 mod p
+  int kind;  // 0 float, 1 mod p, 2 the e^A sequence after the norm (n = s)
   const void* A;
   void* out;
   void* log2;
@@ -142,6 +143,11 @@ bool tc_encode_bf16_map(CUtensorMap* m, const void* base, int N, int ld, int box
 // (exact split; small and medium N).  *used = false when it does not apply.
 matpow_status tc_chain_run(matpow_plan_s* p, const float* dA, int N, uint64_t n, float* dOut,
                            int64_t* dLog2, cudaStream_t s, bool* used);
+// Run `enqueue` on s, or replay the CUDA graph captured from it the first
+// time `key` was seen (the plan's graph cache; direct while timing or inside
+// a caller's capture).
+matpow_status run_graph_or_direct(matpow_plan_s* p, const GraphKey& key, cudaStream_t s,
+                                  const std::function<matpow_status(cudaStream_t)>& enqueue);
 // C = X Y of two float32 N x N matrices (N > tiny_max), value-mode float32
 // output, through the plan's product path (uses buffers 0, 1, scale slots 0-3).
 matpow_status enqueue_product_f32(matpow_plan_s* p, const float* X, const float* Y, int N, float* out,
