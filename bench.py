@@ -598,6 +598,22 @@ def run_ours(args, wk, world, rank, local):
     if tr:
         roof["traffic"] = tr[0]
         roof["traffic_source"] = tr[1]
+    latency = None
+    if N <= 64 and len(ns) == 1:
+        # a latency-bound power: the distribution of one call's device time
+        # (CUDA events around each call, 1000 calls back to back, L2 warm)
+        reps = 1000
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                 for _ in range(reps)]
+        with torch.cuda.stream(stream):
+            for a, b in pairs:
+                a.record(stream)
+                step(stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+        us = sorted(a.elapsed_time(b) * 1e3 for a, b in pairs)
+        latency = {"unit": "us", "p50": us[reps // 2], "p99": us[int(reps * 0.99)], "min": us[0], "reps": reps,
+                   "note": "per call, back to back, L2 warm"}
 
     if rank != 0:
         return
@@ -621,6 +637,8 @@ def run_ours(args, wk, world, rank, local):
         "roofline": roof,
         "cpu_baseline": cb,
     }
+    if latency:
+        line["latency"] = latency
     print(json.dumps(line))
     plan.close()
 
