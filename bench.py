@@ -945,6 +945,42 @@ def run_naive(args, wk, world, rank, local):
     print(json.dumps(line))
 
 
+def batch_roofline_ms(Ns, ns, prec, peaks) -> float:
+    """Lower bound of a batch step's level launches: level L holds the L-th
+    level of every matrix's schedule (its squaring and, if that bit of n is
+    set, R <- R P), and takes at least max(algorithmic bytes / HBM copy
+    bandwidth, tensor flop / bf16 peak); the bound is the sum over levels.
+    Algorithmic bytes of a product: read each distinct operand's slice planes
+    once (2 B per slice per element), write the next ones; orders N <= 64
+    (the on-chip small-order chain) are left out."""
+    planes = {"bf16x6": 3, "bf16x3": 2, "bf16": 1, "fp32": 2}[prec]
+    per_prod = PRODUCTS[prec]
+    levels = {}
+    for N, n in zip(Ns, ns):
+        if N <= 64 or n < 2:
+            continue
+        bits, L, have_r = n, 0, False
+        while bits:
+            ops = []
+            if bits & 1:
+                if have_r:
+                    ops.append(False)  # R <- R P (distinct operands)
+                have_r = True
+            bits >>= 1
+            if bits:
+                ops.append(True)  # P <- P P
+            if ops:
+                by, fl = levels.get(L, (0.0, 0.0))
+                for sq in ops:
+                    by += 2.0 * planes * N * N * ((1 if sq else 2) + 1)
+                    fl += per_prod * 2.0 * N ** 3
+                levels[L] = (by, fl)
+                L += 1
+    bw = peaks.get("hbm_gbs", 6704.5) * 1e9
+    tf = peaks["bf16_tflops"] * 1e12
+    return sum(max(by / bw, fl / tf) for by, fl in levels.values()) * 1e3
+
+
 def run_batched(args, wk, world, rank, local):
     """Config 3: one matpow_batched call over an uneven batch per step."""
     import torch
@@ -1054,6 +1090,7 @@ def run_batched(args, wk, world, rank, local):
     tr = TRAFFIC.get((args.workload, args.precision))
     if tr:
         roof["traffic"], roof["traffic_source"] = tr
+    roof["level_roofline_bound_ms"] = batch_roofline_ms(Ns, ns, args.precision, peaks)
     if rank != 0:
         return
     cb = None
