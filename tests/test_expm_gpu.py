@@ -120,3 +120,26 @@ def test_expm_edge_cases(plans):
     assert mpw.matpow_expm(p.h, dA, 0, out, None) == mpw.OK
     assert mpw.matpow_expm(p.h, dA, 701, out, None) == mpw.EINVAL
     assert p.sync() == mpw.OK
+
+
+def test_expm_other_paths():
+    # plain BF16 products (8 significant bits: a loose class) and the
+    # tensor-core path at N = 64 (tiny_max = 0: one 64 x 64 block, one tile)
+    from paper_1204_3052_gb300 import matpow as mpw
+    A = (wl.gaussian(100, 9) * 1.5).astype(np.float32)
+    want = oracle.expm_f64(A)
+    p = mpw.Plan(128, "bf16")
+    err = np.linalg.norm(run(p, A) - want) / np.linalg.norm(want)
+    p.close()
+    assert err < 0.1, err
+    p = mpw.Plan(64, "bf16x6")
+    p.set_option(mpw.OPT_TINY_MAX, 0)
+    for N in (64,):
+        A = (wl.gaussian(N, 10 + N) * 2.0).astype(np.float32)
+        want = oracle.expm_f64(A)
+        g, s = gate(A, want)
+        M, e = oracle.expm_emu_ps(A, "bf16x6blk")
+        g = max(g, 2.0 * np.linalg.norm(np.ldexp(M.astype(np.float64), e) - want) / np.linalg.norm(want))
+        err = np.linalg.norm(run(p, A) - want) / np.linalg.norm(want)
+        assert err <= g, (N, s, err, g)
+    p.close()
