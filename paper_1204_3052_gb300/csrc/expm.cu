@@ -203,13 +203,18 @@ extern "C" matpow_status matpow_expm(matpow_plan_t p, const float* dA, int N, fl
   unsigned* hbits = p->h_status + 1;  // pinned word next to the status read-back
   CK(p, cudaMemcpyAsync(hbits, dnorm, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(p, cudaEventRecord(p->expm_ev, s));
-  {
+  if (p->prec == MATPOW_FP32_SIMT || fmt_exact(plan_float_fmt(p)) || N <= p->tiny_max) {
     const float* as[3] = {dA, dA, dA};
     const int ns3[3] = {N, N, N};
     const uint64_t ks[3] = {2, 3, 4};
     float* outs[3] = {M[1], M[2], M[3]};
     matpow_status st = matpow_batched(p, 3, as, ns3, ks, outs, (int64_t*)E, stream);
     if (st != MATPOW_OK) return st;
+  } else {  // precisions without grouped launches: three single powers
+    for (int k = 0; k < 3; ++k) {
+      matpow_status st = matpow_f32(p, dA, N, (uint64_t)(k + 2), M[k + 1], (int64_t*)(E + k), stream);
+      if (st != MATPOW_OK) return st;
+    }
   }
   CK(p, cudaEventSynchronize(p->expm_ev));
   float nrm;
