@@ -196,7 +196,8 @@ matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, float* dOut
  *   e^A = T^(2^s) by matpow_f32 (s squarings).
  *   dA, dOut, dLog2Scale   as in matpow_f32; dOut may alias dA.
  * Reads ||A||_1 back to the host (it fixes s), so the call waits for the
- * stream up to that point; not for use inside a stream capture.  A
+ * stream up to that point; on a stream that is being captured it returns
+ * MATPOW_EINVAL without enqueueing anything.  A
  * non-finite entry or ||A||_1 > 2^62 returns MATPOW_EINVAL.  The first call
  * on a plan allocates 7 max_n^2 float32 of scratch (MATPOW_ENOMEM if that
  * fails).  Accuracy: float32 class, the error growing with s (each squaring

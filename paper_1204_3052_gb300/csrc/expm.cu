@@ -173,6 +173,10 @@ extern "C" matpow_status matpow_expm(matpow_plan_t p, const float* dA, int N, fl
     }
   } restore{prev};
   cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(p, cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(p, MATPOW_EINVAL, "matpow_expm: the stream is being captured (the norm is read back to the host)");
   const size_t nn = (size_t)N * N, cap = (size_t)p->max_n * p->max_n;
   if (!p->expm_ws) {
     const size_t bytes = kMats * cap * sizeof(float) + 16 + sizeof(double) * (size_t)p->max_n + 256;

@@ -143,3 +143,21 @@ def test_expm_other_paths():
         err = np.linalg.norm(run(p, A) - want) / np.linalg.norm(want)
         assert err <= g, (N, s, err, g)
     p.close()
+
+
+def test_expm_refuses_stream_capture():
+    import torch
+    from paper_1204_3052_gb300 import matpow as mpw
+    p = mpw.Plan(128, "bf16x6")
+    A = to_dev((wl.gaussian(96, 4)).astype(np.float32))
+    out = torch.empty_like(A)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        st = mpw.matpow_expm(p.h, A, 96, out, None, s)
+        g.capture_end()
+    assert st == mpw.EINVAL
+    assert "captured" in mpw.load().matpow_last_error(p.h).decode()
+    assert p.sync() == mpw.OK
+    p.close()
