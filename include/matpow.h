@@ -72,7 +72,8 @@ typedef struct matpow_plan_s* matpow_plan_t;
  * (>= 1) with float arithmetic `precision`.  The plan allocates its device
  * workspace here (partial products, scale exponents, status words); no later
  * call allocates device memory except matpow_batched, which grows a plan-owned
- * descriptor table on first use of a larger batch.  `workspace_bytes` = 0
+ * descriptor table on first use of a larger batch, and matpow_expm, which
+ * allocates its scratch on its first call.  `workspace_bytes` = 0
  * lets the plan take what max_n needs (matpow_workspace_size); a nonzero
  * value is an upper limit, and the call fails with MATPOW_ENOMEM if the need
  * exceeds it.  Fails with MATPOW_EUNSUPPORTED if the device is not sm_103.
@@ -97,8 +98,11 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       call from a cached CUDA graph; 0: launch directly.
  *   MATPOW_OPT_TIMING   1: record CUDA events around every product kernel on
  *                       the caller's stream (read with matpow_kernel_time); 0 (default).
- *   MATPOW_OPT_TINY_MAX largest N handled by the single-kernel whole-chain path
- *                       (0 disables it; default 64).
+ *   MATPOW_OPT_TINY_MAX largest N handled by the on-chip whole-chain path
+ *                       (float32 products in shared memory: one CTA per
+ *                       matrix, or for a single power with N > 32 one
+ *                       four-CTA cluster; 0 disables it; default and
+ *                       maximum 64).
  *   MATPOW_OPT_TILE     tensor-core tile width override (columns of C per CTA:
  *                       64, 128 or 256; 0 = the built-in choice by N).
  *   MATPOW_OPT_SPLIT    MATPOW_BF16X3 operand split: 0 (default) exact
@@ -119,8 +123,9 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       split-K (bit-for-bit equal to the level path);
  *                       0: one launch per level.
  *   MATPOW_OPT_MODP_TC  1 (default): matpow_mod_p with 64 < N <= 16384 runs on the
- *                       tensor cores (byte slices of the residues, exact partial
- *                       sums); 0: 64-bit integer products on the CUDA cores.
+ *                       tensor cores (balanced byte digits of the residues,
+ *                       exact partial sums); 0: 64-bit integer products on the
+ *                       CUDA cores.
  *   MATPOW_OPT_PERSIST  1 (default): matpow_batched runs each level's 64-column
  *                       tensor-core tiles (orders up to 4096) in one persistent
  *                       launch, one CTA per SM walking the whole tile list; 0:
@@ -150,9 +155,10 @@ matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value)
  *   dLog2Scale  device int64 or NULL.  If non-NULL the result is returned in
  *               mantissa form: dOut holds M and *dLog2Scale holds e with
  *               A^n = M * 2^e (max|M| <= N; never overflows).  If NULL, dOut
- *               holds A^n rounded to float32 (rescaled in float64 on the
- *               device); entries beyond the float32 range become +-inf or 0
- *               and matpow_sync() then returns MATPOW_ERANGE.
+ *               holds A^n as M * 2^e rounded once to float32 (exact while
+ *               the result is a normal float; one rounding into the
+ *               subnormals); entries beyond the float32 range become +-inf
+ *               or 0 and matpow_sync() then returns MATPOW_ERANGE.
  *   stream      cudaStream_t.
  * Intermediate powers are kept with a per-matrix power-of-two exponent so
  * that n up to 2^64-1 never overflows.  Asynchronous.
@@ -197,8 +203,8 @@ matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, float* dOut
  *   dA, dOut, dLog2Scale   as in matpow_f32; dOut may alias dA.
  * Reads ||A||_1 back to the host (it fixes s), so the call waits for the
  * stream up to that point; on a stream that is being captured it returns
- * MATPOW_EINVAL without enqueueing anything.  A
- * non-finite entry or ||A||_1 > 2^62 returns MATPOW_EINVAL.  The first call
+ * MATPOW_EINVAL without enqueueing anything.  A non-finite entry or
+ * ||A||_1 > 2^62 returns MATPOW_EINVAL.  The first call
  * on a plan allocates 7 max_n^2 float32 of scratch (MATPOW_ENOMEM if that
  * fails).  Accuracy: float32 class, the error growing with s (each squaring
  * doubles the relative error of the dominant eigenvalues).
