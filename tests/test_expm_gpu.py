@@ -161,3 +161,18 @@ def test_expm_refuses_stream_capture():
     assert "captured" in mpw.load().matpow_last_error(p.h).decode()
     assert p.sync() == mpw.OK
     p.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x3"])
+def test_expm_bench_workload(plans, prec):
+    # the bench's e^A input (4 N(0, 1/N) of order 512, seed 0; s = 7) through
+    # the same call the bench times
+    A = (wl.gaussian(512, 0) * 4.0).astype(np.float32)
+    want = oracle.expm_f64(A)
+    g, s = gate(A, want)
+    assert s == 7
+    if prec == "bf16x3":
+        M, e = oracle.expm_emu_ps(A, "bf16x3blk")
+        g = max(g, 2.0 * np.linalg.norm(np.ldexp(M.astype(np.float64), e) - want) / np.linalg.norm(want))
+    err = np.linalg.norm(run(plans[prec], A) - want) / np.linalg.norm(want)
+    assert err <= g, (prec, err, g)
