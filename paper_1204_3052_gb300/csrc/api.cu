@@ -585,21 +585,28 @@ static matpow_status enqueue_modp(matpow_plan_s* p, const uint32_t* dA, int N, u
 }
 
 matpow_status mp::enqueue_product_f32(matpow_plan_s* p, const float* X, const float* Y, int N, float* out,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, bool keep_x) {
   const int fmt = plan_float_fmt(p);
   const long long plane = plane_offset_elems(N, fmt);
-  CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * 4, s));
-  if (fmt_exact(fmt)) {
-    CK(p, launch_prep_fxb(X, N, fmt, p->buf[0], &p->scales[1], p->status, s));
-    CK(p, launch_prep_fxb(Y, N, fmt, p->buf[1], &p->scales[2], p->status, s));
-    p->launches += 2;
+  if (keep_x) {  // X's split and slot 1 stay; clear Y's and the output's slots
+    CK(p, cudaMemsetAsync(&p->scales[2], 0, sizeof(Scale) * 2, s));
   } else {
-    CK(p, launch_absmax_f32(X, N, &p->scales[0], p->status, s));
-    CK(p, launch_convert_f32(X, N, &p->scales[0], &p->scales[1], fmt, p->buf[0], plane, s));
+    CK(p, cudaMemsetAsync(p->scales, 0, sizeof(Scale) * 4, s));
+  }
+  if (fmt_exact(fmt)) {
+    if (!keep_x) CK(p, launch_prep_fxb(X, N, fmt, p->buf[0], &p->scales[1], p->status, s));
+    CK(p, launch_prep_fxb(Y, N, fmt, p->buf[1], &p->scales[2], p->status, s));
+    p->launches += keep_x ? 1 : 2;
+  } else {
+    if (!keep_x) {
+      CK(p, launch_absmax_f32(X, N, &p->scales[0], p->status, s));
+      CK(p, launch_convert_f32(X, N, &p->scales[0], &p->scales[1], fmt, p->buf[0], plane, s));
+      p->launches += 2;
+    }
     CK(p, cudaMemsetAsync(&p->scales[0], 0, sizeof(Scale), s));  // slot 0 again for Y's maximum
     CK(p, launch_absmax_f32(Y, N, &p->scales[0], p->status, s));
     CK(p, launch_convert_f32(Y, N, &p->scales[0], &p->scales[2], fmt, p->buf[1], plane, s));
-    p->launches += 4;
+    p->launches += 2;
   }
   GemmPair g{};
   g.count = 1;

@@ -106,14 +106,15 @@ int grid_for(size_t n) {
   return (int)(b < 4096 ? (b ? b : 1) : 4096);
 }
 
-matpow_status product(matpow_plan_s* p, const float* X, const float* Y, int N, float* out, cudaStream_t s) {
+matpow_status product(matpow_plan_s* p, const float* X, const float* Y, int N, float* out, cudaStream_t s,
+                      bool keep_x = false) {
   if (N <= 64 && N <= p->tiny_max) {
     expm_small_product_kernel<<<N, 64, 0, s>>>(X, Y, out, N);
     CK(p, cudaGetLastError());
     p->launches++;
     return MATPOW_OK;
   }
-  return enqueue_product_f32(p, X, Y, N, out, s);
+  return enqueue_product_f32(p, X, Y, N, out, s, keep_x);
 }
 
 // B^4, P0 .. P2, T = P0 + B^4 (P1 + B^4 P2), e^A = T^(2^sq) on stream s.
@@ -135,7 +136,7 @@ matpow_status expm_tail(matpow_plan_s* p, const float* dA, int N, float* const* 
   if ((st = product(p, M[3], M[6], N, M[0], s)) != MATPOW_OK) return st;  // Q = B^4 P2
   expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[5], M[0], M[5], nn);     // P1 + Q
   CK(p, cudaGetLastError());
-  if ((st = product(p, M[3], M[5], N, M[1], s)) != MATPOW_OK) return st;  // R
+  if ((st = product(p, M[3], M[5], N, M[1], s, true)) != MATPOW_OK) return st;  // R (B^4 still split)
   expm_add_kernel<<<grid_for(nn), 256, 0, s>>>(M[4], M[1], M[2], nn);     // T = P0 + R
   CK(p, cudaGetLastError());
   p->launches += 2;

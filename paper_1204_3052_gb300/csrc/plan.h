@@ -150,8 +150,9 @@ matpow_status run_graph_or_direct(matpow_plan_s* p, const GraphKey& key, cudaStr
                                   const std::function<matpow_status(cudaStream_t)>& enqueue);
 // C = X Y of two float32 N x N matrices (N > tiny_max), value-mode float32
 // output, through the plan's product path (uses buffers 0, 1, scale slots 0-3).
+// keep_x: X is the previous call's X, still split in buffer 0 / slot 1.
 matpow_status enqueue_product_f32(matpow_plan_s* p, const float* X, const float* Y, int N, float* out,
-                                  cudaStream_t s);
+                                  cudaStream_t s, bool keep_x = false);
 // One power of a multi-power whole-chain launch: input, order, power, output,
 // its four stored-format buffers and its scale slots (2 + G(n)).
 struct ChainJob {
