@@ -8,7 +8,8 @@ from it; the two meet only through the seeded inputs of
 
 Functions and the passage each follows:
 
-* ``gemm_f64``, ``gemm_modp``: the plain triple-loop product (Sec. 4.1), in C.
+* ``gemm_f64``, ``gemm_modp``: the plain triple-loop product (Sec. 4.1), in C;
+  ``gemm_rows_f64`` the same loop over a range of rows (a timing sample).
 * ``matpow_f64(A, n, mode)``: A^n in float64, as mantissa and power-of-two
   exponent.  ``mode="sqmul"`` is the log2(n)-product method (Sec. 4.3),
   ``mode="brute"`` the n-1 repeated products (Sec. 4.1, 4.2).
@@ -19,9 +20,16 @@ Functions and the passage each follows:
 * ``stationary(A)``: the limit 1 pi^T of A^n for a positive row-stochastic A,
   by float64 power iteration (a closed form for large n).
 * ``fp32_sqmul(A, n)``: the same square-and-multiply with every product
-  rounded to float32 (numpy float32 matmul as the product step).  It is an
-  error yardstick, not a parity target: parity unpinned (its output is only
-  used to size the error a float32-class method attains).
+  rounded to float32 (numpy float32 matmul as the product step).  An error
+  yardstick, not a parity target; pinned by exact integer chains, a diagonal
+  chain against the scalar float32 chain, and a product whose float32 sum
+  rounds differently from the float64 one.
+* ``perturbed_sqmul(A, n, rel, seed)``: the float64 chain with a seeded
+  normwise perturbation of size rel added to every stored partial product:
+  the sensitivity of A^n's chain to storage errors of that size (the
+  float32-class floor of the tests' float bounds where 2e-5 ceil(log2 n) is
+  out of reach).  Pinned by a scalar closed form, linearity in rel and
+  rel = 0 giving the oracle's power.
 * ``round_bf16``, ``split_bf16``: round-to-nearest-even to bfloat16 (8
   significant bits) and the two-part split x ~ hi + lo, hi = bf16(x),
   lo = bf16(x - hi).
@@ -46,9 +54,14 @@ Functions and the passage each follows:
   slices with one scale per matrix; "bf16x3blk": the same with one scale per
   64 x 64 block; "bf16x6blk": three block-scaled slices and the six products
   a_i b_j with i + j <= 2; products and sums in float64, each result rounded
-  to float32).  Like ``fp32_sqmul`` it is an
-  error yardstick for the lower-precision paths, not a parity target; the
-  rounding primitives it uses are pinned by the tests.
+  to float32).  An error yardstick for the lower-precision paths, not a
+  parity target.  Pinned (tests/test_oracle_yardsticks.py) by products on
+  the precisions' exact grids (equal to the exact product), products with
+  one operand off the grid (equal to the exact product of the operand
+  rounded to the grid by a one-step formula), exact integer chains, and a
+  diagonal chain against the scalar chain; a dropped slice product, a wrong
+  slice weight, a skipped rounding, a transposed operand or a dropped
+  multiply step each fail one of them.
 
 Pins (tests/test_oracle_*.py, run with ``-m "not gpu"``): Fibonacci, rotation,
 diagonal, nilpotent shift, permutation and identity closed forms; A^(m+k) =
@@ -98,6 +111,8 @@ def _load():
             lib.oracle_matpow_f64.argtypes = [ctypes.c_int, dp, ctypes.c_uint64, ctypes.c_int,
                                               dp, ip, ip]
             lib.oracle_matpow_f64.restype = ctypes.c_int
+            lib.oracle_gemm_rows_f64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+            lib.oracle_gemm_rows_f64.restype = None
             lib.oracle_gemm_modp.argtypes = [ctypes.c_int, up, up, ctypes.c_uint64, up]
             lib.oracle_gemm_modp.restype = None
             lib.oracle_matpow_modp.argtypes = [ctypes.c_int, up, ctypes.c_uint64, ctypes.c_uint64,
@@ -133,6 +148,19 @@ def gemm_f64(A, B) -> np.ndarray:
     N = _square(A)
     C = np.empty((N, N), dtype=np.float64)
     _load().oracle_gemm_f64(N, _dptr(A), _dptr(B), _dptr(C))
+    return C
+
+
+def gemm_rows_f64(A, B, r0: int, r1: int) -> np.ndarray:
+    """Rows r0 .. r1-1 of A @ B by the same triple loop as ``gemm_f64`` (each
+    entry equal to the full product's); a bounded sample of a large product."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    N = _square(A)
+    if not 0 <= r0 <= r1 <= N:
+        raise ValueError("row range outside the matrix")
+    C = np.empty((r1 - r0, N), dtype=np.float64)
+    _load().oracle_gemm_rows_f64(N, int(r0), int(r1), _dptr(A), _dptr(B), _dptr(C))
     return C
 
 
@@ -242,36 +270,84 @@ def stationary(A, iters: int = 200000, tol: float = 1e-15) -> np.ndarray:
     return pi
 
 
+def _normalise32(X, e):
+    """(X 2^-s, e + s) with s the frexp exponent of max|X| (exact power of two)."""
+    mx = float(np.max(np.abs(X))) if X.size else 0.0
+    if mx == 0.0 or not math.isfinite(mx):
+        return X, e
+    _, s = math.frexp(mx)
+    return np.ldexp(X, -s).astype(np.float32), e + s
+
+
+def _sqmul_chain(A, n: int, product):
+    """Square-and-multiply (Sec. 4.3) over the level plan ``schedule(n)``
+    with ``product(X, Y)`` (float32 result) as the product step and an exact
+    power-of-two rescale after every product.  Returns (M, e): A^n ~ M 2^e."""
+    A = np.asarray(A, dtype=np.float32)
+    N = _square(A)
+    if n == 0:
+        return np.eye(N, dtype=np.float32), 0
+    P, ep = _normalise32(A.copy(), 0)
+    R, er = None, 0
+    for k, (mul, sq) in enumerate(schedule(n)):
+        if mul:
+            R, er = _normalise32(product(R, P), er + ep)
+        elif R is None and (int(n) >> k) & 1:  # the first set bit copies P
+            R, er = P.copy(), ep
+        if sq:
+            P, ep = _normalise32(product(P, P), 2 * ep)
+    return R, er
+
+
+def _fp32_product(X, Y):
+    """float32 product (numpy float32 matmul): the product step of fp32_sqmul."""
+    return np.matmul(np.asarray(X, dtype=np.float32), np.asarray(Y, dtype=np.float32))
+
+
 def fp32_sqmul(A, n: int):
     """Square-and-multiply with float32 products (error yardstick; parity unpinned).
 
     Returns (M, e): A^n ~ M * 2**e, each product rounded to float32 by numpy's
     float32 matmul and rescaled by an exact power of two.
     """
-    A = np.asarray(A, dtype=np.float32)
+    return _sqmul_chain(A, n, lambda X, Y: _fp32_product(X, Y))
+
+
+def perturbed_sqmul(A, n: int, rel: float, seed: int):
+    """The float64 square-and-multiply chain (Sec. 4.3; numpy float64 matmul
+    as the product step) with every stored partial product disturbed
+    normwise: after the exact power-of-two rescale that puts max|X| in
+    [0.5, 1), each entry gets rel * r added, r uniform in [-1, 1) drawn from
+    numpy's default generator seeded with ``seed`` (one draw per entry, in
+    row-major order, stored product after stored product).  The result's
+    deviation from ``matpow_f64`` measures how far relative errors of size
+    rel in each stored matrix carry through the chain (its first-order
+    sensitivity), whatever arithmetic produced those errors; rel = 2^-24 is
+    the storage precision of a float32-class result.  Returns (M, e):
+    A^n ~ M 2^e."""
+    g = np.random.default_rng(seed)
+    A = np.asarray(A, dtype=np.float64)
     N = _square(A)
 
-    def norm(X, e):
+    def store(X, e):
         mx = float(np.max(np.abs(X))) if X.size else 0.0
         if mx == 0.0 or not math.isfinite(mx):
             return X, e
         _, s = math.frexp(mx)
-        return np.ldexp(X, -s).astype(np.float32), e + s
+        X = np.ldexp(X, -s)
+        return X + rel * g.uniform(-1.0, 1.0, X.shape), e + s
 
     if n == 0:
-        return np.eye(N, dtype=np.float32), 0
-    P, ep = norm(A.copy(), 0)
+        return np.eye(N), 0
+    P, ep = store(A.copy(), 0)
     R, er = None, 0
-    bits = int(n)
-    while bits:
-        if bits & 1:
-            if R is None:
-                R, er = P.copy(), ep
-            else:
-                R, er = norm(np.matmul(R, P), er + ep)
-        bits >>= 1
-        if bits:
-            P, ep = norm(np.matmul(P, P), 2 * ep)
+    for k, (mul, sq) in enumerate(schedule(n)):
+        if mul:
+            R, er = store(R @ P, er + ep)
+        elif R is None and (int(n) >> k) & 1:
+            R, er = P.copy(), ep
+        if sq:
+            P, ep = store(P @ P, 2 * ep)
     return R, er
 
 
@@ -296,6 +372,9 @@ def split_bf16(x):
     return hi, lo
 
 
+_rint = np.rint  # round half to even: the slices' rounding step
+
+
 def fixed_slices(X, block=None):
     """(a1, a2, s): X ~ 2^(s-16) (256 a1 + a2), s the frexp exponent of max|X|
     over the whole matrix (block=None) or over each block x block tile (s is
@@ -311,8 +390,8 @@ def fixed_slices(X, block=None):
                 mx = float(np.max(np.abs(X[i:i + block, j:j + block])))
                 s[i:i + block, j:j + block] = math.frexp(mx)[1] if mx > 0.0 else 0
     u = np.ldexp(X, 8 - s)
-    a1 = np.rint(u)
-    a2 = np.rint((u - a1) * 256.0)
+    a1 = _rint(u)
+    a2 = _rint((u - a1) * 256.0)
     return a1, a2, s
 
 
@@ -325,34 +404,42 @@ def fixed_slices_n(X, block, k: int):
     u = np.ldexp(np.asarray(X, dtype=np.float32).astype(np.float64), 8 - s)
     out = []
     for _ in range(k):
-        a = np.rint(u)
+        a = _rint(u)
         out.append(a)
         u = (u - a) * 256.0
     return out, s
 
 
+# Block fixed-point precisions: (slices per operand, the slice products
+# a_i b_j kept).  Slice j of a matrix with block exponent s weighs 2^(s - 8 (j+1)).
+SLICE_TERMS = {
+    "bf16x3blk": (2, ((0, 0), (0, 1), (1, 0))),
+    "bf16x6blk": (3, ((0, 0), (0, 1), (0, 2), (1, 0), (1, 1), (2, 0))),
+}
+SLICE_BITS = 8
+
+
+def _slice_weight_exp(s, j):
+    """Exponent of slice j's weight for block exponent s: s - 8 (j + 1)."""
+    return s - SLICE_BITS * (j + 1)
+
+
 def _emu_product(X, Y, precision: str) -> np.ndarray:
-    if precision == "bf16x6blk":
-        a, sx = fixed_slices_n(X, 64, 3)
-        b, sy = fixed_slices_n(Y, 64, 3)
-        x = [np.ldexp(a[j], sx - 8 * (j + 1)) for j in range(3)]
-        y = [np.ldexp(b[j], sy - 8 * (j + 1)) for j in range(3)]
+    if precision in SLICE_TERMS:
+        k, terms = SLICE_TERMS[precision]
+        a, sx = fixed_slices_n(X, 64, k)
+        b, sy = fixed_slices_n(Y, 64, k)
+        x = [np.ldexp(a[j], _slice_weight_exp(sx, j)) for j in range(k)]
+        y = [np.ldexp(b[j], _slice_weight_exp(sy, j)) for j in range(k)]
         P = np.zeros((x[0].shape[0], y[0].shape[1]))
-        for i in range(3):
-            for j in range(3 - i):
-                P += x[i] @ y[j]
+        for i, j in terms:
+            P += x[i] @ y[j]
         return P.astype(np.float32)
     if precision == "bf16x3fx":
         a1, a2, sx = fixed_slices(X)
         b1, b2, sy = fixed_slices(Y)
         T = a1 @ b1 + (a1 @ b2 + a2 @ b1) / 256.0
         return np.ldexp(T, sx + sy - 16).astype(np.float32)
-    if precision == "bf16x3blk":
-        a1, a2, sx = fixed_slices(X, 64)
-        b1, b2, sy = fixed_slices(Y, 64)
-        x1, x2 = np.ldexp(a1, sx - 8), np.ldexp(a2, sx - 16)
-        y1, y2 = np.ldexp(b1, sy - 8), np.ldexp(b2, sy - 16)
-        return (x1 @ y1 + x1 @ y2 + x2 @ y1).astype(np.float32)
     if precision == "bf16":
         P = round_bf16(X).astype(np.float64) @ round_bf16(Y).astype(np.float64)
     elif precision == "bf16x3":
@@ -371,31 +458,7 @@ def emu_sqmul(A, n: int, precision: str):
     Returns (M, e): A^n ~ M * 2**e.  The stored matrices keep float32 values,
     as the products' accumulators do; each product re-rounds its operands.
     """
-    A = np.asarray(A, dtype=np.float32)
-    N = _square(A)
-
-    def norm(X, e):
-        mx = float(np.max(np.abs(X))) if X.size else 0.0
-        if mx == 0.0 or not math.isfinite(mx):
-            return X, e
-        _, s = math.frexp(mx)
-        return np.ldexp(X, -s).astype(np.float32), e + s
-
-    if n == 0:
-        return np.eye(N, dtype=np.float32), 0
-    P, ep = norm(A.copy(), 0)
-    R, er = None, 0
-    bits = int(n)
-    while bits:
-        if bits & 1:
-            if R is None:
-                R, er = P.copy(), ep
-            else:
-                R, er = norm(_emu_product(R, P, precision), er + ep)
-        bits >>= 1
-        if bits:
-            P, ep = norm(_emu_product(P, P, precision), 2 * ep)
-    return R, er
+    return _sqmul_chain(A, n, lambda X, Y: _emu_product(X, Y, precision))
 
 
 # ---------------------------------------------------------------------------

@@ -68,6 +68,24 @@ void oracle_gemm_f64(int N, const double* A, const double* B, double* C) {
   }
 }
 
+/* Rows r0 .. r1-1 of C = A * B (row-major N x N A, B; C holds r1 - r0 rows
+ * of N): the same triple loop as oracle_gemm_f64 restricted to those rows, so
+ * each entry equals the full product's bit for bit.  A bounded sample of one
+ * large product for timing. */
+void oracle_gemm_rows_f64(int N, int r0, int r1, const double* A, const double* B, double* C) {
+  int i;
+#pragma omp parallel for schedule(static)
+  for (i = r0; i < r1; ++i) {
+    double* c = C + (size_t)(i - r0) * N;
+    for (int j = 0; j < N; ++j) c[j] = 0.0;
+    for (int k = 0; k < N; ++k) {
+      const double a = A[(size_t)i * N + k];
+      const double* b = B + (size_t)k * N;
+      for (int j = 0; j < N; ++j) c[j] = c[j] + a * b[j];
+    }
+  }
+}
+
 /* Rescale M (N x N) by a power of two so that max|M| is in [0.5, 1); add the
  * applied exponent to *e.  M = 0 is left alone. */
 static void normalise(int N, double* M, int64_t* e) {
