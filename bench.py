@@ -1,19 +1,24 @@
 """Benchmark of the integer matrix power A^n on GB300 through libmatpow.
 
-Default workload (one "step"): a single N=512 float32 matrix with entries
-N(0, 1/N), seed 0, raised to every power n in {2, 16, 128, 1024} by binary
-square-and-multiply -- G(n) = {1, 4, 7, 10} products, 22 in all.  The metric
-is effective TFLOP/s = sum over the step of G(n) * 2 N^3 / time (the
-algorithmic count: the three (bf16x3) or six (bf16x6) bfloat16 products of
-the split paths and the n-1 products of the naive method are not counted).
-The default precision is the three-slice exact split (bf16x6), the cheapest
-tensor-core path whose errors stay within 2e-5 * ceil(log2 n) on these
-inputs; the line also carries the plain FP32 SIMT path timed on the same
-workload.
+Default workload (one "step"): a single N=8192 float32 exactly row-stochastic
+matrix (rows U[0,1) normalised so that every float32 row sums to 1 exactly),
+seed 0, raised to n = 2^20 by binary square-and-multiply: 20 squarings,
+G(n) = 20 products of 2 N^3.  The metric is effective TFLOP/s = G(n) 2 N^3 /
+time (the algorithmic count: the three bfloat16 products of the BF16X3 split
+and the n-1 products of the naive method are not counted).  The default
+precision there is the two-slice exact split (BF16X3), the cheapest
+tensor-core path whose error stays within 2e-5 ceil(log2 n) on these inputs;
+the error is measured against the closed form 1 pi^T (pi by float64 power
+iteration) on 64 sampled rows, beside the largest row-sum deviation.  The
+line also carries the plain FP32 SIMT and plain BF16 paths timed on the same
+workload, and the N=512 Gaussian workload (n in {2,16,128,1024}) on every
+float path with its errors per n.
 
-The four powers go through one matpow_batched call (`--api batched`, the
-default), which runs them side by side in one cooperative whole-chain launch;
-`--api single` issues one matpow_f32 call per power.
+Other workloads (``--workload``): the N=512 Gaussian powers alone
+(``single512``), the 4096-matrix batch, the request server, A^n mod p,
+e^A, the naive-method comparison and the N=64 on-chip chain.  ``--api
+single`` issues one matpow_f32 call per power for multi-power workloads
+(default: one matpow_batched call).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -43,17 +48,16 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB of L2
 # kernel changes.
 TRAFFIC = {
     ("single512", "bf16x6"): (1.18e6, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
-                                      "tc_chain_split_kernel<64, 3, 2>, one launch per step "
-                                      "(profiles/tc_chain_kernel_single512.md)"),
-    ("batched4096", "bf16x6"): (9.63e8, "ncu one-pass DRAM counters of tc_fxb_persist_kernel<3>, average over "
-                                        "the 12 level launches of one step "
-                                        "(profiles/tc_fxb_persist_kernel_batched512.md)"),
-    ("modp2048", "bf16x3"): (2.70e7, "ncu one-pass DRAM counters of tc_modp_kernel, average over the 14 "
-                                     "launches of one step (profiles/tc_modp_kernel_modp2048.md)"),
-    ("stoch64", "fp32"): (5.66e4, "ncu dram__bytes_read.sum + dram__bytes_write.sum of tiny_cluster_kernel, "
-                             "one launch (profiles/tiny_cluster_kernel_stoch64.md)"),
+                                      "tc_chain_split_kernel<64, 3, 2>, one launch per step"),
+    ("batched4096", "bf16x6"): (9.63e8, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
+                                        "tc_fxb_persist_kernel<3>, average over the 12 level launches "
+                                        "of one step"),
+    ("modp2048", "bf16x3"): (2.70e7, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
+                                     "tc_modp_kernel, average over the 14 launches of one step"),
+    ("stoch64", "fp32"): (5.66e4, "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                  "tiny_cluster_kernel, one launch"),
     ("large8192", "bf16x3"): (3.04e9, "ncu one-pass dram__bytes_read.sum + dram__bytes_write.sum of "
-                                      "tc_fxb_kernel<128, 2> at full size (profiles/tc_fxb_kernel_large8192.md)"),
+                                      "tc_fxb_kernel<128, 2>, one product at full size"),
 }
 
 # bfloat16 tensor-core products per algorithmic product (roofline counting)
@@ -203,19 +207,37 @@ def make_input(wk):
 
 # ---------------------------------------------------------------------------- oracle timing
 
-def cpu_sample(wk, budget_s: float = 15.0, threads: int = 0):
+def cpu_sample(wk, budget_s: float = 15.0, threads: int = 0, A=None):
     """Time the CPU oracle on a bounded sample of the workload (effective TFLOP/s).
 
     The sample is the workload's list of powers, repeated until about
-    ``budget_s`` seconds of oracle time; for large N (where one power takes
-    far longer) it is a single product (n = 2) of the same matrix.
+    ``budget_s`` seconds of oracle time.  Where one power takes far longer
+    (large N), it is the leading rows of the power's first product A A, by
+    the oracle's triple loop, taken in chunks until about ``budget_s``
+    seconds (2 N^2 flop per row).
     """
     import oracle
-    A = make_input(wk)
+    if A is None:
+        A = make_input(wk)
     N = wk["N"]
     cores = oracle.set_threads(threads)
     per_power_est = max(gemm_count(n) for n in wk["ns"]) * 2.0 * N ** 3 / (1.5e9 * cores)
-    ns = sorted(wk["ns"]) if per_power_est < budget_s else [2]
+    if per_power_est >= budget_s:
+        A64 = np.ascontiguousarray(A, dtype=np.float64)
+        chunk = max(cores, 8)
+        rows, t_total = 0, 0.0
+        while rows < N and t_total < budget_s:
+            r1 = min(N, rows + chunk)
+            t0 = time.perf_counter()
+            oracle.gemm_rows_f64(A64, A64, rows, r1)
+            t_total += time.perf_counter() - t0
+            rows = r1
+        return {"value": rows * 2.0 * N * N / t_total / 1e12, "unit": "TFLOP/s", "cores": cores,
+                "kind": "oracle",
+                "sample": "float64 triple loop, rows 0..%d of the first product A A of the N=%d power "
+                          "(%.1f s; one whole power is %d such products)" % (
+                              rows - 1, N, t_total, max(gemm_count(n) for n in wk["ns"]))}
+    ns = sorted(wk["ns"])
     done_flop, t_total, reps = 0.0, 0.0, 0
     while True:
         for n in ns:
@@ -351,6 +373,7 @@ def run_reference(args, wk, world, rank):
         return
     res = []
     cb = None
+    A_ref = None
     serving = wk.get("kind") == "serving"
     for _ in range(max(args.steps, 1)):
         if wk.get("kind") in ("batched", "serving"):
@@ -362,7 +385,9 @@ def run_reference(args, wk, world, rank):
         elif wk.get("kind") == "naive":
             cb = cpu_sample(dict(wk, ns=wk["ns_list"]), budget_s=args.ref_budget)
         else:
-            cb = cpu_sample(wk, budget_s=args.ref_budget)
+            if A_ref is None:
+                A_ref = make_input(wk)
+            cb = cpu_sample(wk, budget_s=args.ref_budget, A=A_ref)
         res.append(cb["items_per_s"] if serving else cb["value"])
     value = statistics.median(res)
     cb["value"] = value
@@ -415,13 +440,14 @@ def errors_of(wk, A_host, ns, outs, lgs):
     return errs
 
 
-def fp32_compare(args, wk, A, A_host, flush, stream, value):
-    """Time the plain FP32 SIMT path on the same workload (same L2 flush and
-    event timing, fewer steps) and report its value, errors and the ratio."""
+def path_compare(args, wk, A, A_host, flush, stream, value, prec="fp32"):
+    """Time another precision's path (plain FP32 SIMT by default, the metric's
+    comparator) on the same workload, with the same L2 flush and event
+    timing and fewer steps; report its value, errors and the ratio."""
     import torch
     from paper_1204_3052_gb300 import matpow as mpw
     N, ns = wk["N"], wk["ns"]
-    plan = mpw.Plan(N, "fp32", device=A.device.index)
+    plan = mpw.Plan(N, prec, device=A.device.index)
     outs = [torch.empty_like(A) for _ in ns]
     lgs = torch.zeros(len(ns), dtype=torch.int64, device=A.device)
     steps = max(1, min(args.steps, 3 if N > 2048 else 10))
@@ -451,8 +477,71 @@ def fp32_compare(args, wk, A, A_host, flush, stream, value):
     v = steps * flop_step / (ms * 1e-3) / 1e12
     errs = {} if args.no_check else errors_of(wk, A_host, ns, outs, lgs)
     plan.close()
-    return {"value": v, "unit": "TFLOP/s", "steps": steps, "rel_frobenius_vs_f64": errs,
-            "ratio_this_path_over_fp32": value / v if v else None}
+    return {"precision": prec, "value": v, "unit": "TFLOP/s", "steps": steps, "rel_frobenius_vs_f64": errs,
+            "ratio_this_path_over_it": value / v if v else None}
+
+
+def config2_table(args, dev, flush, stream):
+    """The N = 512 Gaussian workload (powers 2, 16, 128, 1024) on every float
+    path -- plain FP32 SIMT, plain BF16, BF16X3 and BF16X6 -- per step one
+    matpow_batched call over the four powers (the exact splits and FP32; plain
+    BF16 has no grouped launch and takes one matpow_f32 call per power), CUDA
+    events, L2 flushed; each power's error against the float64 oracle and
+    whether it met 2e-5 ceil(log2 n)."""
+    import torch
+    import oracle
+    from paper_1204_3052_gb300 import matpow as mpw
+    wk = WORKLOADS["single512"]
+    N, ns = wk["N"], wk["ns"]
+    A_host = make_input(wk)
+    A = torch.from_numpy(A_host).to(dev)
+    ref = {} if args.no_check else {n: oracle.matpow_f64(A_host, n)[:2] for n in ns}
+    flop_step = sum(gemm_count(n) for n in ns) * 2.0 * N ** 3
+    out_all = torch.empty((len(ns), N, N), dtype=torch.float32, device=dev)
+    outs = [out_all[i] for i in range(len(ns))]
+    lgs = torch.zeros(len(ns), dtype=torch.int64, device=dev)
+    table = {}
+    for prec in ("fp32", "bf16", "bf16x3", "bf16x6"):
+        plan = mpw.Plan(N, prec, device=dev.index)
+        steps = max(3, min(args.steps, 20))
+
+        def step():
+            if prec == "bf16":
+                for i, n in enumerate(ns):
+                    mpw._check(mpw.matpow_f32(plan.h, A, N, n, outs[i], lgs[i:i + 1], stream), plan.h)
+            else:
+                mpw._check(mpw.matpow_batched(plan.h, [A] * len(ns), [N] * len(ns), ns, outs, lgs, stream),
+                           plan.h)
+
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                step()
+            plan.check(stream)
+            ms = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+            plan.check(stream)
+        row = {"value": steps * flop_step / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "us_per_step": ms * 1e3 / steps}
+        if ref:
+            errs = {}
+            for i, n in enumerate(ns):
+                M, e = ref[n]
+                errs[str(n)] = oracle.rel_frobenius(outs[i].cpu().numpy().astype(np.float64),
+                                                    int(lgs[i].item()), M, e)
+            row["rel_frobenius_vs_f64"] = errs
+            row["within_2e-5_ceil_log2_n"] = all(errs[str(n)] <= stated_tolerance(n) for n in ns)
+        table[prec] = row
+        plan.close()
+    return {"workload": wk["desc"], "api": "one matpow_batched call over the 4 powers",
+            "l2": "flushed between timed steps (256 MB write)", "paths": table}
 
 
 def run_ours(args, wk, world, rank, local):
@@ -521,10 +610,15 @@ def run_ours(args, wk, world, rank, local):
 
     # ---- accuracy of this run against the oracle (reported, not timed)
     errs = errors_of(wk, A_host, ns, outs, lgs) if rank == 0 and not args.no_check else {}
-    # ---- the plain FP32 SIMT path on the same workload (the comparator of the metric)
-    fp32 = None
+    # ---- the plain FP32 SIMT path on the same workload (the comparator of the
+    # metric) and, for the large power, the plain BF16 path
+    fp32 = bf16 = table2 = None
     if world == 1 and prec != "fp32" and not args.no_fp32:
-        fp32 = fp32_compare(args, wk, A, A_host, flush, stream, value)
+        fp32 = path_compare(args, wk, A, A_host, flush, stream, value, "fp32")
+        if N > 1024 and prec != "bf16":
+            bf16 = path_compare(args, wk, A, A_host, flush, stream, value, "bf16")
+    if world == 1 and N > 1024 and not args.no_config2:
+        table2 = config2_table(args, dev, flush, stream)
 
     # ---- end to end through the C-ABI with host buffers
     A_pin = torch.from_numpy(A_host).pin_memory()
@@ -577,6 +671,8 @@ def run_ours(args, wk, world, rank, local):
                 "frac": achieved / peak, "traffic": None,
                 "kernel": kname, "peak_source": peak_src + " bf16 burst",
                 "counted": "%d bfloat16 product(s) per term" % int(products)}
+        if peaks.get("bf16_tflops_sustained"):
+            roof["frac_of_sustained"] = achieved / peaks["bf16_tflops_sustained"]
     else:
         # float32 FFMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
         smax = peaks.get("sm_max_mhz", 2070.0)
@@ -617,7 +713,7 @@ def run_ours(args, wk, world, rank, local):
 
     if rank != 0:
         return
-    cb = cpu_sample(wk, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
+    cb = cpu_sample(wk, budget_s=args.cpu_budget, A=A_host) if world == 1 and not args.no_cpu else None
     line = {
         "metric": "matpow effective TFLOP/s", "value": value, "unit": "TFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -637,6 +733,10 @@ def run_ours(args, wk, world, rank, local):
         "roofline": roof,
         "cpu_baseline": cb,
     }
+    if bf16:
+        line["bf16_same_workload"] = bf16
+    if table2:
+        line["n512_gaussian_all_paths"] = table2
     if latency:
         line["latency"] = latency
     print(json.dumps(line))
@@ -1284,13 +1384,15 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="single512")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large8192")
     ap.add_argument("--precision", choices=sorted(DTYPE), default=None,
                     help="default: the cheapest path that meets the stated error on the workload "
                          "(bf16x6 for Gaussian inputs, bf16x3 for stochastic ones)")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 SIMT comparator")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the FP32 SIMT (and plain BF16) comparators")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="large workloads: skip the N=512 table of every float path")
     ap.add_argument("--api", choices=["batched", "single"], default="batched",
                     help="single-matrix workloads: all powers in one matpow_batched call (default) or "
                          "one matpow_f32 call per power")

@@ -143,6 +143,56 @@ enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MA
        MATPOW_OPT_NAIVE = 9 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
+/* ---- tile table (launch shapes per size class) ------------------------------ */
+
+/*
+ * The paper keeps a family of product kernels with tile shapes from 4 x 4 to
+ * 16 x 16 and picks one by the problem size and the local memory available
+ * (Sec. 4.3.7).  Here a plan may carry a tile table: rules, each for one
+ * precision and one range of orders, that fix the launch shape of the
+ * products; an autotuner (paper_1204_3052_gb300/autotune.py) measures the
+ * candidates on the device and writes the winners as JSON.  Orders that no
+ * rule covers keep the built-in choice, as does any field set to -1.
+ * Explicit plan options win over the table: MATPOW_OPT_TILE over `bn`,
+ * MATPOW_OPT_CHAIN 0 or 2 over `chain` and `split_k`, MATPOW_OPT_PERSIST 0
+ * over `persist`.
+ */
+typedef struct matpow_tile_rule {
+  int n_lo, n_hi; /* the rule covers orders N with n_lo < N <= n_hi */
+  int precision;  /* matpow_precision the rule is for */
+  int bn;         /* exact-split tile width, columns of C per CTA: 64 or 128 */
+  int split_k;    /* whole-chain launches: CTAs of a cluster sharing one tile's k range: 1, 2, 4 */
+  int chain;      /* single powers (and up to four side by side) with N <= 1024: 1 the
+                     whole chain in one cooperative launch, 0 one launch per level */
+  int persist;    /* matpow_batched levels of 64-column tiles: 1 one persistent CTA per SM
+                     over the tile list, 0 one CTA per tile */
+} matpow_tile_rule;
+
+/* Replace the plan's tile table by `count` rules (copied; count = 0 clears
+ * it).  MATPOW_EINVAL for a rule with n_lo >= n_hi, an unknown precision or
+ * a field outside its values (bn: 64 or 128; split_k: 1, 2 or 4; chain,
+ * persist: 0 or 1; -1 everywhere for "built-in"). */
+matpow_status matpow_plan_set_tile_table(matpow_plan_t plan, const matpow_tile_rule* rules, int count);
+
+/* Read a tile table from the JSON file at `path` (host path) into the plan:
+ * {"rules": [{"precision": "bf16x6", "n_lo": 64, "n_hi": 128, "bn": 64,
+ * "split_k": 2, "chain": 1, "persist": 1, ...}, ...]}; precision is one of
+ * "fp32", "bf16", "bf16x3", "bf16x6"; omitted fields are -1; other keys are
+ * ignored.  MATPOW_EINVAL (with the position in the message) for text that
+ * does not parse or a rule that matpow_plan_set_tile_table rejects. */
+matpow_status matpow_plan_load_tile_table(matpow_plan_t plan, const char* path);
+
+/* Parse tile-table JSON text (NUL-terminated) into at most `cap` rules;
+ * *count receives the number of rules in the text (may exceed cap).  Host
+ * only, needs no device. */
+matpow_status matpow_tile_table_parse(const char* json, matpow_tile_rule* rules, int cap, int* count);
+
+/* The rule a table gives for (precision, N): the last rule in table order
+ * that covers it, copied to *out; MATPOW_EAGAIN if none covers it (then
+ * *out is all -1 but n_lo, n_hi, precision).  Host only. */
+matpow_status matpow_tile_rule_lookup(const matpow_tile_rule* rules, int count, matpow_precision precision,
+                                      int N, matpow_tile_rule* out);
+
 /* ---- the power ------------------------------------------------------------ */
 
 /*
@@ -180,7 +230,10 @@ matpow_status matpow_f32(matpow_plan_t plan, const float* dA, int N, uint64_t n,
  *               thread's current device; 0 <= N <= 512, larger N fails with
  *               MATPOW_EINVAL (and a message naming the limit).
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it with the device's current context; a
+ * call in a new context of that device (after cudaDeviceReset, say) looks
+ * it up again.  Make the first call in each context before any stream
+ * capture.
  * Every call uses the same scratch, so calls whose work overlaps on the GPU
  * (different streams, or threads without ordering) race and corrupt each
  * other: order them on one stream.  Device-side conditions that matpow_sync

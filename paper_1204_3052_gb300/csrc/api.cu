@@ -203,6 +203,8 @@ static void drop_graphs(matpow_plan_s* p) {
   p->graphs.clear();
 }
 
+void mp::drop_plan_graphs(matpow_plan_s* p) { drop_graphs(p); }
+
 extern "C" matpow_status matpow_plan_destroy(matpow_plan_t p) {
   if (!p) return MATPOW_OK;
   int prev = 0;

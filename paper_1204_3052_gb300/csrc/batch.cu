@@ -226,25 +226,38 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
       }
   }
   // ---- product descriptors per level; tensor-core levels get one launch per
-  // tile width (64 columns for N <= 1024, 128 above)
+  // kernel variant: 64-column tiles in the persistent kernel, 64-column tiles
+  // one CTA each, 128-column tiles (built in: 64 columns for N <= 1024 or
+  // three slices, 128 above; persistent where the plan allows it; the tile
+  // table may choose per order range)
   struct Launch {
     int begin, count, tiles, bn, max_n, td;  // td: offset of the tile -> product table
+    bool persist;
+  };
+  auto variant_of = [&](int Ni) -> int {
+    int bn = tc_group_bn(Ni, nsl);
+    const int tb = plan_tile_field(p, Ni, &matpow_tile_rule::bn);
+    if (tb == 64 || (tb == 128 && nsl == 2)) bn = tb;
+    if (bn == 128) return 2;
+    bool per = p->persist;
+    const int tp = plan_tile_field(p, Ni, &matpow_tile_rule::persist);
+    if (p->persist && tp >= 0) per = tp == 1;
+    return per ? 0 : 1;
   };
   int max_levels = 0;
   for (auto& b : big) max_levels = std::max(max_levels, (int)b.levels.size());
   std::vector<GemmDesc> gd;
   std::vector<std::vector<Launch>> lvl_launches(max_levels);
   std::vector<int4> trec;  // persistent-kernel tile records of every launch
-  const int passes[2] = {64, 128};
   for (int L = 0; L < max_levels; ++L) {
-    for (int pi = 0; pi < (tc ? 2 : 1); ++pi) {
-      const int bn = tc ? passes[pi] : 0;
+    for (int pi = 0; pi < (tc ? 3 : 1); ++pi) {
+      const int bn = tc ? (pi == 2 ? 128 : 64) : 0;
       int begin = (int)gd.size(), tiles = 0, max_n = 0;
       for (size_t bi = 0; bi < big.size(); ++bi) {
         const Big& b = big[bi];
         if (L >= (int)b.levels.size()) continue;
         const int Ni = N[b.i];
-        if (tc && tc_group_bn(Ni, nsl) != bn) continue;
+        if (tc && variant_of(Ni) != pi) continue;
         max_n = std::max(max_n, Ni);
         const bool final_level = L + 1 == (int)b.levels.size();
         const LevelOps& lv = b.levels[L];
@@ -283,7 +296,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
       if ((int)gd.size() > begin) {
         const int td = (int)trec.size();
         if (tc && bn == 64) persist_tile_records(gd.data() + begin, (int)gd.size() - begin, nsl, &trec);
-        lvl_launches[L].push_back({begin, (int)gd.size() - begin, tiles, bn, max_n, td});
+        lvl_launches[L].push_back({begin, (int)gd.size() - begin, tiles, bn, max_n, td, pi == 0});
       }
     }
   }
@@ -372,7 +385,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
       timed_begin(p, s, &ev);
       if (tc) {
         if ((st = tc_launch_group_bn(p, g, la.count, la.tiles, (const int4*)(dd + o_td) + la.td,
-                                     p->batch.maps, la.bn, la.max_n, p->batch.scales,
+                                     p->batch.maps, la.bn, la.max_n, la.persist, p->batch.scales,
                                      p->status, s)))
           return st;
         timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);

@@ -44,12 +44,14 @@ __global__ void expm_colsum_kernel(const float* __restrict__ A, int N, double* c
   atomicAdd(&colsum[j], s);
 }
 
-// ||A||_1 = the largest column sum, as float bits; a non-finite entry makes a
-// sum NaN or inf, whose bits (0x7fffffff for NaN) exceed every finite value's.
+// ||A||_1 = the largest column sum, as float bits rounded upward from the
+// float64 sum (so the float never falls below the true norm and the chosen s
+// keeps ||A 2^-s||_1 <= 1); a non-finite entry makes a sum NaN or inf, whose
+// bits (0x7fffffff for NaN) exceed every finite value's.
 __global__ void expm_colmax_kernel(const double* __restrict__ colsum, int N, unsigned* out) {
   unsigned m = 0;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const float f = (float)colsum[j];
+    const float f = __double2float_ru(colsum[j]);
     m = max(m, isnan(f) ? 0x7fffffffu : __float_as_uint(f));
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));

@@ -690,7 +690,12 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
     maxN = std::max(maxN, N);
     minKB = std::min(minKB, (N + chain::BK - 1) / chain::BK);
   }
-  const int BN = maxN <= 768 ? 64 : 128;
+  // the tile table (chain_mode 1 only: modes 0 and 2 are explicit choices):
+  // the whole chain or the level path, its tile width and split-K
+  const matpow_tile_rule* rule = p->chain_mode == 1 ? plan_tile_rule(p, maxN) : nullptr;
+  if (rule && rule->chain == 0) return MATPOW_OK;
+  int BN = maxN <= 768 ? 64 : 128;
+  if (rule && (rule->bn == 64 || (rule->bn == 128 && nsl == 2))) BN = rule->bn;
   if (BN == 128 && nj > 1) return MATPOW_OK;  // one tile width per launch
   static thread_local ChainParams P;  // ~20 KB: kept off the stack
   memset(&P, 0, sizeof P);
@@ -720,12 +725,13 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
   // the smallest multiple of S covering S x (the largest level), capped by
   // the SMs; at least one level must be able to split, or S = 1.
   int S = 1, G = G1;
-  if (p->chain_mode == 1 && BN == 64) {
+  const int want_s = rule ? rule->split_k : -1;  // -1: the largest that fits
+  if (p->chain_mode == 1 && BN == 64 && want_s != 1) {
     int minT = 1 << 30;
     for (int L = 0; L < nlevels; ++L) minT = std::min(minT, (int)P.lvl_begin[L][nj]);
     const int smax = nsl == 3 ? 2 : 4;
     for (int c = smax; c >= 2; c /= 2) {
-      if (c > minKB) continue;
+      if (c > minKB || (want_s > 1 && c != want_s)) continue;
       const int g = std::min(c * G1, p->num_sms / c * c);
       if (g < G1 || 2 * minT > g) continue;  // no level could split
       const int mc = nsl == 3 ? chain_max_clusters<64, 3, 2>()

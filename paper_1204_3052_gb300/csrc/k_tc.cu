@@ -597,6 +597,8 @@ static int pick_bn(matpow_plan_s* p, int N) {
     if (fx2 && p->tile_override == 256) return 128;
     return p->tile_override;
   }
+  const int tb = plan_tile_field(p, N, &matpow_tile_rule::bn);  // the tile table's width
+  if (tb == 64 || tb == 128) return tb;
   return tc_group_bn(N) == 64 ? 64 : (N <= 3072 || fx2) ? 128 : 256;
 }
 
@@ -701,12 +703,12 @@ cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, cons
 
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                                  const int4* d_tile_rec, const void* d_maps, int bn, int max_n,
-                                 Scale* scales, unsigned* status, cudaStream_t s) {
+                                 bool persist, Scale* scales, unsigned* status, cudaStream_t s) {
   const int fmt = plan_float_fmt(p);
   if (!fmt_exact(fmt))
     return fail(p, MATPOW_EUNSUPPORTED, "grouped tensor-core launches need the exact split");
   cudaError_t e = launch_fxb_group(d_descs, count, tiles, d_tile_rec, d_maps, bn, fmt_slices(fmt), max_n,
-                                   p->num_sms, p->persist, scales, status, s);
+                                   p->num_sms, persist, scales, status, s);
   if (e != cudaSuccess) return cuda_fail(p, e, "tc_fxb_group_kernel launch");
   return MATPOW_OK;
 }

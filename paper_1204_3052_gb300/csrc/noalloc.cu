@@ -5,6 +5,7 @@
 // Scratch layout (one copy per GPU that loads the library, held until the
 // process exits): four float32 partial-product buffers of 512 x 512, the
 // scale slots {maxbits, exponent} of one power, and a status word.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -26,22 +27,54 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
-unsigned char* g_dev_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up once).
+// The scratch address is looked up once per device and kept with the CUDA
+// context it belongs to: a context that is destroyed and re-created (after
+// cudaDeviceReset, say) reloads the module, so the lookup is repeated then.
+struct DevScratch {
+  CUcontext ctx;
+  unsigned char* ptr;
+};
+DevScratch g_dev_scratch[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+std::once_flag g_ctx_fn_once;
+
+// The calling thread's current context, or null when it cannot be read.
+CUcontext current_context() {
+  std::call_once(g_ctx_fn_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_ctx_get_current = (CtxGetCurrentFn)fn;
+  });
+  CUcontext c = nullptr;
+  if (!g_ctx_get_current || g_ctx_get_current(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+// Device address of the scratch array on the current device: set up on the
+// first call in each context of the device (cudaGetSymbolAddress with that
+// device current), reused afterwards.
 cudaError_t scratch_for_current_device(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_dev_scratch[dev]) {
+  DevScratch& d = g_dev_scratch[dev];
+  const CUcontext ctx = current_context();
+  if (!d.ptr || !ctx || ctx != d.ctx) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_scratch);
     if (e != cudaSuccess) return e;
-    g_dev_scratch[dev] = (unsigned char*)ptr;
+    d.ptr = (unsigned char*)ptr;
+    d.ctx = current_context();  // the lookup initialises the context if it was not yet
   }
-  *out = g_dev_scratch[dev];
+  *out = d.ptr;
   return cudaSuccess;
 }
 

@@ -117,10 +117,19 @@ struct matpow_plan_s {
   mp::BatchState batch;
   // tensor-core path state (tensor maps etc.), owned by k_tc.cu
   void* tc = nullptr;
+  // tile table: launch shapes per order range (matpow_plan_set_tile_table)
+  std::vector<matpow_tile_rule> tiles;
 };
 
 namespace mp {
 matpow_status fail(matpow_plan_s* plan, matpow_status st, const char* fmt, ...);
+// The tile-table rule that covers order N for the plan's precision (the
+// last one in table order), or null; plan_tile_field gives one field of it
+// (-1 when no rule covers N or the rule leaves the field to the built-in).
+const matpow_tile_rule* plan_tile_rule(const matpow_plan_s* p, int N);
+int plan_tile_field(const matpow_plan_s* p, int N, int matpow_tile_rule::*field);
+// Destroy the plan's cached single-call CUDA graphs.
+void drop_plan_graphs(matpow_plan_s* p);
 matpow_status cuda_fail(matpow_plan_s* plan, cudaError_t e, const char* what);
 size_t matrix_bytes(int N, int fmt);
 long long plane_offset_elems(int N, int fmt);
@@ -182,8 +191,8 @@ cudaError_t launch_modp_tc_group(const GemmDesc* d_descs, int count, int tiles, 
 // among the products).
 matpow_status tc_launch_group_bn(matpow_plan_s* p, const GemmDesc* d_descs, int count, int tiles,
                                  const int4* d_tile_rec, const void* d_maps, int bn, int max_n,
-                                 Scale* scales, unsigned* status, cudaStream_t s);
-int tc_group_bn(int N, int nsl = 2);  // tile width of grouped launches for order N
+                                 bool persist, Scale* scales, unsigned* status, cudaStream_t s);
+int tc_group_bn(int N, int nsl = 2);  // built-in tile width of grouped launches for order N
 // Plan-free grouped exact-split launch (descriptor and TMA tables on the
 // device): the persistent kernel (one CTA per SM over the whole tile list;
 // d_tile_desc[t] = index of the product owning tile t | its k-blocks << 24)

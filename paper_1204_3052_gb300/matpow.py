@@ -39,7 +39,14 @@ EXPORTS = [
     "matpow_gemm_count", "matpow_kernel_time", "matpow_launch_count", "matpow_server_create",
     "matpow_submit", "matpow_poll", "matpow_server_latencies", "matpow_server_destroy",
     "matpow_f32_noalloc", "matpow_selftest_wait_timeout", "matpow_expm",
+    "matpow_plan_set_tile_table", "matpow_plan_load_tile_table", "matpow_tile_table_parse",
+    "matpow_tile_rule_lookup",
 ]
+
+# The tile table tuned on a GB300 (written by autotune.py); plans load it when
+# asked (Plan(tile_table=DEFAULT_TILE_TABLE)).
+DEFAULT_TILE_TABLE = os.path.join(_HERE, "tile_table_gb300.json")
+TILE_FIELDS = ("n_lo", "n_hi", "precision", "bn", "split_k", "chain", "persist")
 
 
 class MatpowError(RuntimeError):
@@ -53,6 +60,13 @@ class ServerDesc(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_n", ctypes.c_int), ("precision", ctypes.c_int),
                 ("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int),
                 ("max_queue", ctypes.c_int)]
+
+
+class TileRule(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in TILE_FIELDS]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f in TILE_FIELDS}
 
 
 class Request(ctypes.Structure):
@@ -103,6 +117,12 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "matpow_f32_noalloc": (i32, [vp, i32, u64, vp, vp, vp]),
             "matpow_selftest_wait_timeout": (i32, [vp, u64, vp]),
             "matpow_expm": (i32, [vp, vp, i32, vp, vp, vp]),
+            "matpow_plan_set_tile_table": (i32, [vp, ctypes.POINTER(TileRule), i32]),
+            "matpow_plan_load_tile_table": (i32, [vp, ctypes.c_char_p]),
+            "matpow_tile_table_parse": (i32, [ctypes.c_char_p, ctypes.POINTER(TileRule), i32,
+                                              ctypes.POINTER(i32)]),
+            "matpow_tile_rule_lookup": (i32, [ctypes.POINTER(TileRule), i32, i32, i32,
+                                              ctypes.POINTER(TileRule)]),
         }
         for name, (res, args) in protos.items():
             fn = getattr(lib, name)
@@ -198,6 +218,48 @@ def matpow_selftest_wait_timeout(plan: int, budget_ns: int, stream=None) -> int:
     return load().matpow_selftest_wait_timeout(plan, int(budget_ns), _stream(stream))
 
 
+def _rules_array(rules):
+    arr = (TileRule * max(len(rules), 1))()
+    for i, r in enumerate(rules):
+        d = dict(r)
+        if isinstance(d.get("precision"), str):
+            d["precision"] = PRECISIONS[d["precision"]]
+        for f in TILE_FIELDS:
+            setattr(arr[i], f, int(d.get(f, -1)))
+    return arr
+
+
+def matpow_plan_set_tile_table(plan: int, rules) -> int:
+    """rules: a list of dicts with the fields of matpow_tile_rule (precision may be a name)."""
+    return load().matpow_plan_set_tile_table(plan, _rules_array(rules), len(rules))
+
+
+def matpow_plan_load_tile_table(plan: int, path: str) -> int:
+    return load().matpow_plan_load_tile_table(plan, os.fsencode(path))
+
+
+def matpow_tile_table_parse(text: str):
+    """(status, [rule dicts]) of tile-table JSON text, parsed by the library."""
+    lib = load()
+    n = ctypes.c_int()
+    st = lib.matpow_tile_table_parse(text.encode(), None, 0, ctypes.byref(n))
+    if st != OK:
+        return st, []
+    arr = (TileRule * max(n.value, 1))()
+    st = lib.matpow_tile_table_parse(text.encode(), arr, n.value, ctypes.byref(n))
+    return st, [arr[i].as_dict() for i in range(n.value)]
+
+
+def matpow_tile_rule_lookup(rules, precision, N: int):
+    """(status, rule dict) the library selects from `rules` for (precision, N)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    out = TileRule()
+    st = load().matpow_tile_rule_lookup(_rules_array(rules), len(rules), int(precision), int(N),
+                                        ctypes.byref(out))
+    return st, out.as_dict()
+
+
 def matpow_gemm_count(n: int) -> int:
     return int(load().matpow_gemm_count(int(n)))
 
@@ -253,11 +315,21 @@ def matpow_server_destroy(server: int) -> None:
 class Plan:
     """Owns one libmatpow plan; tensors are torch CUDA tensors."""
 
-    def __init__(self, max_n: int, precision="fp32", device: int = 0, workspace_bytes: int = 0):
+    def __init__(self, max_n: int, precision="fp32", device: int = 0, workspace_bytes: int = 0,
+                 tile_table: Optional[str] = None):
         self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.device = device
         self.max_n = max_n
         self.h = matpow_plan(max_n, self.precision, workspace_bytes, device)
+        if tile_table:
+            self.load_tile_table(tile_table)
+
+    def load_tile_table(self, path: str):
+        """Launch shapes per order range from a tile-table JSON file."""
+        _check(matpow_plan_load_tile_table(self.h, path), self.h)
+
+    def set_tile_table(self, rules):
+        _check(matpow_plan_set_tile_table(self.h, rules), self.h)
 
     def close(self):
         if self.h:

@@ -5,22 +5,10 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import gate, to_dev
+from helpers import check_float, to_dev
 from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
-
-EMU = {"bf16x3": "bf16x3blk", "bf16x6": "bf16x6blk"}
-
-
-def floor_for(prec, A, n, M, e):
-    Mf, ef = oracle.fp32_sqmul(A, n)
-    f = oracle.rel_frobenius(Mf, ef, M, e)
-    if prec in EMU and A.shape[0] > 64:
-        Me, ee = oracle.emu_sqmul(A, n, EMU[prec])
-        f = max(f, oracle.rel_frobenius(Me, ee, M, e))
-    return f
-
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16x6"])
 def test_uneven_batch_matches_oracle_and_single_calls(prec):
@@ -40,7 +28,7 @@ def test_uneven_batch_matches_oracle_and_single_calls(prec):
     for i, (A, n) in enumerate(zip(As, ns)):
         M, e, _ = oracle.matpow_f64(A, n)
         err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lgs[i]), M, e)
-        assert err <= gate(n, floor_for(prec, A, n, M, e)), (i, A.shape[0], n, err)
+        check_float(err, prec, n, A, M, e, what="batch")
         alone, alone_lg = plan.f32(dAs[i], n, mantissa=True)
         plan.check()
         assert torch.equal(alone, outs[i]) and int(alone_lg.item()) == int(lgs[i]), (i, A.shape[0], n)
@@ -74,7 +62,7 @@ def test_batch_with_wide_tiles(prec):
         if Ns[i] <= 300:
             M, e, _ = oracle.matpow_f64(A, n)
             err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
-            assert err <= gate(n, floor_for(prec, A, n, M, e))
+            check_float(err, prec, n, A, M, e, what="batch")
     plan.close()
 
 
@@ -106,7 +94,7 @@ def test_persistent_levels_equal_per_tile_levels(prec):
     for i in range(0, len(As), 97):
         M, e, _ = oracle.matpow_f64(As[i], ns[i])
         err = oracle.rel_frobenius(res[1][0][i].cpu().numpy(), int(res[1][1][i].item()), M, e)
-        assert err <= gate(ns[i], floor_for(prec, As[i], ns[i], M, e)), (i, Ns[i], ns[i], err)
+        check_float(err, prec, ns[i], As[i], M, e, what="batch")
 
 
 def test_batched_graph_replay_follows_new_contents():
@@ -165,7 +153,7 @@ def test_few_powers_run_side_by_side_in_one_chain(prec):
             if n <= 4096:
                 M, e, _ = oracle.matpow_f64(A, n)
                 err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lg[i].item()), M, e)
-                assert err <= gate(n, floor_for(prec, A, n, M, e)), (mode, Ns[i], n, err)
+                check_float(err, prec, n, A, M, e, what="batch")
         plan.close()
 
 
@@ -192,5 +180,5 @@ def test_tiny_single_forms_match_group_kernel_bitwise(N):
             if n <= 100:
                 M, e, _ = oracle.matpow_f64(A, n)
                 err = oracle.rel_frobenius(alone.cpu().numpy(), int(alone_lg.item()), M, e)
-                assert err <= gate(n, floor_for("fp32", A, n, M, e)), (N, n, err)
+                check_float(err, "fp32", n, A, M, e, what="batch")
     plan.close()

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import gate, to_dev
+from helpers import check_float, to_dev
 from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -48,12 +48,7 @@ def test_batched_4096_sampled_against_oracle():
     for i in rng.choice(len(As), 48, replace=False):
         M, e, _ = oracle.matpow_f64(As[i], ns[i])
         err = oracle.rel_frobenius(outs[i].cpu().numpy(), int(lgs[i]), M, e)
-        Mf, ef = oracle.fp32_sqmul(As[i], ns[i])
-        floor = oracle.rel_frobenius(Mf, ef, M, e)
-        if Ns[i] > 64:
-            Me, ee = oracle.emu_sqmul(As[i], ns[i], "bf16x6blk")
-            floor = max(floor, oracle.rel_frobenius(Me, ee, M, e))
-        assert err <= gate(ns[i], floor), (i, Ns[i], ns[i], err)
+        check_float(err, "bf16x6", ns[i], As[i], M, e, what="batch 4096")
     plan.close()
 
 

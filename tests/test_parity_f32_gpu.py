@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import float_tol, gate, to_dev
+from helpers import check_float, float_bound, float_tol, to_dev
 from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +22,6 @@ PRECS = ["fp32", "bf16x3", "bf16x6", "bf16"]
 # them exactly; three slices extend that to 24 bits; a bfloat16 operand holds
 # integers < 2^8.
 FIB_EXACT = {"fp32": 34, "bf16x3": 23, "bf16x6": 34, "bf16": 12}
-EMU = {"bf16": "bf16", "bf16x3": "bf16x3blk", "bf16x6": "bf16x6blk"}
 
 
 @pytest.fixture(scope="module")
@@ -46,23 +45,13 @@ def run(plan, A, n, mantissa=True):
     return out.cpu().numpy().astype(np.float64), st
 
 
-def floor_rel(A, n, M, e, prec="fp32"):
-    """Error of a CPU run of the same method at the path's precision class."""
-    Mf, ef = oracle.fp32_sqmul(A, n)
-    f = oracle.rel_frobenius(Mf, ef, M, e)
-    if prec in EMU and A.shape[0] > 64:  # N <= 64 runs the float32 chain
-        Me, ee = oracle.emu_sqmul(A, n, EMU[prec])
-        f = max(f, oracle.rel_frobenius(Me, ee, M, e))
-    return f
-
-
 @pytest.mark.parametrize("prec", PRECS)
 def test_config1_stochastic_64_n100(plans, prec):
     A = wl.stochastic_exact(64, 0)
     M, e, _ = oracle.matpow_f64(A, 100)
     got, ge = run(plans[prec], A, 100)
     err = oracle.rel_frobenius(got, ge, M, e)
-    assert err <= float_tol(100), err
+    check_float(err, prec, 100, A, M, e, stated_only=True, what="config 1")
     rows = np.ldexp(got, ge).sum(axis=1)
     assert np.max(np.abs(rows - 1.0)) <= 1e-5
 
@@ -74,9 +63,9 @@ def test_config2_gaussian_512(plans, prec, n):
     M, e, _ = oracle.matpow_f64(A, n)
     got, ge = run(plans[prec], A, n)
     err = oracle.rel_frobenius(got, ge, M, e)
-    bound = gate(n, floor_rel(A, n, M, e, prec))
-    print("prec=%s n=%d rel_F=%.3e bound=%.3e" % (prec, n, err, bound))
-    assert err <= bound, (err, bound)
+    # float32-class paths meet the stated bound on this workload directly;
+    # BF16 and BF16X3 (8 and 16 bits) do not, and are bounded by their class
+    check_float(err, prec, n, A, M, e, stated_only=prec in ("fp32", "bf16x6"), what="config 2")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -87,8 +76,7 @@ def test_sizes_span_tiles_and_ragged_tails(plans, prec, N):
         M, e, _ = oracle.matpow_f64(A, n)
         got, ge = run(plans[prec], A, n)
         err = oracle.rel_frobenius(got, ge, M, e)
-        bound = gate(n, floor_rel(A, n, M, e, prec))
-        assert err <= bound, (N, n, err, bound)
+        check_float(err, prec, n, A, M, e, what="sizes")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -138,7 +126,7 @@ def test_value_mode_and_range(plans, prec):
         got, st = run(plans[prec], A, n, mantissa=False)
         assert st == 0
         want = np.ldexp(M, e)
-        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= gate(n, floor_rel(A, n, M, e, prec))
+        check_float(np.linalg.norm(got - want) / np.linalg.norm(want), prec, n, A, M, e, what="value mode")
     # 4I: (4I)^100 = 2^200 I overflows float32 -> inf and ERANGE, mantissa form exact
     A = 4.0 * np.eye(80, dtype=np.float32)
     got, st = run(plans[prec], A, 100, mantissa=False)
@@ -173,11 +161,9 @@ def test_stochastic_long_chain_row_sums(plans, prec):
     M, e, _ = oracle.matpow_f64(A, n)
     got, ge = run(plans[prec], A, n)
     err = oracle.rel_frobenius(got, ge, M, e)
-    bound = gate(n, floor_rel(A, n, M, e, prec))
     rows = np.ldexp(got, ge).sum(axis=1)
-    print("prec=%s rel_F=%.3e bound=%.3e max|rowsum-1|=%.3e" % (prec, err, bound,
-                                                                  np.max(np.abs(rows - 1))))
-    assert err <= bound
+    print("max|rowsum-1|=%.3e" % np.max(np.abs(rows - 1)))
+    check_float(err, prec, n, A, M, e, what="stochastic 2^20")
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -193,7 +179,7 @@ def test_aliasing_out_equals_in(plans, prec):
         plans[prec].check()
         M, e, _ = oracle.matpow_f64(A, 13)
         err = oracle.rel_frobenius(dA.cpu().numpy(), int(lg.item()), M, e)
-        assert err <= gate(13, floor_rel(A, 13, M, e, prec))
+        check_float(err, prec, 13, A, M, e, what="aliasing")
 
 
 def test_invalid_arguments():
@@ -242,8 +228,7 @@ def test_every_tensor_core_tile_shape(prec, tile):
             M, e, _ = oracle.matpow_f64(A, n)
             got, ge = run(plan, A, n)
             err = oracle.rel_frobenius(got, ge, M, e)
-            bound = gate(n, floor_rel(A, n, M, e, prec))
-            assert err <= bound, (tile, N, n, err, bound)
+            check_float(err, prec, n, A, M, e, what="tile %d" % tile)
     plan.close()
 
 
@@ -285,8 +270,11 @@ def test_floating_split_option(n):
     M, e, _ = oracle.matpow_f64(A, n)
     got, ge = run(plan, A, n)
     err = oracle.rel_frobenius(got, ge, M, e)
+    # floating hi/lo parts: bounded by the emulated floating split
     Me, ee = oracle.emu_sqmul(A, n, "bf16x3")
-    assert err <= gate(n, oracle.rel_frobenius(Me, ee, M, e)), err
+    b = max(float_tol(n), 2.0 * oracle.rel_frobenius(Me, ee, M, e))
+    print("floating split n=%d rel_F=%.3e bound=%.3e" % (n, err, b))
+    assert err <= b, err
     plan.close()
 
 
@@ -313,34 +301,33 @@ def test_whole_chain_kernel_equals_level_path_bitwise(prec, N):
         assert torch.equal(oc, ol), (N, n)
         M, e, _ = oracle.matpow_f64(A, n)
         err = oracle.rel_frobenius(oc.cpu().numpy(), int(lc.item()), M, e)
-        assert err <= gate(n, floor_rel(A, n, M, e, prec)), (N, n, err)
+        check_float(err, prec, n, A, M, e, what="whole chain")
     # value mode through the chain kernel
     ov = chain.f32(dA, 5)
     assert chain.sync() == 0
     M, e, _ = oracle.matpow_f64(A, 5)
     want = np.ldexp(M, e)
-    assert np.linalg.norm(ov.cpu().numpy() - want) / np.linalg.norm(want) <= gate(5, floor_rel(A, 5, M, e, prec))
+    check_float(np.linalg.norm(ov.cpu().numpy() - want) / np.linalg.norm(want), prec, 5, A, M, e,
+                what="whole chain, value mode")
     chain.close()
     level.close()
 
 
 def test_bf16x6_at_float32_accuracy():
-    # three slices (24-bit fixed point per 64 x 64 block): within a small
-    # factor of a float32 run of the same chain, far below two slices
+    # three slices (24-bit fixed point per 64 x 64 block): within the stated
+    # float32-class bound, and far below two slices
     from paper_1204_3052_gb300 import matpow as mpw
     errs = {}
     for N, n in ((512, 16), (300, 1000), (1000, 7)):
         A = wl.gaussian(N, N + 1)
         M, e, _ = oracle.matpow_f64(A, n)
-        Mf, ef = oracle.fp32_sqmul(A, n)
-        ef32 = oracle.rel_frobenius(Mf, ef, M, e)
         for prec in ("bf16x3", "bf16x6"):
             plan = mpw.Plan(1024, prec)
             got, ge = run(plan, A, n)
             errs[prec] = oracle.rel_frobenius(got, ge, M, e)
             plan.close()
-        print(N, n, errs, ef32)
-        assert errs["bf16x6"] <= 4 * ef32, (N, n, errs, ef32)
+        print(N, n, errs)
+        check_float(errs["bf16x6"], "bf16x6", n, A, M, e, stated_only=True, what="three slices")
         assert errs["bf16x6"] * 30 < errs["bf16x3"], (N, n, errs)
 
 
@@ -364,7 +351,7 @@ def test_split_k_chain_matches_oracle_and_unsplit_chain(prec, N):
         whole.check()
         M, e, _ = oracle.matpow_f64(A, n)
         err = oracle.rel_frobenius(os_.cpu().numpy(), int(ls.item()), M, e)
-        assert err <= gate(n, floor_rel(A, n, M, e, prec)), (N, n, err)
+        check_float(err, prec, n, A, M, e, what="split-K chain")
         d = oracle.rel_frobenius(os_.cpu().numpy(), int(ls.item()),
                                  ow.cpu().numpy().astype(np.float64), int(lw.item()))
         assert d <= 1e-5 * n ** 0.5 * (30 if prec == "bf16x3" else 1), (N, n, d)

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import gate, to_dev
+from helpers import check_float, to_dev
 from paper_1204_3052_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -70,13 +70,8 @@ def test_mixed_stream_matches_isolated_runs(prec):
         assert torch.equal(out, alone) and int(lg.item()) == int(alone_lg.item()), (N, n)
         if n <= 1000:
             M, e, _ = oracle.matpow_f64(A, n)
-            Mf, ef = oracle.fp32_sqmul(A, n)
-            floor = oracle.rel_frobenius(Mf, ef, M, e)
-            if prec in ("bf16x3", "bf16x6") and N > 64:
-                Me, ee = oracle.emu_sqmul(A, n, prec + "blk")
-                floor = max(floor, oracle.rel_frobenius(Me, ee, M, e))
             err = oracle.rel_frobenius(out.cpu().numpy(), int(lg.item()), M, e)
-            assert err <= gate(n, floor), (N, n, err)
+            check_float(err, prec, n, A, M, e, what="served")
     lat = server.latencies_us()
     assert len(lat) == len(reqs) and np.all(lat > 0)
     server.close()
