@@ -75,8 +75,8 @@ WORKLOADS = {
     "batched4096": dict(kind="batched", count=4096, n_max=4096, N=256, ns=[], prec="bf16x6",
                         desc="batched: 4096 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
                              "n log-uniform in [1,4096], seed 0; one grouped launch per level"),
-    "serving": dict(kind="serving", count=2000, N=2048, ns=[], prec="bf16x6",
-                    desc="serving: 2000 Poisson-arrival requests, N log-uniform [8,2048], n log-uniform "
+    "serving": dict(kind="serving", count=20000, N=2048, ns=[], prec="bf16x6",
+                    desc="serving: 20000 Poisson-arrival requests, N log-uniform [8,2048], n log-uniform "
                          "[1,2^30], 90% float / 10% mod 65521, seed 0"),
     "modp2048": dict(kind="modp", N=2048, ns=[1000], p=65521, prec="bf16x3",
                      desc="single N=2048 U{0..65520} uint32, A^1000 mod 65521 (14 products), seed 0"),
@@ -93,10 +93,42 @@ WORKLOADS = {
     "batched512": dict(kind="batched", count=512, n_max=4096, N=256, ns=[], prec="bf16x6",
                        desc="batched: 512 N(0,1/N) float32 matrices, N uniform over {16,...,256}, "
                             "n log-uniform in [1,4096], seed 0; one grouped launch per level"),
+    # one product at N=8192 (operand planes 256 MB, twice the L2; ~2 GB on the
+    # device in all): the headline kernel's profiling case
+    "probe8192": dict(N=8192, ns=[2], gen="stochastic", prec="bf16x3",
+                      desc="single N=8192 exact row-stochastic float32, n=2 (one product), seed 0"),
     # one product at N=4096 (operands 64 MB each, beyond L2): profiling case
     "probe4096": dict(N=4096, ns=[2], gen="stochastic", prec="bf16x3",
                       desc="single N=4096 exact row-stochastic float32, n=2 (one product), seed 0"),
 }
+
+
+def tile_table_path(args):
+    """The tile table the bench's plans load: the tuned table shipped with the
+    package (``--tile-table default``, when present), a file, or none."""
+    if args.tile_table == "none":
+        return None
+    if args.tile_table == "default":
+        from paper_1204_3052_gb300 import matpow as mpw
+        return mpw.DEFAULT_TILE_TABLE if os.path.exists(mpw.DEFAULT_TILE_TABLE) else None
+    return args.tile_table
+
+
+_FP32_PEAK = {}
+
+
+def fp32_peak(dev_index: int):
+    """Measured FP32 FFMA TFLOP/s of the device (register-only probe of the
+    library, best of 5 timed launches of ~0.1 s of work), cached per device;
+    with a note of where it came from."""
+    if dev_index not in _FP32_PEAK:
+        from paper_1204_3052_gb300 import matpow as mpw
+        plan = mpw.Plan(64, "fp32", device=dev_index)
+        v = mpw.measure_fp32_peak(plan.h, iters=1 << 17)
+        plan.close()
+        _FP32_PEAK[dev_index] = (v, "measured: matpow_selftest_ffma, 8 CTAs x 256 threads per SM, "
+                                    "8 register FFMA chains per thread, best of 5")
+    return _FP32_PEAK[dev_index]
 
 
 def gemm_count(n: int) -> int:
@@ -339,13 +371,16 @@ def reference_items(wk):
 def config_for(args, wk, world):
     """The `config` object of a bench line, identical for both arms."""
     from paper_1204_3052_gb300 import workloads as wl
-    cfg = {"workload": wk["desc"], "precision": args.precision}
+    tt = tile_table_path(args)
+    cfg = {"workload": wk["desc"], "precision": args.precision,
+           "tile_table": os.path.basename(tt) if tt else "built-in rules"}
     if wk.get("kind") == "batched":
         bd = wl.batched_draw(count=wk["count"], seed=0, n_max=wk["n_max"])
         cfg.update(matrices=wk["count"], gemms_per_step=int(sum(gemm_count(int(n)) for n in bd.ns)),
                    l2="flushed between timed steps (256 MB write)")
     elif wk.get("kind") == "serving":
-        cfg.update(requests=wk["count"], load_sweep=list(args.sweep), sweep_requests=args.sweep_count)
+        cfg.update(requests=wk["count"], load_sweep=list(args.sweep),
+                   sweep_requests=min(wk["count"], args.sweep_count) if args.sweep_count > 0 else wk["count"])
     elif wk.get("kind") == "naive":
         cfg.update(orders=wk["Ns"], powers=wk["ns_list"], l2="flushed between timed runs (256 MB write)")
     elif wk.get("kind") == "modp":
@@ -477,8 +512,13 @@ def path_compare(args, wk, A, A_host, flush, stream, value, prec="fp32"):
     v = steps * flop_step / (ms * 1e-3) / 1e12
     errs = {} if args.no_check else errors_of(wk, A_host, ns, outs, lgs)
     plan.close()
-    return {"precision": prec, "value": v, "unit": "TFLOP/s", "steps": steps, "rel_frobenius_vs_f64": errs,
-            "ratio_this_path_over_it": value / v if v else None}
+    out = {"precision": prec, "value": v, "unit": "TFLOP/s", "steps": steps, "rel_frobenius_vs_f64": errs,
+           "ratio_this_path_over_it": value / v if v else None}
+    if prec == "fp32":  # the comparator's own quality: its rate against the measured FFMA peak
+        pk, _ = fp32_peak(A.device.index)
+        out["measured_fp32_peak_tflops"] = pk
+        out["frac_of_fp32_peak"] = v / pk
+    return out
 
 
 def config2_table(args, dev, flush, stream):
@@ -563,7 +603,7 @@ def run_ours(args, wk, world, rank, local):
     lgs = torch.zeros(len(ns), dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    plan = mpw.Plan(N, prec, device=local)
+    plan = mpw.Plan(N, prec, device=local, tile_table=tile_table_path(args))
     plan.set_option(mpw.OPT_CHAIN, args.chain_mode)
 
     def step(s):
@@ -674,14 +714,13 @@ def run_ours(args, wk, world, rank, local):
         if peaks.get("bf16_tflops_sustained"):
             roof["frac_of_sustained"] = achieved / peaks["bf16_tflops_sustained"]
     else:
-        # float32 FFMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock
-        smax = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * smax * 1e6 / 1e12
+        # float32 FFMA peak, measured by the library's register-only probe
+        peak, psrc = fp32_peak(local)
         achieved = kflop / (kms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "kernel": "simt_gemm" if kind == mpw.KERNEL_SIMT else "tiny_chain",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+                "peak_source": psrc}
         if kind == mpw.KERNEL_TINY:
             # the chain is a dependent sequence of products on the SMs of one
             # CTA (N <= 32) or one four-CTA cluster: their share of the peak
@@ -874,7 +913,7 @@ def run_expm(args, wk, world, rank, local):
     lg = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    plan = mpw.Plan(N, args.precision, device=local)
+    plan = mpw.Plan(N, args.precision, device=local, tile_table=tile_table_path(args))
 
     def step(s):
         st = mpw.matpow_expm(plan.h, A, N, out, lg, s)
@@ -957,12 +996,10 @@ def run_expm(args, wk, world, rank, local):
                 "kernel": "tc_chain kernels and tc_fxb_kernel (powers, products, squarings)",
                 "peak_source": peak_src + " bf16 burst", "counted": "%d bfloat16 product(s) per term" % products}
     else:
-        smax = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * smax * 1e6 / 1e12
+        peak, psrc = fp32_peak(local)
         achieved = kflop / (kms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "simt_gemm",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % smax}
+                "traffic": None, "kernel": "simt_gemm", "peak_source": psrc}
     roof["launches_timed"] = kl
     roof["avg_launch_us"] = kms * 1e3 / max(kl, 1)
     roof["kernel_share_of_step"] = kms / max(args.steps, 3) / (t_ms / args.steps)
@@ -1107,7 +1144,7 @@ def run_batched(args, wk, world, rank, local):
     flop_step = sum(gemm_count(n) * 2.0 * N ** 3 for N, n in zip(Ns, ns))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    plan = mpw.Plan(max(Ns), args.precision, device=local)
+    plan = mpw.Plan(max(Ns), args.precision, device=local, tile_table=tile_table_path(args))
 
     def step(s):
         mpw._check(mpw.matpow_batched(plan.h, dA, Ns, ns, outs, lg, s), plan.h)
@@ -1250,16 +1287,32 @@ def run_serving(args, wk, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     count = wk["count"]
-    sweep_count = min(count, args.sweep_count)
+    sweep_count = min(count, args.sweep_count) if args.sweep_count > 0 else count
     base_rate = 1000.0
     reqs = wl.serving_stream(count=count, seed=0, rate_per_s=base_rate)
-    host = [wl.request_matrix(r) for r in reqs]
+    # inputs drawn on a thread pool and moved to the device as they come; the
+    # host keeps only the matrices the oracle checks (every mod-p request with
+    # N <= 256, and float requests with N <= 512, n <= 1024, one in 50)
+    check_mod = [r.kind == 1 and r.N <= 256 for r in reqs]
+    check_flt = [r.kind == 0 and r.N <= 512 and r.n <= 1024 for r in reqs]
+    kf = [i for i, c in enumerate(check_flt) if c][::50]
+    check_flt = [False] * count
+    for i in kf:
+        check_flt[i] = True
+    host = [None] * count
     dA, outs, lgs = [], [], []
-    for r, a in zip(reqs, host):
-        t = torch.from_numpy(a.view(np.int32) if r.kind else a).to(dev)
-        dA.append(t)
-        outs.append(torch.empty_like(t))
-        lgs.append(torch.zeros(1, dtype=torch.int64, device=dev) if r.kind == 0 else None)
+    from concurrent.futures import ThreadPoolExecutor
+    t_gen = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
+        for i, a in enumerate(ex.map(wl.request_matrix, reqs)):
+            r = reqs[i]
+            t = torch.from_numpy(a.view(np.int32) if r.kind else a).to(dev)
+            dA.append(t)
+            outs.append(torch.empty_like(t))
+            lgs.append(torch.zeros(1, dtype=torch.int64, device=dev) if r.kind == 0 else None)
+            if check_mod[i] or check_flt[i]:
+                host[i] = a
+    t_gen = time.perf_counter() - t_gen
     flop = sum(gemm_count(r.n) * 2.0 * r.N ** 3 for r in reqs)
     server = mpw.Server(2048, args.precision, device=local, hbm_budget_bytes=16 << 30,
                         max_inflight=256, max_queue=count + 16)
@@ -1310,15 +1363,21 @@ def run_serving(args, wk, world, rank, local):
                       "p50_ms": float(np.percentile(lat, 50) / 1e3),
                       "p99_ms": float(np.percentile(lat, 99) / 1e3)})
     server.close()
-    # exact mod-p requests checked against the oracle (those with N <= 256)
+    # exact mod-p requests checked against the oracle (those with N <= 256),
+    # and a sample of float requests (their errors reported)
     checked = mism = 0
+    ferrs = []
     if not args.no_check:
         import oracle
-        for r, a, o in zip(reqs, host, outs):
-            if r.kind == 1 and r.N <= 256:
+        for i, (r, a, o) in enumerate(zip(reqs, host, outs)):
+            if check_mod[i]:
                 want, _ = oracle.matpow_modp(a, r.n, r.p)
                 checked += 1
                 mism += int(not np.array_equal(o.cpu().numpy().view(np.uint32).astype(np.uint64), want))
+            elif check_flt[i]:
+                M, e, _ = oracle.matpow_f64(a, r.n)
+                err = oracle.rel_frobenius(o.cpu().numpy(), int(lgs[i].item()), M, e)
+                ferrs.append((err, err <= stated_tolerance(r.n)))
     # ---- 3. unbatched comparator: single-request calls, one at a time
     plan_f = mpw.Plan(2048, args.precision, device=local)
     plan_m = mpw.Plan(2048, "fp32", device=local)
@@ -1369,6 +1428,10 @@ def run_serving(args, wk, world, rank, local):
             "latency_note": "p50/p99 of the closed burst (queueing included); see load_sweep",
             "load_sweep": sweep, "effective_tflops": flop / wall / 1e12, "failed_requests": bad,
             "modp_checked": checked, "modp_mismatches": mism,
+            "float_checked": len(ferrs),
+            "float_max_rel_frobenius": max((e for e, _ in ferrs), default=None),
+            "float_within_2e-5_ceil_log2_n": sum(ok for _, ok in ferrs),
+            "input_generation_s": t_gen,
             "unbatched": unb, "speedup_over_unbatched": capacity / unb_cap,
             "clocks": clocks,
             "e2e": {"value": capacity, "unit": "req/s", "h2d_bytes_per_step": 0,
@@ -1403,7 +1466,11 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=5.0)
     ap.add_argument("--sweep", type=float, nargs="*", default=[0.5, 0.8, 1.0, 1.2],
                     help="serving: offered loads as fractions of the measured capacity")
-    ap.add_argument("--sweep-count", type=int, default=1000)
+    ap.add_argument("--sweep-count", type=int, default=0,
+                    help="serving: requests per load point (0: the whole stream)")
+    ap.add_argument("--tile-table", default="default",
+                    help="'default' (the tuned table shipped with the package, if present), 'none' "
+                         "(built-in rules) or a tile-table JSON file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

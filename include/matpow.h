@@ -310,6 +310,20 @@ matpow_status matpow_sync(matpow_plan_t plan, void* stream);
  */
 matpow_status matpow_selftest_wait_timeout(matpow_plan_t plan, uint64_t budget_ns, void* stream);
 
+/*
+ * FP32 throughput probe (the roofline denominator of the float32 SIMT path).
+ * Launches 8 CTAs of 256 threads per SM; every thread runs 8 independent
+ * float32 fused multiply-add chains of `iters` steps on registers only
+ * (`iters` a multiple of 16 in [16, 2^32], else MATPOW_EINVAL): exactly
+ * 2 x 8 x iters x 256 x 8 x (SMs) flop, no memory traffic.  Time it with
+ * CUDA events on `stream`.  Asynchronous.  (No counterpart in the paper,
+ * whose Fermi figures are nominal.)
+ */
+matpow_status matpow_selftest_ffma(matpow_plan_t plan, int64_t iters, void* stream);
+
+/* Streaming multiprocessors of the plan's device (sizes the probe above). */
+int matpow_plan_sm_count(matpow_plan_t plan);
+
 /* G(n) = floor(log2 n) + popcount(n) - 1 (0 for n <= 1): products that A^n takes. */
 int matpow_gemm_count(uint64_t n);
 

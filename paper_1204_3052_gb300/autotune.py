@@ -1,0 +1,247 @@
+"""Tile-shape autotuner for libmatpow: measures launch shapes on the device
+and writes the winners as a tile table (include/matpow.h, matpow_tile_rule).
+
+The paper keeps a family of product kernels with tile shapes 4 x 4 .. 16 x 16
+and chooses one by the problem and the local memory (arXiv 1204.3052,
+Sec. 4.3.7).  Here the family is the set of launch shapes the library can
+run for the exact splits (BF16X3, BF16X6), and the choice is measured:
+
+* single powers, per range of orders (representative order: the range's top,
+  A^1024 of a N(0, 1/N) matrix, one matpow_f32 call timed by CUDA events
+  with L2 flushed between calls): the whole chain in one cooperative launch
+  or one launch per level; the tile width (64 or 128 columns; BF16X6 only
+  64); split-K over 1, 2 or 4 CTAs of a cluster (whole chain, 64 columns);
+* batches, per range of orders present in the batch (a draw of the batched
+  workload: N = 16 U{1..16}, n log-uniform in [1, 4096]; one matpow_batched
+  call timed): the persistent kernel or one CTA per tile, one range at a
+  time with the others held (coordinate descent).
+
+Every candidate's result is compared with the built-in choice's on the same
+input before its time counts (a launch shape changes the order of the float32
+sums at most, so the results agree to rounding; a candidate that does not is
+dropped).  The table keeps every measurement beside the chosen fields.
+
+    python -m paper_1204_3052_gb300.autotune [--out FILE] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import datetime
+import json
+import os
+import statistics
+import sys
+
+import numpy as np
+
+from . import matpow as mpw
+from . import workloads as wl
+
+SINGLE_EDGES = [64, 128, 256, 384, 512, 768, 1024, 2048, 4096, 8192]
+BATCH_EDGES = [64, 128, 192, 256, 1024, 4096]
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _time_ms(fn, flush, stream, reps: int, warmup: int = 2) -> float:
+    """Median CUDA-event milliseconds of fn() over reps calls (L2 flushed before each)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _rel(a, la, b, lb) -> float:
+    """||a 2^la - b 2^lb||_F / ||b 2^lb||_F with exponents aligned (float64)."""
+    x = np.ldexp(a.astype(np.float64), la - lb)
+    y = b.astype(np.float64)
+    d = np.linalg.norm(y)
+    return float(np.linalg.norm(x - y) / d) if d else float(np.linalg.norm(x))
+
+
+# a candidate's A^1024 against the built-in choice's: two results of the same
+# class differ by up to about twice their error against the exact power
+# (2e-4 is the stated float32-class bound at n = 1024; the 16-bit split
+# reaches ~2e-3 there)
+AGREE = {"bf16x3": 1e-2, "bf16x6": 4e-4}
+
+
+def single_candidates(prec: str, N: int):
+    bns = [64] if prec == "bf16x6" else [64, 128]
+    out = []
+    if N <= 1024:
+        for bn in bns:
+            for sk in ([1, 2] if prec == "bf16x6" else [1, 2, 4]):
+                if bn == 128 and sk > 1:
+                    continue  # split-K runs at 64 columns
+                out.append({"chain": 1, "bn": bn, "split_k": sk})
+        for bn in bns:
+            out.append({"chain": 0, "bn": bn})
+    else:
+        out += [{"bn": bn} for bn in bns]
+    return out
+
+
+def tune_single(prec: str, edges, n: int, reps: int, flush, stream, log):
+    import torch
+    rules = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        N = hi
+        cands = single_candidates(prec, N)
+        if len(cands) < 2:
+            continue
+        A = torch.from_numpy(wl.gaussian(N, 1000 + N)).cuda()
+        plan = mpw.Plan(N, prec)
+        ref, ref_lg = plan.f32(A, n, mantissa=True)  # built-in choice
+        plan.check()
+        ref, ref_lg = ref.cpu().numpy(), int(ref_lg.item())
+        out = torch.empty_like(A)
+        lg = torch.zeros(1, dtype=torch.int64, device="cuda")
+        t_builtin = _time_ms(lambda: mpw._check(mpw.matpow_f32(plan.h, A, N, n, out, lg, stream), plan.h),
+                             flush, stream, reps)
+        results = []
+        for c in cands:
+            rule = dict({"precision": prec, "n_lo": lo, "n_hi": hi, "bn": -1, "split_k": -1, "chain": -1,
+                         "persist": -1}, **c)
+            plan.set_tile_table([rule])
+
+            def call():
+                mpw._check(mpw.matpow_f32(plan.h, A, N, n, out, lg, stream), plan.h)
+
+            call()
+            plan.check(stream)
+            agree = _rel(out.cpu().numpy(), int(lg.item()), ref, ref_lg)
+            ok = agree <= AGREE[prec]
+            t = _time_ms(call, flush, stream, reps) if ok else None
+            results.append(dict(c, us=None if t is None else round(t * 1e3, 2), agrees=ok,
+                                rel_to_builtin=agree))
+            log("  %s N=%d %s: %s" % (prec, N, c, "%.1f us" % (t * 1e3) if ok else "REJECTED %.2e" % agree))
+        plan.close()
+        good = [r for r in results if r["agrees"]]
+        best = min(good, key=lambda r: r["us"])
+        rule = {"precision": prec, "n_lo": lo, "n_hi": hi, "bn": best.get("bn", -1),
+                "split_k": best.get("split_k", -1), "chain": best.get("chain", -1), "persist": -1,
+                "measured_at": {"N": N, "n": n}, "builtin_us": round(t_builtin * 1e3, 2),
+                "best_us": best["us"], "candidates": results}
+        log("%s (%d, %d]: built-in %.1f us -> %s %.1f us" % (prec, lo, hi, t_builtin * 1e3,
+                                                             {k: best[k] for k in c if k in best}, best["us"]))
+        rules.append(rule)
+    return rules
+
+
+def tune_batched(prec: str, rules, count: int, reps: int, flush, stream, log):
+    """Persistent kernel or one CTA per tile, per range of orders in the
+    batch (the single-power rules' own ranges, plus ranges of BATCH_EDGES for
+    orders no rule covers), one range at a time with the others held; the
+    single-power fields stay.  Returns the updated rules and the trials."""
+    import torch
+    bd = wl.batched_draw(count=count, seed=0, n_max=4096)
+    Ns = [int(x) for x in bd.Ns]
+    ns = [int(x) for x in bd.ns]
+    offs = np.cumsum([0] + [N * N for N in Ns])
+    dbuf = torch.from_numpy(np.concatenate([wl.gaussian(N, int(s)).reshape(-1) for N, s in zip(Ns, bd.seeds)]))
+    dbuf = dbuf.cuda()
+    obuf = torch.empty_like(dbuf)
+    As = [dbuf[int(o):int(o) + N * N].view(N, N) for o, N in zip(offs[:-1], Ns)]
+    outs = [obuf[int(o):int(o) + N * N].view(N, N) for o, N in zip(offs[:-1], Ns)]
+    lg = torch.zeros(len(As), dtype=torch.int64, device="cuda")
+    plan = mpw.Plan(max(Ns), prec)
+
+    def call():
+        mpw._check(mpw.matpow_batched(plan.h, As, Ns, ns, outs, lg, stream), plan.h)
+
+    table = [dict(r) for r in rules if r["precision"] == prec]
+    others = [r for r in rules if r["precision"] != prec]
+    big = [N for N, n in zip(Ns, ns) if N > 64 and n >= 2]  # the tensor-core levels' orders
+    for lo, hi in zip(BATCH_EDGES[:-1], BATCH_EDGES[1:]):
+        if any(lo < N <= hi for N in big) and not any(r["n_lo"] < N <= r["n_hi"] for r in table for N in big
+                                                       if lo < N <= hi):
+            table.append({"precision": prec, "n_lo": lo, "n_hi": hi, "bn": -1, "split_k": -1, "chain": -1,
+                          "persist": -1})
+    tuned = [i for i, r in enumerate(table) if any(r["n_lo"] < N <= r["n_hi"] for N in big)]
+    plan.set_tile_table(_clean(table))
+    call()
+    plan.check(stream)
+    ref = [o.cpu().numpy() for o in outs]
+    ref_lg = lg.cpu().numpy().copy()
+    t0 = _time_ms(call, flush, stream, reps)
+    log("%s batch of %d: single-power table %.3f ms" % (prec, count, t0))
+    measured = []
+    best_t = t0
+    for i in tuned:
+        keep = table[i]["persist"]
+        best_v = keep
+        for v in (1, 0):
+            table[i]["persist"] = v
+            plan.set_tile_table(_clean(table))
+            call()
+            plan.check(stream)
+            lgs = lg.cpu().numpy()
+            worst = max(_rel(outs[k].cpu().numpy(), int(lgs[k]), ref[k], int(ref_lg[k]))
+                        for k in range(0, len(outs), 64))
+            ok = worst <= 1e-4
+            t = _time_ms(call, flush, stream, reps) if ok else None
+            measured.append({"range": [table[i]["n_lo"], table[i]["n_hi"]], "persist": v, "ms": t, "agrees": ok})
+            log("  batch range (%d, %d] persist=%d: %s" % (table[i]["n_lo"], table[i]["n_hi"], v,
+                                                         "%.3f ms" % t if ok else "REJECTED"))
+            if ok and t < best_t:
+                best_t, best_v = t, v
+        table[i]["persist"] = best_v
+    plan.close()
+    log("%s batch: %.3f ms -> %.3f ms" % (prec, t0, best_t))
+    return others + table, {"precision": prec, "count": count, "ms_single_power_table": t0,
+                            "ms_best": best_t, "trials": measured}
+
+
+def _clean(rules):
+    keys = ("precision", "n_lo", "n_hi", "bn", "split_k", "chain", "persist")
+    return [{k: r[k] for k in keys} for r in rules]
+
+
+def main(argv=None):
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=mpw.DEFAULT_TILE_TABLE)
+    ap.add_argument("--quick", action="store_true", help="fewer repetitions and orders (a check run)")
+    ap.add_argument("--precisions", nargs="*", default=["bf16x6", "bf16x3"])
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=4096)
+    args = ap.parse_args(argv)
+    assert torch.cuda.is_available(), "the autotuner measures on a CUDA device"
+    reps = 3 if args.quick else 9
+    edges = SINGLE_EDGES[:6] if args.quick else SINGLE_EDGES
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    log = lambda m: print(m, file=sys.stderr, flush=True)  # noqa: E731
+    rules, batch_info = [], []
+    for prec in args.precisions:
+        rules += tune_single(prec, edges, args.n, reps, flush, stream, log)
+        if args.batch:
+            rules, info = tune_batched(prec, rules, args.batch if not args.quick else 512, reps, flush, stream,
+                                       log)
+            batch_info.append(info)
+    doc = {"version": 1, "device": torch.cuda.get_device_name(0),
+           "measured": datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%dT%H:%M:%SZ"),
+           "method": "CUDA-event medians, L2 flushed; single powers A^%d of N(0,1/N) at each range's top "
+                     "order; batches: the batched workload draw (seed 0)" % args.n,
+           "rules": rules, "batched": batch_info}
+    tmp = args.out + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(doc, f, indent=1)
+    os.replace(tmp, args.out)
+    log("wrote %s (%d rules)" % (args.out, len(rules)))
+
+
+if __name__ == "__main__":
+    main()

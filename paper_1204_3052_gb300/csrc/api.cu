@@ -338,6 +338,8 @@ extern "C" matpow_status matpow_kernel_time(matpow_plan_t p, int kind, int64_t* 
 
 extern "C" int64_t matpow_launch_count(matpow_plan_t p) { return p ? p->launches : 0; }
 
+extern "C" int matpow_plan_sm_count(matpow_plan_t p) { return p ? p->num_sms : 0; }
+
 // ---------------------------------------------------------------------------
 // scheduling one power
 
@@ -762,6 +764,17 @@ extern "C" matpow_status matpow_selftest_wait_timeout(matpow_plan_t p, uint64_t 
     return fail(p, MATPOW_EINVAL, "matpow_selftest_wait_timeout: budget_ns must be in [1e3, 1e10]");
   DeviceGuard dg(p->device);
   CK(p, launch_selftest_wait((unsigned long long)budget_ns, p->status, (cudaStream_t)stream));
+  p->launches++;
+  return MATPOW_OK;
+}
+
+extern "C" matpow_status matpow_selftest_ffma(matpow_plan_t p, int64_t iters, void* stream) {
+  if (!p) return fail(nullptr, MATPOW_EINVAL, "matpow_selftest_ffma: plan is NULL");
+  if (iters < 16 || iters > (int64_t)1 << 32 || (iters & 15))
+    return fail(p, MATPOW_EINVAL, "matpow_selftest_ffma: iters must be a multiple of 16 in [16, 2^32]");
+  DeviceGuard dg(p->device);
+  // eight CTAs of 256 threads per SM: 64 warps, each with 8 independent chains
+  CK(p, launch_ffma_probe((long long)iters, 8 * p->num_sms, p->status + 3, (cudaStream_t)stream));
   p->launches++;
   return MATPOW_OK;
 }

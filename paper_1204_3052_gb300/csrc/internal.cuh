@@ -194,6 +194,8 @@ struct TinyDesc {
   int pad_;
 };
 cudaError_t launch_selftest_wait(unsigned long long budget_ns, unsigned* status, cudaStream_t s);
+// FP32 FFMA throughput probe: `blocks` CTAs of 256 threads, 8 x iters FFMA each.
+cudaError_t launch_ffma_probe(long long iters, int blocks, unsigned* sink, cudaStream_t s);
 cudaError_t launch_tiny_one(const TinyDesc& d, unsigned* status, cudaStream_t s);
 cudaError_t launch_tiny_group(const TinyDesc* d_descs, int count, unsigned* status, cudaStream_t s);
 int tiny_max_supported();

@@ -228,4 +228,34 @@ cudaError_t launch_selftest_wait(unsigned long long budget_ns, unsigned* status,
   return cudaGetLastError();
 }
 
+// FP32 fused multiply-add throughput probe: every thread runs 8 independent
+// chains a <- a * b + c (b, c kernel arguments, so nothing folds at compile
+// time; |b| < 1 keeps the chains bounded and normal), iters x 8 FFMA per
+// thread, all operands in registers.  One store per thread, only if a chain
+// reaches a value it cannot reach (keeps the loop live without memory traffic).
+__global__ void __launch_bounds__(256) ffma_probe_kernel(long long iters, float b, float c, unsigned* sink) {
+  float a0 = threadIdx.x * 1e-3f, a1 = a0 + 0.1f, a2 = a0 + 0.2f, a3 = a0 + 0.3f;
+  float a4 = a0 + 0.4f, a5 = a0 + 0.5f, a6 = a0 + 0.6f, a7 = a0 + 0.7f;
+  for (long long i = 0; i < iters; i += 16) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      a0 = fmaf(a0, b, c);
+      a1 = fmaf(a1, b, c);
+      a2 = fmaf(a2, b, c);
+      a3 = fmaf(a3, b, c);
+      a4 = fmaf(a4, b, c);
+      a5 = fmaf(a5, b, c);
+      a6 = fmaf(a6, b, c);
+      a7 = fmaf(a7, b, c);
+    }
+  }
+  const float t = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+  if (t == -1.0f) atomicAdd(sink, 1u);
+}
+
+cudaError_t launch_ffma_probe(long long iters, int blocks, unsigned* sink, cudaStream_t s) {
+  ffma_probe_kernel<<<blocks, 256, 0, s>>>(iters, 0.999f, 1e-3f, sink);
+  return cudaGetLastError();
+}
+
 }  // namespace mp

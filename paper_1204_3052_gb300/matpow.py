@@ -40,7 +40,7 @@ EXPORTS = [
     "matpow_submit", "matpow_poll", "matpow_server_latencies", "matpow_server_destroy",
     "matpow_f32_noalloc", "matpow_selftest_wait_timeout", "matpow_expm",
     "matpow_plan_set_tile_table", "matpow_plan_load_tile_table", "matpow_tile_table_parse",
-    "matpow_tile_rule_lookup",
+    "matpow_tile_rule_lookup", "matpow_selftest_ffma", "matpow_plan_sm_count",
 ]
 
 # The tile table tuned on a GB300 (written by autotune.py); plans load it when
@@ -117,6 +117,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "matpow_f32_noalloc": (i32, [vp, i32, u64, vp, vp, vp]),
             "matpow_selftest_wait_timeout": (i32, [vp, u64, vp]),
             "matpow_expm": (i32, [vp, vp, i32, vp, vp, vp]),
+            "matpow_selftest_ffma": (i32, [vp, i64, vp]),
+            "matpow_plan_sm_count": (i32, [vp]),
             "matpow_plan_set_tile_table": (i32, [vp, ctypes.POINTER(TileRule), i32]),
             "matpow_plan_load_tile_table": (i32, [vp, ctypes.c_char_p]),
             "matpow_tile_table_parse": (i32, [ctypes.c_char_p, ctypes.POINTER(TileRule), i32,
@@ -258,6 +260,33 @@ def matpow_tile_rule_lookup(rules, precision, N: int):
     st = load().matpow_tile_rule_lookup(_rules_array(rules), len(rules), int(precision), int(N),
                                         ctypes.byref(out))
     return st, out.as_dict()
+
+
+def matpow_selftest_ffma(plan: int, iters: int, stream=None) -> int:
+    return load().matpow_selftest_ffma(plan, int(iters), _stream(stream))
+
+
+def matpow_plan_sm_count(plan: int) -> int:
+    return int(load().matpow_plan_sm_count(plan))
+
+
+def measure_fp32_peak(plan: int, iters: int = 1 << 16, reps: int = 5, stream=None) -> float:
+    """FP32 FFMA TFLOP/s of the plan's device: the best of `reps` timed runs
+    of matpow_selftest_ffma (CUDA events on the stream)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    flop = 2.0 * 8 * iters * 256 * 8 * matpow_plan_sm_count(plan)
+    best = 0.0
+    _check(matpow_selftest_ffma(plan, iters, s), plan)  # warm-up
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check(matpow_selftest_ffma(plan, iters, s), plan)
+        e1.record(s)
+        e1.synchronize()
+        best = max(best, flop / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
 
 
 def matpow_gemm_count(n: int) -> int:
