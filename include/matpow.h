@@ -130,6 +130,16 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       tensor-core tiles (orders up to 4096) in one persistent
  *                       launch, one CTA per SM walking the whole tile list; 0:
  *                       one CTA per tile.  Results are identical either way.
+ *   MATPOW_OPT_PAIR     0 (default): one SM per 128 x 128 tile; 1: exact-split
+ *                       BF16X3 products of orders above 2048 with 128-column
+ *                       tiles run on CTA pairs: one 256 x 128 tile per two
+ *                       SMs, M = 256 tensor-core MMAs (tcgen05 cta_group::2)
+ *                       over both SMs' shared memory, each SM holding half of
+ *                       the B operand.  Results are bit-for-bit those of the
+ *                       one-SM kernel; it runs slower on a GB300 (N = 8192:
+ *                       2.93 ms per product against 2.47 ms), since the
+ *                       per-k-block accumulator hand-off then crosses SMs and
+ *                       the pair saves no shared-memory operand reads.
  *   MATPOW_OPT_NAIVE    0 (default); 1: matpow_f32 with N above the whole-chain
  *                       limit (MATPOW_OPT_TINY_MAX) computes A^n the way the
  *                       paper's naive GPU method does (Sec. 4.2): n - 1
@@ -140,7 +150,7 @@ const char* matpow_last_error(matpow_plan_t plan);
  */
 enum { MATPOW_OPT_GRAPHS = 1, MATPOW_OPT_TIMING = 2, MATPOW_OPT_TINY_MAX = 3, MATPOW_OPT_TILE = 4,
        MATPOW_OPT_SPLIT = 5, MATPOW_OPT_CHAIN = 6, MATPOW_OPT_MODP_TC = 7, MATPOW_OPT_PERSIST = 8,
-       MATPOW_OPT_NAIVE = 9 };
+       MATPOW_OPT_NAIVE = 9, MATPOW_OPT_PAIR = 10 };
 matpow_status matpow_plan_set_option(matpow_plan_t plan, int key, int64_t value);
 
 /* ---- tile table (launch shapes per size class) ------------------------------ */

@@ -43,13 +43,17 @@ L2_FLUSH_BYTES = 256 << 20
 
 
 def _time_ms(fn, flush, stream, reps: int, warmup: int = 2) -> float:
-    """Median CUDA-event milliseconds of fn() over reps calls (L2 flushed before each)."""
+    """Median CUDA-event milliseconds of fn() over reps calls, L2 flushed
+    before each.  The calls are enqueued back to back (one synchronisation
+    after the last), as a caller streaming work would issue them, so the
+    host's time to build a call's arguments overlaps the previous call's
+    device work instead of showing up between the events."""
     import torch
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
-        ts = []
+        evs = []
         for _ in range(reps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -57,9 +61,9 @@ def _time_ms(fn, flush, stream, reps: int, warmup: int = 2) -> float:
             e0.record(stream)
             fn()
             e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-    return statistics.median(ts)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
 
 
 def _rel(a, la, b, lb) -> float:

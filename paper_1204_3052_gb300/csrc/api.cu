@@ -264,6 +264,10 @@ extern "C" matpow_status matpow_plan_set_option(matpow_plan_t p, int key, int64_
     case MATPOW_OPT_PERSIST:
       p->persist = value != 0;
       return MATPOW_OK;
+    case MATPOW_OPT_PAIR:
+      p->pair = value != 0;
+      drop_graphs(p);
+      return MATPOW_OK;
     case MATPOW_OPT_MODP_TC:
       p->modp_tc = value != 0;
       drop_graphs(p);

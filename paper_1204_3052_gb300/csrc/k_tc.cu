@@ -584,6 +584,7 @@ cudaError_t tc_init(matpow_plan_s*) {
   MP_FXB_ATTR(tc_fxb_group_kernel, 128, 2)
   MP_FXB_ATTR(tc_fxb_group_kernel, 64, 3)
 #undef MP_FXB_ATTR
+  if ((e = tc_pair_init()) != cudaSuccess) return e;
   return tc_persist_init();
 }
 
@@ -658,7 +659,15 @@ matpow_status tc_launch_pair(matpow_plan_s* p, const GemmPair& g, cudaStream_t s
   P.tiles0 = g.count > 1 ? g.d[1].tile_begin : g.tiles_total;
   const int bn = g.d[0].bn;
   cudaError_t e;
-  if (fmt == FMT_FX3) {
+  bool on_pairs = fmt == FMT_FX2 && bn == 128 && p->pair;
+  for (int i = 0; i < g.count; ++i) on_pairs = on_pairs && g.d[i].N > 2048 && g.d[i].bn == 128;
+  if (on_pairs) {
+    // 256 x 128 tiles over CTA pairs (same arithmetic, bit-identical results)
+    P.tiles0 = pair_tiles(g.d[0].N);
+    const int total = P.tiles0 + (g.count > 1 ? pair_tiles(g.d[1].N) : 0);
+    if (g.count == 1) P.tiles0 = total;
+    e = launch_fxb_pair(P, total, p->scales, p->status, s);
+  } else if (fmt == FMT_FX3) {
     tc_fxb_kernel<64, 3><<<g.tiles_total, fx::Cfg<64, 3>::THREADS, fx::Cfg<64, 3>::SMEM, s>>>(
         P, p->scales, p->status);
     e = cudaGetLastError();

@@ -103,6 +103,7 @@ struct matpow_plan_s {
   bool modp_tc = true;    // mod-p products on the tensor cores (64 < N <= 16384)
   bool persist = true;    // batched 64-column levels: persistent grouped kernel
   bool naive = false;     // float powers by n - 1 products R <- R A (comparison method)
+  bool pair = false;      // exact-split 128-column levels with N > 2048 on CTA pairs (opt-in)
   unsigned* gbar = nullptr;  // grid-barrier counter of the whole-chain kernel
   float* expm_ws = nullptr;  // matpow_expm scratch: 7 max_n^2 float32 + column sums, on first use
   cudaEvent_t expm_ev = nullptr;  // matpow_expm: the norm's read-back has landed
@@ -203,6 +204,12 @@ cudaError_t launch_fxb_group(const GemmDesc* d_descs, int count, int tiles, cons
                              const void* d_maps, int bn, int nsl, int max_n, int num_sms, bool persist,
                              Scale* scales, unsigned* status, cudaStream_t s);
 cudaError_t tc_persist_init();
+// CTA-pair exact-split products (k_tc2.cu): 256 x 128 tiles over two SMs.
+struct TcPairParams;
+cudaError_t tc_pair_init();
+int pair_tiles(int N);
+cudaError_t launch_fxb_pair(const TcPairParams& P, int pair_tiles_total, Scale* scales, unsigned* status,
+                            cudaStream_t s);
 // Per-tile records of a 64-column grouped level, in tile order: {product
 // index | k-blocks << 24, m0 | n0 << 16, A-role map index, B-role map index}.
 void persist_tile_records(const GemmDesc* descs, int count, int nsl, std::vector<int4>* out);

@@ -31,6 +31,7 @@ PRECISIONS = {"fp32": FP32_SIMT, "fp32_simt": FP32_SIMT, "bf16": BF16, "bf16x3":
               "bf16x6": BF16X6}
 OPT_GRAPHS, OPT_TIMING, OPT_TINY_MAX, OPT_TILE, OPT_SPLIT, OPT_CHAIN, OPT_MODP_TC, OPT_PERSIST, OPT_NAIVE = (
     1, 2, 3, 4, 5, 6, 7, 8, 9)
+OPT_PAIR = 10
 KERNEL_SIMT, KERNEL_TC, KERNEL_TINY, KERNEL_MODP, KERNEL_AUX = range(5)
 
 EXPORTS = [
