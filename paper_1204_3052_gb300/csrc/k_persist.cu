@@ -15,13 +15,17 @@
 // The host gives one 16-byte record per tile (product, depth, origin, the
 // two tensor-map indices), so the producer and MMA warps read one record
 // per tile and prefetch the next.
-//   warps 4-11  fold finished k-blocks into float32 registers, then write
-//           the next operand's slices with plain global stores (no staging
-//           in the ring, which the next tile is already filling); warp w
-//           takes TMEM lane quadrant w % 4 and the tile's column half
-//           (w - 4) / 4, so two warps per scheduler share the epilogue work
-//           (with one warp per quadrant the MMA warp waited on the epilogue
-//           for 43 % of its time with three slices)
+//   warps 4-11  two groups of four: group g folds the finished k-blocks of
+//           the CTA's tiles g, g + 2, g + 4, ... into float32 registers,
+//           then writes the next operand's slices with plain global stores
+//           (no staging in the ring, which the next tile is already
+//           filling); warp w takes TMEM lane quadrant w % 4 and all 64
+//           columns.  While one group re-splits and stores a tile, the other
+//           folds the next tile's k-blocks, so the MMA warp does not wait
+//           through the store phase (with one group of eight warps sharing
+//           every tile, it waited for an accumulator set 40 % of its time
+//           with three slices: only two sets of 3 x 64 columns fit TMEM, and
+//           a tile of N <= 256 has at most four k-blocks)
 //
 // The arithmetic per tile is that of tc_fxb_group_kernel: the same k-block
 // order, the same fold, the same slicing, so the results are bit-for-bit the
@@ -42,7 +46,8 @@ namespace persist {
 
 constexpr int BM = 128, BN = 64, BK = 64, THREADS = 384;
 constexpr int EW = 8;      // epilogue warps (4..11)
-constexpr int WC = BN / 2; // columns per epilogue thread
+constexpr int GW = 4;      // epilogue warps per group (one per TMEM lane quadrant)
+constexpr int WC = BN;     // columns per epilogue thread
 constexpr int KB_MAX = 64;  // N <= 4096
 constexpr int EXPB = 4;     // tiles staged ahead by warp 3 (one per group of 8 lanes)
 constexpr uint64_t WAIT_NS = 2000000000ull;
@@ -66,8 +71,9 @@ struct Cfg {
   static constexpr int NBUF = NSL == 3 ? 2 : 4;
   static constexpr int TMEM_COLS = 512;
   // barriers: full[S], empty[S], accfull[NBUF], accempty[NBUF], expfull[EXPB],
-  // expempty[EXPB], drain; then tmem slot, abort flag, epilogue verdict
-  static constexpr int NBARS = 2 * STAGES + 2 * NBUF + 2 * EXPB + 1;
+  // expempty[EXPB], drain, folded[2]; then tmem slot, abort flag, the two
+  // epilogue groups' verdicts
+  static constexpr int NBARS = 2 * STAGES + 2 * NBUF + 2 * EXPB + 1 + 2;
   static constexpr int BAR_BYTES = 256;
   static constexpr int EXP_INTS = 3 * KB_MAX;  // eA (2 block rows) + eB (1 block column)
   static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + BAR_BYTES + EXPB * EXP_INTS * 4 + 64 +
@@ -78,6 +84,11 @@ struct Cfg {
 };
 
 }  // namespace persist
+
+// Named barrier 1 + grp over the 4 warps of epilogue group grp.
+__device__ __forceinline__ void grp_bar(int grp) {
+  asm volatile("bar.sync %0, 128;" ::"r"(1 + grp) : "memory");
+}
 
 template <int NSL>
 __global__ void __launch_bounds__(persist::THREADS, 1)
@@ -92,9 +103,9 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
   uint64_t* bars = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
   uint32_t* tmem_slot = (uint32_t*)(bars + C::NBARS);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  volatile int* epi_ok = (volatile int*)(tmem_slot + 2);
+  volatile int* epi_ok = (volatile int*)(tmem_slot + 2);  // [2]: one verdict per epilogue group
   int* expbuf = (int*)((uint8_t*)bars + C::BAR_BYTES);  // [EXPB][EXP_INTS]
-  float* red = (float*)(expbuf + EXPB * C::EXP_INTS);   // 4 floats (16 slots)
+  float* red = (float*)(expbuf + EXPB * C::EXP_INTS);   // [2 groups][4 quadrants] (16 slots)
   TileInfo* info = (TileInfo*)(red + 16);                // [EXPB]
   const uint32_t full0 = ptx::smem_u32(bars);
   const uint32_t empty0 = ptx::smem_u32(bars + STAGES);
@@ -103,6 +114,8 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
   const uint32_t expfull0 = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF);
   const uint32_t expempty0 = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF + EXPB);
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF + 2 * EXPB);
+  // folded[g]: epilogue group g has folded every k-block of one of its tiles
+  const uint32_t folded0 = ptx::smem_u32(bars + 2 * STAGES + 2 * NBUF + 2 * EXPB + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
@@ -114,13 +127,14 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
     }
     for (int b = 0; b < NBUF; ++b) {
       ptx::mbar_init(accfull0 + 8 * b, 1);
-      ptx::mbar_init(accempty0 + 8 * b, EW);  // one arrival per epilogue warp
+      ptx::mbar_init(accempty0 + 8 * b, GW);  // one arrival per warp of the folding group
     }
     for (int b = 0; b < EXPB; ++b) {
       ptx::mbar_init(expfull0 + 8 * b, 8);     // the 8 lanes of one group of warp 3
-      ptx::mbar_init(expempty0 + 8 * b, 32 * EW);  // every epilogue thread
+      ptx::mbar_init(expempty0 + 8 * b, 32 * GW);  // every thread of the tile's epilogue group
     }
     ptx::mbar_init(drainb, 1);
+    for (int g = 0; g < 2; ++g) ptx::mbar_init(folded0 + 8 * g, GW);  // one arrival per warp of group g
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
@@ -276,18 +290,28 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
       ptx::mbar_arrive(expfull0 + 8 * e);  // release: this lane's writes are visible
     }
   } else if (warp >= 4) {
-    const int q = warp & 3;          // TMEM lane quadrant: rows 32 q .. 32 q + 31
-    const int h = q >> 1;            // the tile's 64-row block row
-    const int ch = (warp - 4) >> 2;  // columns 32 ch .. 32 ch + 31
-    const bool lead = warp == 4 && lane == 0;
+    const int grp = (warp - 4) / GW;  // this group takes the CTA's tiles grp, grp + 2, ...
+    const int q = warp & 3;           // TMEM lane quadrant: rows 32 q .. 32 q + 31
+    const int h = q >> 1;             // the tile's 64-row block row
+    const bool lead = q == 0 && lane == 0;
     float T[WC];
     for (int lt = 0;; ++lt) {
       const int tb = blockIdx.x + lt * G;
       if (tb >= tiles_total) break;
+      if ((lt & 1) != grp) {  // the other group's tile: its k-blocks pass by
+        gk += recs[tb].x >> 24;
+        continue;
+      }
       const int e = lt & (EXPB - 1);
       bool ok = true;
       int dummy = 0;
-      if (!ptx::mbar_wait(expfull0 + 8 * e, (lt / EXPB) & 1, &dummy, 2 * WAIT_NS)) ok = false;
+      // the other group has folded the tile before this one: every
+      // accumulator phase up to it has been consumed, so the accfull waits
+      // below are at most one phase ahead (a parity wait cannot tell phases
+      // further apart).  Its store phase still overlaps this tile's fold.
+      if (lt > 0 && !ptx::mbar_wait(folded0 + 8 * (grp ^ 1), ((lt - 1) >> 1) & 1, &dummy, 2 * WAIT_NS))
+        ok = false;
+      if (ok && !ptx::mbar_wait(expfull0 + 8 * e, (lt / EXPB) & 1, &dummy, 2 * WAIT_NS)) ok = false;
       const TileInfo ti = info[e];
       const int KB = ok ? ti.KB : 0;
       // the store phase's fields, loaded now and used after the fold (a
@@ -299,7 +323,7 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
       void* outp = d.out;
       long long* out_log2 = d.out_log2;
       const int row = ti.m0 + 32 * q + lane;
-      const int c0 = ti.n0 + WC * ch;
+      const int c0 = ti.n0;
       const int* eA = expbuf + e * C::EXP_INTS;
       const int* eB = eA + 2 * KB_MAX;
 #pragma unroll
@@ -308,59 +332,72 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
         const int buf = gk % NBUF;
         if (!ptx::mbar_wait(accfull0 + 8 * buf, (gk / NBUF) & 1, &dummy, 2 * WAIT_NS)) {
           ok = false;
+          gk += KB - kb;  // keep the set phases of the k-blocks that follow
           break;
         }
         ptx::tc_fence_after();
         const int kr = fxb::rot_kb(kb, KB, fxb::tile_rot(ti.m0, ti.n0, KB));
         const float f = fxb::pow2f(eA[h * KB + kr] + eB[kr] - 16 - ti.sx - ti.sy);
-        // the fold of fxb::fold on this thread's 32 columns: accumulator w at
-        // column offset w * BN of the k-block's set
-        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN + WC * ch);
-        uint32_t rm[32], rc[32];
-        ptx::tmem_ld_32x32b_x32(tq, rm);
-        ptx::tmem_ld_32x32b_x32(tq + BN, rc);
-        if (NSL == 3) {
-          uint32_t rd[32];
-          ptx::tmem_ld_32x32b_x32(tq + 2 * BN, rd);
-          ptx::tmem_ld_wait();
+        // the fold of fxb::fold on this thread's 64 columns, 32 at a time:
+        // accumulator w at column offset w * BN of the k-block's set; the set
+        // is released once its last columns are in registers
+        const uint32_t tq = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN);
+#pragma unroll
+        for (int c = 0; c < WC / 32; ++c) {
+          uint32_t rm[32], rc[32];
+          if (NSL == 3) {
+            uint32_t rd[32];
+            ptx::tmem_ld_32x32b_x32(tq + 32 * c + BN, rc);
+            ptx::tmem_ld_32x32b_x32(tq + 32 * c + 2 * BN, rd);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              rc[j] = __float_as_uint(fmaf(__uint_as_float(rd[j]), 0.00390625f, __uint_as_float(rc[j])));
+            ptx::tmem_ld_32x32b_x32(tq + 32 * c, rm);
+            ptx::tmem_ld_wait();
+          } else {
+            ptx::tmem_ld_32x32b_x32(tq + 32 * c, rm);
+            ptx::tmem_ld_32x32b_x32(tq + 32 * c + BN, rc);
+            ptx::tmem_ld_wait();
+          }
+          if (c == WC / 32 - 1) {
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);  // the set is in registers
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            rc[j] = __float_as_uint(fmaf(__uint_as_float(rd[j]), 0.00390625f, __uint_as_float(rc[j])));
-        } else {
-          ptx::tmem_ld_wait();
+            T[32 * c + j] =
+                fmaf(fmaf(__uint_as_float(rc[j]), 0.00390625f, __uint_as_float(rm[j])), f, T[32 * c + j]);
         }
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);  // the set is in registers
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          T[j] = fmaf(fmaf(__uint_as_float(rc[j]), 0.00390625f, __uint_as_float(rm[j])), f, T[j]);
       }
       ptx::mbar_arrive(expempty0 + 8 * e);  // this tile's exponents and record are no longer read
-      // one verdict for the epilogue warps (they share named barrier 1)
-      fxb::epi_bar<32 * EW>();
-      if (lead) *epi_ok = ok && !*abort_flag;
-      fxb::epi_bar<32 * EW>();
-      if (!*epi_ok) {
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(folded0 + 8 * grp);  // the next tile's group may fold
+      // one verdict for the group's warps (they share named barrier 1 + grp)
+      grp_bar(grp);
+      if (lead) epi_ok[grp] = ok && !*abort_flag;
+      grp_bar(grp);
+      if (!epi_ok[grp]) {
         *abort_flag = 1;
         break;
       }
       const bool first = ti.m0 == 0 && ti.n0 == 0;  // tile 0 of its product
       if (mode == OUT_INTERNAL) {
         if (first && lead) scales[sc].E = ti.Ec;
-        // block maximum of the 64 x 64 block (rows of quadrants 2h, 2h + 1,
-        // both column halves), its exponent, then this thread's slices
+        // block maximum of the 64 x 64 block (rows of quadrants 2h, 2h + 1),
+        // its exponent, then this thread's slices
         float m = 0.f;
 #pragma unroll
         for (int j = 0; j < WC; ++j) m = fmaxf(m, fabsf(T[j]));
         m = warp_max(m);
-        if (lane == 0) red[2 * q + ch] = m;
-        fxb::epi_bar<32 * EW>();
-        const float bm = fmaxf(fmaxf(red[4 * h], red[4 * h + 1]), fmaxf(red[4 * h + 2], red[4 * h + 3]));
+        if (lane == 0) red[4 * grp + q] = m;
+        grp_bar(grp);
+        const float bm = fmaxf(red[4 * grp + 2 * h], red[4 * grp + 2 * h + 1]);
         const int ex = fxb::frexp_exp(bm);
         const int nb = fxb::nblocks(N);
         const int I = ti.m0 / fxb::BLK + h, J = ti.n0 / fxb::BLK;
-        if ((q & 1) == 0 && ch == 0 && lane == 0 && I < nb && J < nb) {
+        if ((q & 1) == 0 && lane == 0 && I < nb && J < nb) {
           ((int*)((char*)Cp + fxb::bexp_offset(N, ld, NSL)))[I * nb + J] = ex;
           if (bm > 0.f) atomicMax(&scales[sc].maxbits, __float_as_uint(bm));
         }
@@ -390,7 +427,7 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
             }
           }
         }
-        fxb::epi_bar<32 * EW>();  // red may be reused
+        grp_bar(grp);  // red may be reused
       } else {
         if (first && lead && mode == OUT_USER_MANT && out_log2) *out_log2 = ti.Ec;
         if (row < N)
