@@ -240,7 +240,10 @@ __device__ __forceinline__ void chain_finish(float (&T)[BN], bool ok, volatile i
              // read them after the grid barrier)
       fxb::store_slices<BN, NT, NSL>(T, row, m0, n0, q, lane, N, Q.ld, (__nv_bfloat16*)Q.slices[op.cb], Q.plane,
                                      Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered);
-    __threadfence();  // this thread's stores are visible GPU-wide before the barrier
+    // the next level's TMA reads these stores after the grid barrier, whose
+    // __syncthreads and single fenced arrival make every thread's stores
+    // visible GPU-wide (as for the prep's stores); the proxy fence orders
+    // them before async-proxy reads
     fence_proxy_async_global();
   }
 }
