@@ -174,6 +174,64 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
   epi_bar<NT>();  // red may be reused
 }
 
+// store_slices for epilogue threads that each hold WC (32 or 64) of a
+// tile's columns: T is row `row` of the tile at columns c0 .. c0 + WC - 1
+// (c0 = the tile's n0 + cs WC, cs the thread's column part).  A 64 x 64
+// block's maximum is reduced over the warps that hold it -- the quadrant
+// pair (q, q ^ 1) and, for WC = 32, both column halves -- through red
+// (8 floats per 64-column block of the tile); then the block exponent, the
+// matrix maximum and this thread's slices as in store_slices.  NT epilogue
+// threads share named barrier 1.
+template <int WC, int NT, int NSL>
+__device__ __forceinline__ void store_slices_part(const float (&T)[WC], int row, int m0, int n0, int c0, int q,
+                                                  int cs, int lane, int N, int ld, __nv_bfloat16* a1p,
+                                                  long long plane, int* bexp, unsigned* maxbits, float* red) {
+  static_assert(WC == 32 || WC == 64, "column part");
+  constexpr int NPART = 64 / WC;  // column parts per 64-column block
+  const int gblk = (c0 - n0) / BLK;  // this thread's block within the tile
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < WC; ++j) m = fmaxf(m, fabsf(T[j]));
+  m = warp_max(m);
+  if (lane == 0) red[gblk * 8 + q * NPART + (NPART == 2 ? (cs & 1) : 0)] = m;
+  epi_bar<NT>();
+  const int nb = nblocks(N);
+  const int I = m0 / BLK + (q >> 1);
+  float bm = fmaxf(red[gblk * 8 + q * NPART], red[gblk * 8 + (q ^ 1) * NPART]);
+  if (NPART == 2) bm = fmaxf(bm, fmaxf(red[gblk * 8 + q * NPART + 1], red[gblk * 8 + (q ^ 1) * NPART + 1]));
+  const int e = frexp_exp(bm);
+  const int J = n0 / BLK + gblk;
+  if ((q & 1) == 0 && lane == 0 && (NPART == 1 || (cs & 1) == 0) && I < nb && J < nb) {
+    bexp[I * nb + J] = e;
+    if (bm > 0.f) atomicMax(maxbits, __float_as_uint(bm));
+  }
+  if (row < N) {
+    // 16-byte groups of 8 columns, as in store_slices
+    __nv_bfloat16* p1 = a1p + (size_t)row * ld + c0;
+#pragma unroll
+    for (int g8 = 0; g8 < WC / 8; ++g8) {
+      if (c0 + 8 * g8 < N) {
+        uint32_t w[NSL][4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          float x0[NSL], x1[NSL];
+          slice_n<NSL>(T[8 * g8 + 2 * h], e, x0);
+          slice_n<NSL>(T[8 * g8 + 2 * h + 1], e, x1);
+#pragma unroll
+          for (int k = 0; k < NSL; ++k) {
+            __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
+            w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NSL; ++k)
+          *reinterpret_cast<uint4*>(p1 + k * plane + 8 * g8) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
+      }
+    }
+  }
+  epi_bar<NT>();  // red may be reused
+}
+
 // Like store_slices, but the slice planes leave through TMA: each epilogue
 // thread writes its row of every 64-column box into shared memory in the
 // 128-byte-swizzled layout the tensor map expects (16-byte chunk c of row r at
@@ -250,10 +308,10 @@ __device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, in
 }
 
 // Fold one finished k-block into T with the block factors fac[g] (one per 64
-// columns).  Accumulator k (0: main, 1: weight 2^-8, 2: weight 2^-16) sits at
-// TMEM column tq + k * acc_stride.
+// columns; BN = 32 takes fac[0]).  Accumulator k (0: main, 1: weight 2^-8,
+// 2: weight 2^-16) sits at TMEM column tq + k * acc_stride.
 template <int BN, int NSL = 2>
-__device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&fac)[BN / BLK],
+__device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float* fac,
                                      uint32_t acc_stride = BN) {
 #pragma unroll
   for (int c = 0; c < BN / 32; ++c) {
@@ -279,26 +337,37 @@ __device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float (&
 }
 
 // One 64 x 64 block (I, J) of a float32 matrix A (leading dimension N) split
-// into the stored format by a CTA of 256 threads: block exponent, slices,
-// matrix maximum, non-finite check.  red: 8 floats of shared scratch.
+// into the stored format by the first 256 threads of the CTA (any further
+// threads take part in its barriers only): block exponent, slices, matrix
+// maximum, non-finite check.  red: 8 floats of shared scratch.  In two
+// steps: prep_load reads this thread's 16 values of the block (so that a
+// kernel can start the reads early), prep_split does the rest; prep_block
+// runs both.
+__device__ __forceinline__ void prep_load(const float* __restrict__ A, int N, int I, int J, float (&v)[16]) {
+  const int tid = threadIdx.x;
+  const int r = tid < 256 ? I * BLK + (tid >> 2) : N;  // idle threads: past the last row
+  const int c0 = J * BLK + (tid & 3) * 16;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = (r < N && c0 + j < N) ? A[(size_t)r * N + c0 + j] : 0.f;
+}
+
 template <int NSL = 2>
-__device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, int ld, int I, int J,
+__device__ __forceinline__ void prep_split(const float (&v)[16], int N, int ld, int I, int J,
                                            __nv_bfloat16* a1p, long long plane, int* bexp,
                                            unsigned* maxbits, unsigned* status, float* red) {
   const int tid = threadIdx.x;
-  const int r = I * BLK + (tid >> 2);
+  const bool act = tid < 256;
+  const int r = act ? I * BLK + (tid >> 2) : N;
   const int c0 = J * BLK + (tid & 3) * 16;
-  float v[16];
   float m = 0.f;
   bool bad = false;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    v[j] = (r < N && c0 + j < N) ? A[(size_t)r * N + c0 + j] : 0.f;
     bad |= !isfinite(v[j]);
     m = fmaxf(m, fabsf(v[j]));
   }
   m = warp_max(m);
-  if ((tid & 31) == 0) red[tid >> 5] = m;
+  if (act && (tid & 31) == 0) red[tid >> 5] = m;
   if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_BADINPUT);
   float bm = red[0];
 #pragma unroll
@@ -343,6 +412,15 @@ __device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, i
     }
   }
   __syncthreads();  // red may be reused
+}
+
+template <int NSL = 2>
+__device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, int ld, int I, int J,
+                                           __nv_bfloat16* a1p, long long plane, int* bexp,
+                                           unsigned* maxbits, unsigned* status, float* red) {
+  float v[16];
+  prep_load(A, N, I, J, v);
+  prep_split<NSL>(v, N, ld, I, J, a1p, plane, bexp, maxbits, status, red);
 }
 
 // Exponent table of one tile, staged in shared memory by warp 3:

@@ -43,7 +43,9 @@
 namespace mp {
 
 namespace chain {
-constexpr int BM = 128, BK = 64, THREADS = 256, CHUNK_KB = 4;
+// warps 0-3: TMA, MMA, TMEM allocation, exponent staging; warps 4-11: the
+// epilogue, warp 4 + 4 cs + q holding rows 32q.. and columns half cs of the tile
+constexpr int BM = 128, BK = 64, THREADS = 384, NEPI = 256, CHUNK_KB = 4;
 constexpr int MAX_LEVELS = 64;
 constexpr uint64_t WAIT_NS = 2000000000ull;
 // dynamic shared memory: the 227 KB per CTA less the per-level work table
@@ -207,39 +209,32 @@ struct LevelWork {
 static_assert(sizeof(LevelWork) * chain::MAX_LEVELS <= chain::WORK_BYTES, "work table");
 
 // The end of a tile's level work by the NT epilogue threads that own its rows
-// (q_first: the first of their warps): one verdict over them, then the user
-// output (final product) or the next operand's block exponents and slices.
-template <int BN, int NSL, int NT>
-__device__ __forceinline__ void chain_finish(float (&T)[BN], bool ok, volatile int* epi_ok,
-                                             volatile int* abort_flag, int q, int lane, int row, int t, int m0,
-                                             int n0, int N, const ChainProblem& Q, const chain::Op& op,
+// (q_first: the first of their row quadrants; each thread holds WC columns
+// from c0 = n0 + cs WC): one verdict over them, then the user output (final
+// product) or the next operand's block exponents and slices.
+template <int WC, int NSL, int NT>
+__device__ __forceinline__ void chain_finish(float (&T)[WC], bool ok, volatile int* epi_ok,
+                                             volatile int* abort_flag, int q, int cs, int lane, int row, int t,
+                                             int m0, int n0, int N, const ChainProblem& Q, const chain::Op& op,
                                              long long Ec, unsigned* status, float* ered, int q_first) {
+  const int c0 = n0 + cs * WC;
+  const bool first = cs == 0 && lane == 0;
   fxb::epi_bar<NT>();
-  if (q == q_first && lane == 0) *epi_ok = ok && !*abort_flag;
+  if (q == q_first && first) *epi_ok = ok && !*abort_flag;
   fxb::epi_bar<NT>();
   ok = *epi_ok != 0;
   if (op.last) {
     if (ok) {
-      if (t == 0 && q == 0 && lane == 0 && Q.out_log2) *Q.out_log2 = Ec;
-      if (row < N) {
-        float* O = Q.out + (size_t)row * N;
-        if constexpr (BN == 64) {  // 16-byte stores where the rows allow
-          store_row_f32<BN>(T, O, n0, N, Q.out_log2 != nullptr, Ec, status, Q.out);
-        } else {
-#pragma unroll
-          for (int j = 0; j < BN; ++j) {
-            const int c = n0 + j;
-            if (c < N) O[c] = Q.out_log2 ? T[j] : final_value(T[j], Ec, status);
-          }
-        }
-      }
+      if (t == 0 && q == 0 && first && Q.out_log2) *Q.out_log2 = Ec;
+      // 16-byte stores where the rows allow
+      if (row < N) store_row_f32<WC>(T, Q.out + (size_t)row * N, c0, N, Q.out_log2 != nullptr, Ec, status, Q.out);
     }
   } else {
-    if (t == 0 && q == 0 && lane == 0) Q.scales[op.sc].E = Ec;
+    if (t == 0 && q == 0 && first) Q.scales[op.sc].E = Ec;
     if (ok)  // 16-byte stores straight from registers (the next level's copies
              // read them after the grid barrier)
-      fxb::store_slices<BN, NT, NSL>(T, row, m0, n0, q, lane, N, Q.ld, (__nv_bfloat16*)Q.slices[op.cb], Q.plane,
-                                     Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered);
+      fxb::store_slices_part<WC, NT, NSL>(T, row, m0, n0, c0, q, cs, lane, N, Q.ld, (__nv_bfloat16*)Q.slices[op.cb],
+                                          Q.plane, Q.bexp[op.cb], &Q.scales[op.sc].maxbits, ered);
     // the next level's TMA reads these stores after the grid barrier, whose
     // __syncthreads and single fenced arrival make every thread's stores
     // visible GPU-wide (as for the prep's stores); the proxy fence orders
@@ -256,17 +251,23 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* bars = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
-  // full[S], empty[S], accfull[2], accempty[2], drain
+  // full[S], empty[S], accfull[2], accempty[2], drain, (tmem_slot, flags,
+  // red), xbar, full2[S]: full completes with a stage's first A slice and
+  // its B slices, full2 with the other A slices
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   volatile int* epi_ok = (volatile int*)(tmem_slot + 2);
   float* red = (float*)(tmem_slot + 4);  // 8 floats
   constexpr int NG = C::NG;
+  constexpr int WC = BN / 2;              // columns of one epilogue thread
+  constexpr int NGW = WC < 64 ? 1 : WC / 64;  // its 64-column blocks
   int* eA = (int*)(smem + STAGES * C::STAGE_BYTES + 256);
   int* eB = eA + 2 * C::KB_MAX;
   float* ered = (float*)(eB + NG * C::KB_MAX);
   // split-K: partial tiles pushed by the other CTAs of the cluster, as
   // float4 [rank - 1][BN / 4][128 rows]; xbar completes once per level
+  // ((S - 1) x NEPI arrivals: pushing threads arrive with weights that
+  // complete it for every split factor)
   float4* xbuf = (float4*)(smem + STAGES * C::STAGE_BYTES + C::XOFF);
   const uint32_t xbar = ptx::smem_u32(bars + 2 * STAGES + 5 + 8);  // past tmem_slot..red
   const uint32_t full0 = ptx::smem_u32(bars);
@@ -274,10 +275,27 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   const uint32_t accfull0 = ptx::smem_u32(bars + 2 * STAGES);
   const uint32_t accempty0 = ptx::smem_u32(bars + 2 * STAGES + 2);
   const uint32_t drainb = ptx::smem_u32(bars + 2 * STAGES + 4);
+  const uint32_t full2_0 = ptx::smem_u32(bars + 2 * STAGES + 14);
+  static_assert((3 * STAGES + 14) * 8 <= 256, "barrier area");
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned G = gridDim.x;
   unsigned bar_no = 0;
+
+  // the reads of this CTA's first two prep blocks go out before the setup
+  float pv[2][16];
+  const int n_prep = P.prep_begin[P.nprob];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int b = blockIdx.x + i * G;
+    if (b < n_prep) {
+      int pi = 0;
+      while (pi + 1 < P.nprob && b >= P.prep_begin[pi + 1]) ++pi;
+      const int nb = fxb::nblocks(P.pr[pi].N);
+      const int lb = b - P.prep_begin[pi];
+      fxb::prep_load(P.pr[pi].A, P.pr[pi].N, lb / nb, lb % nb, pv[i]);
+    }
+  }
   // split-K needs the launch's clusters of S; launched without them (each CTA
   // its own cluster), every CTA computes whole tiles
   const bool clustered = S > 1 && cluster_nctarank() == (uint32_t)S;
@@ -286,14 +304,15 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       ptx::mbar_init(full0 + 8 * s, 1);
+      ptx::mbar_init(full2_0 + 8 * s, 1);
       ptx::mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(accfull0 + 8 * b, 1);
-      ptx::mbar_init(accempty0 + 8 * b, 4);
+      ptx::mbar_init(accempty0 + 8 * b, NEPI / 32);
     }
     ptx::mbar_init(drainb, 1);
-    if (clustered) ptx::mbar_init(xbar, (S - 1) * 128);
+    if (clustered) ptx::mbar_init(xbar, (S - 1) * NEPI);
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
@@ -358,14 +377,19 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   // ---- prep: block-scaled exact split of each A into its buffer 0, max|A|
   // into its slot 1
   {
-    for (int b = blockIdx.x; b < P.prep_begin[P.nprob]; b += G) {
+    int i = 0;
+    for (int b = blockIdx.x; b < n_prep; b += G, ++i) {
       int pi = 0;
       while (pi + 1 < P.nprob && b >= P.prep_begin[pi + 1]) ++pi;
       const ChainProblem& Q = P.pr[pi];
       const int nb = fxb::nblocks(Q.N);
       const int lb = b - P.prep_begin[pi];
-      fxb::prep_block<NSL>(Q.A, Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0], Q.plane, Q.bexp[0],
-                           &Q.scales[1].maxbits, P.status, red);
+      if (i < 2)
+        fxb::prep_split<NSL>(i == 0 ? pv[0] : pv[1], Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0],
+                             Q.plane, Q.bexp[0], &Q.scales[1].maxbits, P.status, red);
+      else
+        fxb::prep_block<NSL>(Q.A, Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0], Q.plane, Q.bexp[0],
+                             &Q.scales[1].maxbits, P.status, red);
     }
     fence_proxy_async_global();
   }
@@ -374,7 +398,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
 
   int kb_base = 0;  // k-blocks done by this CTA: ring and accumulator-buffer phases
   uint32_t xph = 0;  // phase of xbar (leader)
-  float T[BN];
+  float T[WC];
   for (int L = 0; L < P.nlevels && !*abort_flag; ++L) {
     // this CTA's work at level L, worked out at kernel start
     const LevelWork W = s_work[L];
@@ -392,7 +416,8 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
     const int i0 = rank * KB / f, i1 = (rank + 1) * KB / f;
     const int nkb = i1 - i0;
     const int m0 = W.m0, n0 = W.n0;
-    const int q = warp - 4;
+    const int q = (warp - 4) & 3;    // TMEM lane quadrant: rows 32q .. 32q + 31
+    const int cs = (warp - 4) >> 2;  // column half of the tile
     const int row = m0 + 32 * q + lane;
 
     if (has) {
@@ -406,13 +431,14 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
               *abort_flag = 1;
               break;
             }
-            const uint32_t fb = full0 + 8 * s;
-            ptx::mbar_expect_tx(fb, C::STAGE_BYTES);
+            // the first A slice and the B slices (the first MMAs' operands)
+            // on full, the other A slices on full2
+            const uint32_t fb = full0 + 8 * s, fb2 = full2_0 + 8 * s;
+            ptx::mbar_expect_tx(fb, C::A_BYTES + NSL * C::B_BYTES);
+            ptx::mbar_expect_tx(fb2, (NSL - 1) * C::A_BYTES);
             const uint32_t base = ptx::smem_u32(smem + s * C::STAGE_BYTES);
             const int kx = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB)) * BK;
-#pragma unroll
-            for (int k = 0; k < NSL; ++k)
-              ptx::tma_load_2d(base + k * C::A_BYTES, &Q.amap[op.xb][k], kx, m0, fb);
+            ptx::tma_load_2d(base, &Q.amap[op.xb][0], kx, m0, fb);
             const uint32_t bbase = base + NSL * C::A_BYTES;
 #pragma unroll
             for (int c = 0; c < BN / 64; ++c)
@@ -420,6 +446,9 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
               for (int k = 0; k < NSL; ++k)
                 ptx::tma_load_2d(bbase + k * C::B_BYTES + c * 8192, &Q.bmap[op.yb][k], n0 + 64 * c, kx,
                                  fb);
+#pragma unroll
+            for (int k = 1; k < NSL; ++k)
+              ptx::tma_load_2d(base + k * C::A_BYTES, &Q.amap[op.xb][k], kx, m0, fb2);
           }
         }
       } else if (warp == 1) {
@@ -433,24 +462,34 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
               break;
             }
             const int s = g % STAGES;
-            if (!ptx::mbar_wait(full0 + 8 * s, (g / STAGES) & 1, abort_flag, WAIT_NS)) {
+            const uint32_t ph = (g / STAGES) & 1;
+            if (!ptx::mbar_wait(full0 + 8 * s, ph, abort_flag, WAIT_NS)) {
               *abort_flag = 1;
               break;
             }
             ptx::tc_fence_after();
             const uint32_t a0 = ptx::smem_u32(smem + s * C::STAGE_BYTES);
             const uint32_t b0 = a0 + NSL * C::A_BYTES;
+            // slice-major: a_0 [b_0 | ... ] over the four k-steps (the k-step-0
+            // MMA initialises every accumulator), then, once full2 completes,
+            // a_i [b_0 | ... | b_(NSL-1-i)] for i >= 1.  The accumulators hold
+            // exact integer sums, so this order gives fxb::slice_mmas' results.
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k) {
-              uint64_t ad[NSL], bd[NSL];
-#pragma unroll
-              for (int i = 0; i < NSL; ++i) {
-                ad[i] = ptx::smem_desc(a0 + i * C::A_BYTES + 32 * k, 16, 1024);
-                bd[i] = ptx::smem_desc(b0 + i * C::B_BYTES + 2048 * k, 8192, 1024);
-              }
-              const uint32_t acc = k == 0 ? 0u : 1u;
-              fxb::slice_mmas<BN, NSL>(t0, ad, bd[0], acc);
+            for (int k = 0; k < BK / 16; ++k)
+              ptx::mma_f16(t0, ptx::smem_desc(a0 + 32 * k, 16, 1024),
+                           ptx::smem_desc(b0 + 2048 * k, 8192, 1024), idesc_bf16(128, NSL * BN),
+                           k == 0 ? 0u : 1u);
+            if (!ptx::mbar_wait(full2_0 + 8 * s, ph, abort_flag, WAIT_NS)) {
+              *abort_flag = 1;
+              break;
             }
+            ptx::tc_fence_after();
+#pragma unroll
+            for (int i = 1; i < NSL; ++i)
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                ptx::mma_f16(t0 + (uint32_t)(i * BN), ptx::smem_desc(a0 + i * C::A_BYTES + 32 * k, 16, 1024),
+                             ptx::smem_desc(b0 + 2048 * k, 8192, 1024), idesc_bf16(128, (NSL - i) * BN), 1u);
             ptx::mma_commit(empty0 + 8 * s);
             ptx::mma_commit(accfull0 + 8 * buf);
           }
@@ -458,7 +497,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
       } else if (warp == 3) {
         fxb::load_tile_exponents<BN>(Q.bexp[op.xb], Q.bexp[op.yb], N, m0, n0, KB, eA, eB, lane);
         __syncwarp();
-        asm volatile("bar.arrive 2, 160;" ::: "memory");
+        asm volatile("bar.arrive 2, %0;" ::"n"(32 + NEPI) : "memory");
       } else if (warp >= 4) {
         const int h = q >> 1;
         // scale slots are written by other CTAs: read them from L2, not L1
@@ -466,8 +505,9 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
         const int sy = scale_exp_from_bits(__ldcg(&Q.scales[op.sy].maxbits));
         const long long Ec = __ldcg(&Q.scales[op.sx].E) + __ldcg(&Q.scales[op.sy].E) + sx + sy;
 #pragma unroll
-        for (int j = 0; j < BN; ++j) T[j] = 0.f;
-        asm volatile("bar.sync 2, 160;" ::: "memory");  // exponents staged
+        for (int j = 0; j < WC; ++j) T[j] = 0.f;
+        asm volatile("bar.sync 2, %0;" ::"n"(32 + NEPI) : "memory");  // exponents staged
+        const int gb0 = cs * WC / 64;  // first 64-column block of this thread's columns
         bool ok = true;
         for (int kb = i0; kb < i1; ++kb) {
           const int g = kb_base + kb - i0;
@@ -480,17 +520,18 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           }
           ptx::tc_fence_after();
           const int kr = fxb::rot_kb(kb, KB, fxb::tile_rot(m0, n0, KB));
-          float fac[NG];
+          float fac[NGW];
 #pragma unroll
-          for (int gg = 0; gg < NG; ++gg)
-            fac[gg] = fxb::pow2f(eA[h * KB + kr] + eB[kr * NG + gg] - 16 - sx - sy);
-          fxb::fold<BN, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN), fac,
+          for (int gg = 0; gg < NGW; ++gg)
+            fac[gg] = fxb::pow2f(eA[h * KB + kr] + eB[kr * NG + gb0 + gg] - 16 - sx - sy);
+          fxb::fold<WC, NSL>(T, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * NSL * BN + cs * WC), fac,
                              BN);
           ptx::tc_fence_before();
           __syncwarp();
           if (lane == 0) ptx::mbar_arrive(accempty0 + 8 * buf);
         }
-        const int et = 32 * q + lane;  // epilogue thread = tile row
+        const int et = 32 * q + lane;  // tile row
+        const int cq0 = cs * WC / 4;   // this thread's first float4 column
         // f = 2: the two CTAs of the tile each finish one 64-row block row
         // (warps q with q / 2 = rank) and send the other rows to the partner;
         // f = 4: the group's first CTA gathers the other three partial tiles
@@ -499,13 +540,12 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
         if (rows2) {
           if (!mine) {
             // this row belongs to the partner's block row: push it there
-            // (weighted: 64 pushing threads complete the barrier, which is
-            // initialised for (S - 1) x 128 arrivals)
+            // (weighted: NEPI / 2 pushing threads complete the barrier)
             const uint32_t prt = (uint32_t)(lead_rank + 1 - rank);
             const uint32_t dst = mapa_rank(ptx::smem_u32(xbuf), prt);
 #pragma unroll
-            for (int c = 0; c < BN / 4; ++c)
-              st_cluster_v4(dst + (uint32_t)((c * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
+            for (int c = 0; c < WC / 4; ++c)
+              st_cluster_v4(dst + (uint32_t)(((cq0 + c) * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
                             T[4 * c + 3]);
             mbar_arrive_remote(mapa_rank(xbar, prt), (uint32_t)(2 * (S - 1)));
           } else {
@@ -514,9 +554,9 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
               ok = false;
             }
             if (ok) {
-              const float4* src = xbuf + et;
+              const float4* src = xbuf + cq0 * 128 + et;
 #pragma unroll
-              for (int c = 0; c < BN / 4; ++c) {
+              for (int c = 0; c < WC / 4; ++c) {
                 const float4 v = src[c * 128];
                 T[4 * c] += v.x;
                 T[4 * c + 1] += v.y;
@@ -533,8 +573,8 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           const uint32_t dst =
               mapa_rank(ptx::smem_u32(xbuf + (size_t)(rank - 1) * (BN / 4) * 128), (uint32_t)lead_rank);
 #pragma unroll
-          for (int c = 0; c < BN / 4; ++c)
-            st_cluster_v4(dst + (uint32_t)((c * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
+          for (int c = 0; c < WC / 4; ++c)
+            st_cluster_v4(dst + (uint32_t)(((cq0 + c) * 128 + et) * 16), T[4 * c], T[4 * c + 1], T[4 * c + 2],
                           T[4 * c + 3]);
           mbar_arrive_remote(mapa_rank(xbar, (uint32_t)lead_rank), (uint32_t)((S - 1) / (f - 1)));
         } else if (f > 1) {
@@ -547,9 +587,9 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           if (ok) {
 #pragma unroll 1
             for (int r = 1; r < f; ++r) {
-              const float4* src = xbuf + (size_t)(r - 1) * (BN / 4) * 128 + et;
+              const float4* src = xbuf + (size_t)(r - 1) * (BN / 4) * 128 + cq0 * 128 + et;
 #pragma unroll
-              for (int c = 0; c < BN / 4; ++c) {
+              for (int c = 0; c < WC / 4; ++c) {
                 const float4 v = src[c * 128];
                 T[4 * c] += v.x;
                 T[4 * c + 1] += v.y;
@@ -560,12 +600,12 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
           }
         }
         if (mine) {
-          if (rows2)  // two warps (one block row) share the named barriers
-            chain_finish<BN, NSL, 64>(T, ok, epi_ok, abort_flag, q, lane, row, t, m0, n0, N, Q, op, Ec,
-                                      P.status, ered, 2 * rank);
+          if (rows2)  // four warps (one block row) share the named barriers
+            chain_finish<WC, NSL, NEPI / 2>(T, ok, epi_ok, abort_flag, q, cs, lane, row, t, m0, n0, N, Q, op, Ec,
+                                            P.status, ered, 2 * rank);
           else
-            chain_finish<BN, NSL, 128>(T, ok, epi_ok, abort_flag, q, lane, row, t, m0, n0, N, Q, op, Ec,
-                                       P.status, ered, 0);
+            chain_finish<WC, NSL, NEPI>(T, ok, epi_ok, abort_flag, q, cs, lane, row, t, m0, n0, N, Q, op, Ec,
+                                        P.status, ered, 0);
         }
       }
       kb_base += nkb;  // ring and accumulator counters advance only with work done
@@ -581,6 +621,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
     for (int g = kb_base - STAGES < 0 ? 0 : kb_base - STAGES; g < kb_base; ++g) {
       int dummy = 0;
       ptx::mbar_wait(full0 + 8 * (g % STAGES), (g / STAGES) & 1, &dummy, WAIT_NS);
+      ptx::mbar_wait(full2_0 + 8 * (g % STAGES), (g / STAGES) & 1, &dummy, WAIT_NS);
     }
   }
   if (warp == 1 && lane == 0) {
