@@ -70,6 +70,14 @@ __device__ __forceinline__ int tile_rot(int m0, int n0, int KB) { return KB > 32
 
 __device__ __forceinline__ int frexp_exp(float m) { return scale_exp_from_bits(__float_as_uint(m)); }
 
+// The bfloat16 pair (x0 low, x1 high) of two floats whose values are exact in
+// bfloat16 (the integer slices: at most 8 significant bits), so that their
+// low 16 bits are zero and rounding changes nothing: the upper halves, one
+// byte permute instead of a conversion.
+__device__ __forceinline__ uint32_t pack_bf16_exact(float x0, float x1) {
+  return __byte_perm(__float_as_uint(x0), __float_as_uint(x1), 0x7632);
+}
+
 __device__ __forceinline__ void slice(float v, int e, float* h, float* l) {
   const float u = mul_pow2(v, 8 - e);
   *h = rintf(u);
@@ -160,8 +168,7 @@ __device__ __forceinline__ void store_slices(const float (&T)[BN], int row, int 
             slice_n<NSL>(T[BLK * g + 8 * g8 + 2 * h + 1], e, x1);
 #pragma unroll
             for (int k = 0; k < NSL; ++k) {
-              __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
-              w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+              w[k][h] = pack_bf16_exact(x0[k], x1[k]);
             }
           }
 #pragma unroll
@@ -219,8 +226,7 @@ __device__ __forceinline__ void store_slices_part(const float (&T)[WC], int row,
           slice_n<NSL>(T[8 * g8 + 2 * h + 1], e, x1);
 #pragma unroll
           for (int k = 0; k < NSL; ++k) {
-            __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
-            w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+            w[k][h] = pack_bf16_exact(x0[k], x1[k]);
           }
         }
 #pragma unroll
@@ -282,8 +288,7 @@ __device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, in
         slice_n<NSL>(T[BLK * g + 8 * c + 2 * h + 1], e, x1);
 #pragma unroll
         for (int k = 0; k < NSL; ++k) {
-          __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
-          w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+          w[k][h] = pack_bf16_exact(x0[k], x1[k]);
         }
       }
       const int pos = (c ^ (r & 7)) * 16;
@@ -305,6 +310,32 @@ __device__ __forceinline__ void store_slices_tma(const float (&T)[WC], int r, in
     ptx::fence_proxy_async_global();
   }
   epi_bar<NT>();  // the stage and red may be reused
+}
+
+// Transpose of 8 x 8 chunks of 8 floats within each group of 8 lanes (lane
+// i = lane % 8 of group g = lane / 8), by three butterfly exchanges of half
+// the chunks with the lane at distance 4, 2, 1.  Before: T[8 c + r] is
+// element r of chunk c of the lane's own row.  After: T[8 j + r] is element
+// r of chunk i of the row held by lane 8 g + j.  Every lane of the warp must
+// take part.
+__device__ __forceinline__ void transpose8x8(float (&T)[64], int lane) {
+#pragma unroll
+  for (int s = 4; s >= 1; s >>= 1) {
+    const bool hi = (lane & s) != 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c & s) continue;  // chunk pair (c, c | s)
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float send = hi ? T[8 * c + r] : T[8 * (c | s) + r];
+        const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+        if (hi)
+          T[8 * c + r] = recv;
+        else
+          T[8 * (c | s) + r] = recv;
+      }
+    }
+  }
 }
 
 // Fold one finished k-block into T with the block factors fac[g] (one per 64
@@ -391,8 +422,7 @@ __device__ __forceinline__ void prep_split(const float (&v)[16], int N, int ld, 
           slice_n<NSL>(v[8 * g8 + 2 * h + 1], e, x1);
 #pragma unroll
           for (int k = 0; k < NSL; ++k) {
-            __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
-            w[k][h] = *reinterpret_cast<uint32_t*>(&v2);
+            w[k][h] = pack_bf16_exact(x0[k], x1[k]);
           }
         }
 #pragma unroll

@@ -401,30 +401,35 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
           ((int*)((char*)Cp + fxb::bexp_offset(N, ld, NSL)))[I * nb + J] = ex;
           if (bm > 0.f) atomicMax(&scales[sc].maxbits, __float_as_uint(bm));
         }
-        if (row < N) {
-          // 16-byte groups of 8 columns; a group that starts below N ends
-          // within the row's padding to ld (a multiple of 8), which no
-          // product reads, and its columns past N hold exact zeros
-          __nv_bfloat16* p1 = (__nv_bfloat16*)Cp + (size_t)row * ld + c0;
+        // the stores: a lane holding a row would put each 16-byte store of a
+        // warp on its own cache line (32 lines per instruction, which the
+        // L1 data path shares with the next tile's copies and MMA operand
+        // reads); transposed within 8-lane groups, lane 8 g + i holds
+        // columns c0 + 8 i .. + 7 of rows 32 q + 8 g + j (j = 0..7), and a
+        // warp store covers 4 rows x 128 contiguous bytes.  A group that
+        // starts below N ends within the row's padding to ld (a multiple of
+        // 8), which no product reads, and its columns past N hold exact zeros
+        fxb::transpose8x8(T, lane);
+        const int col = c0 + 8 * (lane & 7);
+        const int r0 = ti.m0 + 32 * q + 8 * (lane >> 3);
 #pragma unroll
-          for (int g8 = 0; g8 < WC / 8; ++g8) {
-            if (c0 + 8 * g8 < N) {
-              uint32_t w[NSL][4];
+        for (int j = 0; j < 8; ++j) {
+          if (r0 + j < N && col < N) {
+            uint32_t w[NSL][4];
 #pragma unroll
-              for (int hh = 0; hh < 4; ++hh) {
-                float x0[NSL], x1[NSL];
-                fxb::slice_n<NSL>(T[8 * g8 + 2 * hh], ex, x0);
-                fxb::slice_n<NSL>(T[8 * g8 + 2 * hh + 1], ex, x1);
+            for (int hh = 0; hh < 4; ++hh) {
+              float x0[NSL], x1[NSL];
+              fxb::slice_n<NSL>(T[8 * j + 2 * hh], ex, x0);
+              fxb::slice_n<NSL>(T[8 * j + 2 * hh + 1], ex, x1);
 #pragma unroll
-                for (int k = 0; k < NSL; ++k) {
-                  __nv_bfloat162 v2 = __floats2bfloat162_rn(x0[k], x1[k]);
-                  w[k][hh] = *reinterpret_cast<uint32_t*>(&v2);
-                }
+              for (int k = 0; k < NSL; ++k) {
+                w[k][hh] = fxb::pack_bf16_exact(x0[k], x1[k]);
               }
-#pragma unroll
-              for (int k = 0; k < NSL; ++k)
-                *reinterpret_cast<uint4*>(p1 + k * plane + 8 * g8) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
             }
+            __nv_bfloat16* p1 = (__nv_bfloat16*)Cp + (size_t)(r0 + j) * ld + col;
+#pragma unroll
+            for (int k = 0; k < NSL; ++k)
+              *reinterpret_cast<uint4*>(p1 + k * plane) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
           }
         }
         grp_bar(grp);  // red may be reused
