@@ -717,6 +717,54 @@ static int chain_max_clusters() {
   return n;
 }
 
+// The level at which each power's chain starts.  A power's products are
+// sequential, but the powers of a launch are independent, so a chain shorter
+// than the longest may start later.  A level lasts about as long as its
+// deepest run of k-blocks per CTA, ceil(KB / f), where f is the split-K its
+// tile count allows (the largest f <= smax with f x tiles <= the SMs); the
+// powers are placed, longest first, at the start that minimises the sum of
+// that depth over the levels (ties: the earliest start).  With smax = 1 every
+// start is 0.
+static void chain_place(const std::vector<LevelOps>* levels, const int* tpo, const int* kb, int nj, int nlevels,
+                        int smax, int num_sms, int* start) {
+  std::vector<int> order(nj);
+  for (int j = 0; j < nj; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return levels[a].size() > levels[b].size(); });
+  std::vector<int> tiles(nlevels, 0), deep(nlevels, 0);
+  auto depth = [&](int T, int K) {
+    if (T == 0) return 0;
+    int f = smax;
+    while (f > 1 && f * T > num_sms) f >>= 1;
+    return (K + f - 1) / f;
+  };
+  for (int j : order) {
+    const int len = (int)levels[j].size();
+    int best = 0;
+    long long best_cost = -1;
+    for (int d = 0; d + len <= nlevels; ++d) {
+      long long cost = 0;
+      for (int L = 0; L < nlevels; ++L) {
+        int T = tiles[L], K = deep[L];
+        if (L >= d && L < d + len) {
+          T += (int)levels[j][L - d].ops.size() * tpo[j];
+          K = std::max(K, kb[j]);
+        }
+        cost += depth(T, K);
+      }
+      if (best_cost < 0 || cost < best_cost) {
+        best_cost = cost;
+        best = d;
+      }
+    }
+    start[j] = best;
+    for (int L = best; L < best + len; ++L) {
+      tiles[L] += (int)levels[j][L - best].ops.size() * tpo[j];
+      deep[L] = std::max(deep[L], kb[j]);
+    }
+  }
+}
+
 // Whole-chain launch of up to four independent powers (same tile width and
 // slice count); *used stays false when the powers do not fit one cooperative
 // wave (the caller then runs the level-by-level path).
@@ -750,15 +798,26 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
     if ((int)levels[j].size() > chain::MAX_LEVELS) return MATPOW_OK;
     nlevels = std::max(nlevels, (int)levels[j].size());
   }
+  // where each power's chain starts (the split-K the launch may use decides
+  // which placement is best; see below for the split itself)
+  const int want_s = rule ? rule->split_k : -1;  // -1: the largest that fits
+  const bool may_split = p->chain_mode == 1 && BN == 64 && want_s != 1;
+  int tpo[CHAIN_MAXP], kbj[CHAIN_MAXP], start[CHAIN_MAXP];
+  for (int j = 0; j < nj; ++j) {
+    const int N = jobs[j].N;
+    tpo[j] = ((N + chain::BM - 1) / chain::BM) * ((N + BN - 1) / BN);
+    kbj[j] = (N + chain::BK - 1) / chain::BK;
+  }
+  chain_place(levels, tpo, kbj, nj, nlevels, may_split ? (want_s > 1 ? want_s : nsl == 3 ? 2 : 4) : 1, p->num_sms,
+              start);
   // CTA groups per level: the powers' tiles one after another
   int G1 = 0;
   for (int L = 0; L < nlevels; ++L) {
     int acc = 0;
     for (int j = 0; j < nj; ++j) {
       P.lvl_begin[L][j] = (short)acc;
-      const int N = jobs[j].N;
-      const int tpo = ((N + chain::BM - 1) / chain::BM) * ((N + BN - 1) / BN);
-      if (L < (int)levels[j].size()) acc += (int)levels[j][L].ops.size() * tpo;
+      const int Lj = L - start[j];
+      if (Lj >= 0 && Lj < (int)levels[j].size()) acc += (int)levels[j][Lj].ops.size() * tpo[j];
     }
     P.lvl_begin[L][nj] = (short)acc;
     G1 = std::max(G1, acc);
@@ -769,8 +828,7 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
   // the smallest multiple of S covering S x (the largest level), capped by
   // the SMs; at least one level must be able to split, or S = 1.
   int S = 1, G = G1;
-  const int want_s = rule ? rule->split_k : -1;  // -1: the largest that fits
-  if (p->chain_mode == 1 && BN == 64 && want_s != 1) {
+  if (may_split) {
     int minT = 1 << 30;
     for (int L = 0; L < nlevels; ++L) minT = std::min(minT, (int)P.lvl_begin[L][nj]);
     const int smax = nsl == 3 ? 2 : 4;
@@ -818,7 +876,7 @@ matpow_status tc_chain_launch(matpow_plan_s* p, const ChainJob* jobs, int nj, cu
     for (size_t L = 0; L < lv.size(); ++L)
       for (size_t i = 0; i < lv[L].ops.size(); ++i) {
         const Op& o = lv[L].ops[i];
-        chain::Op& c = Q.ops[2 * L + i];
+        chain::Op& c = Q.ops[2 * (L + start[j]) + i];
         c.xb = (signed char)o.xb;
         c.yb = (signed char)o.yb;
         c.cb = (signed char)o.cb;

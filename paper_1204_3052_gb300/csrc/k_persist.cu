@@ -295,13 +295,14 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
     const int h = q >> 1;             // the tile's 64-row block row
     const bool lead = q == 0 && lane == 0;
     float T[WC];
-    for (int lt = 0;; ++lt) {
+    // the other group's tiles (lt of the other parity): their k-blocks pass
+    // by.  Each one's depth is read a tile ahead, so that the global load
+    // overlaps this group's fold instead of delaying its next tile.
+    if (grp == 1 && (int)blockIdx.x < tiles_total) gk += recs[blockIdx.x].x >> 24;
+    for (int lt = grp;; lt += 2) {
       const int tb = blockIdx.x + lt * G;
       if (tb >= tiles_total) break;
-      if ((lt & 1) != grp) {  // the other group's tile: its k-blocks pass by
-        gk += recs[tb].x >> 24;
-        continue;
-      }
+      const int kb_skip = tb + G < tiles_total ? recs[tb + G].x >> 24 : 0;
       const int e = lt & (EXPB - 1);
       bool ok = true;
       int dummy = 0;
@@ -438,6 +439,7 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
         if (row < N)
           store_row_f32<WC>(T, (float*)outp + (size_t)row * N, c0, N, mode == OUT_USER_MANT, ti.Ec, status, outp);
       }
+      gk += kb_skip;
     }
   }
   ptx::tc_fence_before();
