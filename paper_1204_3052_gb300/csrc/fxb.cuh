@@ -368,9 +368,10 @@ __device__ __forceinline__ void fold(float (&T)[BN], uint32_t tq, const float* f
 }
 
 // One 64 x 64 block (I, J) of a float32 matrix A (leading dimension N) split
-// into the stored format by the first 256 threads of the CTA (any further
-// threads take part in its barriers only): block exponent, slices, matrix
-// maximum, non-finite check.  red: 8 floats of shared scratch.  In two
+// into the stored format by the first 256 threads of the CTA (with NB = 0
+// any further threads take part in its barriers only; with NB = 256 they do
+// not take part at all): block exponent, slices, matrix maximum, non-finite
+// check.  red: 8 floats of shared scratch.  In two
 // steps: prep_load reads this thread's 16 values of the block (so that a
 // kernel can start the reads early), prep_split does the rest; prep_block
 // runs both.
@@ -382,7 +383,32 @@ __device__ __forceinline__ void prep_load(const float* __restrict__ A, int N, in
   for (int j = 0; j < 16; ++j) v[j] = (r < N && c0 + j < N) ? A[(size_t)r * N + c0 + j] : 0.f;
 }
 
-template <int NSL = 2>
+// NB = 0: the CTA's barrier (every thread takes part); NB = 256: named
+// barrier 3 over threads 0..255 alone (the other warps may do other work).
+template <int NB>
+__device__ __forceinline__ bool prep_sync_or(bool pred) {
+  if constexpr (NB == 0) {
+    return __syncthreads_or(pred);
+  } else {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.or.pred q, 3, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "n"(NB)
+        : "memory");
+    return r != 0;
+  }
+}
+template <int NB>
+__device__ __forceinline__ void prep_sync() {
+  if constexpr (NB == 0)
+    __syncthreads();
+  else
+    asm volatile("barrier.cta.sync 3, %0;" ::"n"(NB) : "memory");
+}
+
+template <int NSL = 2, int NB = 0>
 __device__ __forceinline__ void prep_split(const float (&v)[16], int N, int ld, int I, int J,
                                            __nv_bfloat16* a1p, long long plane, int* bexp,
                                            unsigned* maxbits, unsigned* status, float* red) {
@@ -399,7 +425,7 @@ __device__ __forceinline__ void prep_split(const float (&v)[16], int N, int ld, 
   }
   m = warp_max(m);
   if (act && (tid & 31) == 0) red[tid >> 5] = m;
-  if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_BADINPUT);
+  if (prep_sync_or<NB>(bad) && tid == 0) atomicOr(status, ST_BADINPUT);
   float bm = red[0];
 #pragma unroll
   for (int w = 1; w < 8; ++w) bm = fmaxf(bm, red[w]);
@@ -441,16 +467,16 @@ __device__ __forceinline__ void prep_split(const float (&v)[16], int N, int ld, 
       }
     }
   }
-  __syncthreads();  // red may be reused
+  prep_sync<NB>();  // red may be reused
 }
 
-template <int NSL = 2>
+template <int NSL = 2, int NB = 0>
 __device__ __forceinline__ void prep_block(const float* __restrict__ A, int N, int ld, int I, int J,
                                            __nv_bfloat16* a1p, long long plane, int* bexp,
                                            unsigned* maxbits, unsigned* status, float* red) {
   float v[16];
   prep_load(A, N, I, J, v);
-  prep_split<NSL>(v, N, ld, I, J, a1p, plane, bexp, maxbits, status, red);
+  prep_split<NSL, NB>(v, N, ld, I, J, a1p, plane, bexp, maxbits, status, red);
 }
 
 // Exponent table of one tile, staged in shared memory by warp 3:

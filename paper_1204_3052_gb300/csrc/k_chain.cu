@@ -316,67 +316,12 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
     *abort_flag = 0;
     ptx::fence_barrier_init();
   }
-  // this CTA's work at every level (tile, power, split), from the launch
-  // tables in parameter space, once: one thread per level
+  __syncthreads();  // barriers and the abort flag initialised
   __shared__ LevelWork s_work[chain::MAX_LEVELS];
-  for (int L = threadIdx.x; L < P.nlevels; L += blockDim.x) {
-    // the level's split: f CTAs of a cluster share a tile, the largest f
-    // (dividing S) with f x (tiles of the level) <= G; the cluster's S CTAs
-    // then work on S / f tiles
-    const int T_L = P.lvl_begin[L][P.nprob];
-    int f = 1;
-    if (clustered) {
-      f = S;
-      while (f > 1 && f * T_L > (int)G) f >>= 1;
-    }
-    const int t_all = clustered ? (int)(blockIdx.x / S) * (S / f) + crank / f : (int)blockIdx.x;
-    LevelWork w;
-    w.f = (short)f;
-    w.pi = -1;
-    w.t = 0;
-    w.m0 = w.n0 = 0;
-    w.N = (short)P.pr[0].N;
-    w.op = P.pr[0].ops[2 * L];
-    if (t_all < T_L) {
-      int pi = 0;  // the power this CTA group works for at level L
-      while (pi + 1 < P.nprob && t_all >= P.lvl_begin[L][pi + 1]) ++pi;
-      const ChainProblem& Q = P.pr[pi];
-      const int local = t_all - P.lvl_begin[L][pi];
-      const int oi = local / Q.tiles_per_op;
-      const int t = local - oi * Q.tiles_per_op;
-      const int tm = t / Q.tiles_n, tn = t - tm * Q.tiles_n;
-      w.pi = (short)pi;
-      w.t = (short)t;
-      w.op = Q.ops[2 * L + oi];
-      w.N = (short)Q.N;
-      w.m0 = (short)(tm * BM);
-      w.n0 = (short)(tn * BN);
-    }
-    s_work[L] = w;
-  }
-  // every CTA of the cluster has started and initialised its barriers before
-  // any remote store or arrival
-  if (clustered) cluster_sync_all();
-  if (warp == 2) {
-    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
-    ptx::tmem_relinquish();
-  }
-  if (warp == 0 && lane == 0) {
-    for (int pi = 0; pi < P.nprob; ++pi)
-      for (int b = 0; b < 4; ++b)
-        for (int k = 0; k < NSL; ++k) {
-          ptx::prefetch_tmap(&P.pr[pi].amap[b][k]);
-          ptx::prefetch_tmap(&P.pr[pi].bmap[b][k]);
-        }
-  }
-  ptx::tc_fence_before();
-  __syncthreads();
-  ptx::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  // ---- prep: block-scaled exact split of each A into its buffer 0, max|A|
-  // into its slot 1
-  {
+  if (threadIdx.x < 256) {
+    // ---- prep: block-scaled exact split of each A into its buffer 0,
+    // max|A| into its slot 1 (threads 0..255 on named barrier 3, while the
+    // other warps set up the levels)
     int i = 0;
     for (int b = blockIdx.x; b < n_prep; b += G, ++i) {
       int pi = 0;
@@ -385,17 +330,74 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
       const int nb = fxb::nblocks(Q.N);
       const int lb = b - P.prep_begin[pi];
       if (i < 2)
-        fxb::prep_split<NSL>(i == 0 ? pv[0] : pv[1], Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0],
-                             Q.plane, Q.bexp[0], &Q.scales[1].maxbits, P.status, red);
+        fxb::prep_split<NSL, 256>(i == 0 ? pv[0] : pv[1], Q.N, Q.ld, lb / nb, lb % nb,
+                                  (__nv_bfloat16*)Q.slices[0], Q.plane, Q.bexp[0], &Q.scales[1].maxbits, P.status,
+                                  red);
       else
-        fxb::prep_block<NSL>(Q.A, Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0], Q.plane, Q.bexp[0],
-                             &Q.scales[1].maxbits, P.status, red);
+        fxb::prep_block<NSL, 256>(Q.A, Q.N, Q.ld, lb / nb, lb % nb, (__nv_bfloat16*)Q.slices[0], Q.plane,
+                                  Q.bexp[0], &Q.scales[1].maxbits, P.status, red);
     }
     fence_proxy_async_global();
+  } else if (warp == 8) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
+    ptx::tmem_relinquish();
+  } else if (warp == 9) {
+    if (lane == 0)
+      for (int pi = 0; pi < P.nprob; ++pi)
+        for (int b = 0; b < 4; ++b)
+          for (int k = 0; k < NSL; ++k) {
+            ptx::prefetch_tmap(&P.pr[pi].amap[b][k]);
+            ptx::prefetch_tmap(&P.pr[pi].bmap[b][k]);
+          }
+  } else {
+    // this CTA's work at every level (tile, power, split), from the launch
+    // tables in parameter space, once: one thread of warps 10-11 per level
+    for (int L = threadIdx.x - 320; L < P.nlevels; L += 64) {
+      // the level's split: f CTAs of a cluster share a tile, the largest f
+      // (dividing S) with f x (tiles of the level) <= G; the cluster's S CTAs
+      // then work on S / f tiles
+      const int T_L = P.lvl_begin[L][P.nprob];
+      int f = 1;
+      if (clustered) {
+        f = S;
+        while (f > 1 && f * T_L > (int)G) f >>= 1;
+      }
+      const int t_all = clustered ? (int)(blockIdx.x / S) * (S / f) + crank / f : (int)blockIdx.x;
+      LevelWork w;
+      w.f = (short)f;
+      w.pi = -1;
+      w.t = 0;
+      w.m0 = w.n0 = 0;
+      w.N = (short)P.pr[0].N;
+      w.op = P.pr[0].ops[2 * L];
+      if (t_all < T_L) {
+        int pi = 0;  // the power this CTA group works for at level L
+        while (pi + 1 < P.nprob && t_all >= P.lvl_begin[L][pi + 1]) ++pi;
+        const ChainProblem& Q = P.pr[pi];
+        const int local = t_all - P.lvl_begin[L][pi];
+        const int oi = local / Q.tiles_per_op;
+        const int t = local - oi * Q.tiles_per_op;
+        const int tm = t / Q.tiles_n, tn = t - tm * Q.tiles_n;
+        w.pi = (short)pi;
+        w.t = (short)t;
+        w.op = Q.ops[2 * L + oi];
+        w.N = (short)Q.N;
+        w.m0 = (short)(tm * BM);
+        w.n0 = (short)(tn * BN);
+      }
+      s_work[L] = w;
+    }
   }
+  // every CTA of the cluster has started and initialised its barriers before
+  // any remote store or arrival
+  if (clustered) cluster_sync_all();
+  // the grid barrier's CTA barrier also publishes the work table and the
+  // TMEM address
+  ptx::tc_fence_before();
   grid_sync(P.gbar, ++bar_no * G, P.status, abort_flag);
+  ptx::tc_fence_after();
   fence_proxy_async_global();
-
+  const uint32_t tmem = *tmem_slot;
   int kb_base = 0;  // k-blocks done by this CTA: ring and accumulator-buffer phases
   uint32_t xph = 0;  // phase of xbar (leader)
   float T[WC];
@@ -631,7 +633,7 @@ __device__ __forceinline__ void chain_body(const ChainParams& P) {
   }
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == 2) {
+  if (warp == 8) {  // the allocating warp
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, C::TMEM_COLS);
   }
