@@ -456,6 +456,8 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
     const LevelOps& lv = levels[li];
     GemmPair g{};
     g.count = (int)lv.ops.size();
+    const int t128 = tiles_for(N, 128);
+    const int edge = simt_tile_edge(g.count * t128 * t128, p->num_sms);  // SIMT tiles
     int t = 0;
     for (int i = 0; i < g.count; ++i) {
       const Op& op = lv.ops[i];
@@ -480,7 +482,7 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
         if (st != MATPOW_OK) return st;
         t += nt;
       } else {
-        d.tiles_n = tiles_for(N, simt_tile_edge());
+        d.tiles_n = tiles_for(N, edge);
         t += d.tiles_n * d.tiles_n;
       }
     }
@@ -494,7 +496,7 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       if (st != MATPOW_OK) return st;
       timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
     } else {
-      CK(p, launch_simt_pair(g, p->scales, p->status, s));
+      CK(p, launch_simt_pair(g, edge, p->scales, p->status, s));
       timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
     }
     p->launches++;
@@ -644,9 +646,11 @@ matpow_status mp::enqueue_product_f32(matpow_plan_s* p, const float* X, const fl
     if (st != MATPOW_OK) return st;
     timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
   } else {
-    d.tiles_n = tiles_for(N, simt_tile_edge());
+    const int t128 = tiles_for(N, 128);
+    const int edge = simt_tile_edge(t128 * t128, p->num_sms);
+    d.tiles_n = tiles_for(N, edge);
     g.tiles_total = d.tiles_n * d.tiles_n;
-    CK(p, launch_simt_pair(g, p->scales, p->status, s));
+    CK(p, launch_simt_pair(g, edge, p->scales, p->status, s));
     timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
   }
   p->launches++;

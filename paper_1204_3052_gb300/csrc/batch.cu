@@ -251,7 +251,19 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
   std::vector<int4> trec;  // persistent-kernel tile records of every launch
   for (int L = 0; L < max_levels; ++L) {
     for (int pi = 0; pi < (tc ? 3 : 1); ++pi) {
-      const int bn = tc ? (pi == 2 ? 128 : 64) : 0;
+      // SIMT: one tile edge for the whole launch (64 when its 128-tiles would
+      // not fill the SMs); carried in the launch's bn
+      int sedge = 128;
+      if (!tc) {
+        int t128 = 0;
+        for (const Big& b : big)
+          if (L < (int)b.levels.size()) {
+            const int tt = (N[b.i] + 127) / 128;
+            t128 += (int)b.levels[L].ops.size() * tt * tt;
+          }
+        sedge = simt_tile_edge(t128, p->num_sms);
+      }
+      const int bn = tc ? (pi == 2 ? 128 : 64) : sedge;
       int begin = (int)gd.size(), tiles = 0, max_n = 0;
       for (size_t bi = 0; bi < big.size(); ++bi) {
         const Big& b = big[bi];
@@ -287,7 +299,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
             d.map_c = mpb * (4 * (int)bi + (last ? op.xb : op.cb));
             tiles += ((Ni + 127) / 128) * d.tiles_n;
           } else {
-            d.tiles_n = (Ni + simt_tile_edge() - 1) / simt_tile_edge();
+            d.tiles_n = (Ni + bn - 1) / bn;
             tiles += d.tiles_n * d.tiles_n;
           }
           gd.push_back(d);
@@ -390,7 +402,7 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
           return st;
         timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
       } else {
-        CK(p, launch_simt_group(g, la.count, la.tiles, p->batch.scales, p->status, s));
+        CK(p, launch_simt_group(g, la.count, la.tiles, la.bn, p->batch.scales, p->status, s));
         timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
       }
       p->launches++;

@@ -3,9 +3,10 @@
 //  * simt_gemm: C = X * Y for stored float32 matrices (arXiv 1204.3052
 //    Sec. 4.1's c_ij = sum_k x_ik y_kj), tiled through shared memory
 //    (Sec. 4.3.2, 4.3.7) with 128-bit vector loads (Sec. 4.3.5) and coalesced
-//    row-major access (Sec. 4.3.3).  On sm_103a: a 128x128 CTA tile, 16-deep
-//    k-steps double-buffered in shared memory, an 8x8 register tile per
-//    thread.  The epilogue applies the lagged power-of-two scale of the
+//    row-major access (Sec. 4.3.3).  On sm_103a: a 128x128 CTA tile with an
+//    8x8 register tile per thread, or 64x64 with 4x4 where 128-wide tiles
+//    would leave most SMs idle; 16-deep k-steps double-buffered in shared
+//    memory.  The epilogue applies the lagged power-of-two scale of the
 //    operands, writes the stored result (or the user's float32 output) and
 //    folds max|C| into the result's scale slot.
 //  * tiny_chain: the whole square-and-multiply chain (Sec. 4.3) for N <= 64
@@ -15,39 +16,47 @@
 namespace mp {
 
 namespace simt {
-constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8;
-constexpr int THREADS = (BM / TM) * (BN / TN);  // 256
-constexpr int PAD = 4;
+constexpr int BK = 16, THREADS = 256, PAD = 4;
 }  // namespace simt
 
-int simt_tile_edge() { return simt::BM; }
+// The tile edge E of a launch: 128 x 128 tiles (an 8 x 8 register tile per
+// thread) unless they leave most SMs idle -- fewer 128-tiles than SMs, as for
+// orders up to ~1500 -- then 64 x 64 tiles (4 x 4 per thread, four times the
+// CTAs).
+int simt_tile_edge(int tiles128, int num_sms) { return tiles128 < num_sms ? 64 : 128; }
 
-// One 128x128 tile of one product.
+// One E x E tile of one product (256 threads as 16 x 16, each holding an
+// (E / 16) x (E / 16) register tile: rows 4 ty + 64 h + i, columns
+// 4 tx + 64 h + j).
+template <int E>
 __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* scales,
                                           unsigned* status) {
   using namespace simt;
-  __shared__ __align__(16) float As[2][BK][BM + PAD];
-  __shared__ __align__(16) float Bs[2][BK][BN + PAD];
+  static_assert(E == 64 || E == 128, "tile edge");
+  constexpr int T = E / 16;  // register tile edge
+  constexpr int H = E / 64;  // 4-wide groups per register-tile edge
+  __shared__ __align__(16) float As[2][BK][E + PAD];
+  __shared__ __align__(16) float Bs[2][BK][E + PAD];
   __shared__ float red[THREADS / 32];
 
   const int N = d.N, ld = d.ld;
   int tm, tn;
   tile_raster(tile, d.tiles_n, d.tiles_n, &tm, &tn);  // square tiles
-  const int m0 = tm * BM, n0 = tn * BN;
+  const int m0 = tm * E, n0 = tn * E;
   const float* __restrict__ X = (const float*)d.X;
   const float* __restrict__ Y = (const float*)d.Y;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
 
-  // loader coordinates: X tile 128 rows x 16 k as float4 along k
-  const int xr = tid >> 2, xq = tid & 3;  // rows xr, xr+64; k quad xq
-  // Y tile 16 k x 128 cols as float4 along n
-  const int yk = tid >> 5, yc = tid & 31;  // k rows yk, yk+8; col quad yc
+  // loader coordinates: X tile E rows x 16 k as float4 along k (rows xr + 64 h);
+  // Y tile 16 k x E cols as float4 along n (k rows yk + (1024 / E) h)
+  const int xr = tid >> 2, xq = tid & 3;
+  const int yk = tid / (E / 4), yc = tid % (E / 4);
 
-  float4 xa[2], yb[2];
+  float4 xa[H], yb[H];
   auto load_tile = [&](int k0) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < H; ++h) {
       int r = m0 + xr + 64 * h, k = k0 + 4 * xq;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r < N && k < N) {
@@ -57,7 +66,7 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
         if (k + 3 >= N) v.w = 0.f;
       }
       xa[h] = v;
-      int kk = k0 + yk + 8 * h, c = n0 + 4 * yc;
+      int kk = k0 + yk + (1024 / E) * h, c = n0 + 4 * yc;
       float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
       if (kk < N && c < N) {
         w = *reinterpret_cast<const float4*>(Y + (size_t)kk * ld + c);
@@ -70,21 +79,21 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
   };
   auto store_tile = [&](int buf) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < H; ++h) {
       int r = xr + 64 * h;
       As[buf][4 * xq + 0][r] = xa[h].x;
       As[buf][4 * xq + 1][r] = xa[h].y;
       As[buf][4 * xq + 2][r] = xa[h].z;
       As[buf][4 * xq + 3][r] = xa[h].w;
-      *reinterpret_cast<float4*>(&Bs[buf][yk + 8 * h][4 * yc]) = yb[h];
+      *reinterpret_cast<float4*>(&Bs[buf][yk + (1024 / E) * h][4 * yc]) = yb[h];
     }
   };
 
-  float acc[TM][TN];
+  float acc[T][T];
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+  for (int i = 0; i < T; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < T; ++j) acc[i][j] = 0.f;
 
   const int KT = (N + BK - 1) / BK;
   load_tile(0);
@@ -95,19 +104,18 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
     if (kt + 1 < KT) load_tile((kt + 1) * BK);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      float a[TM], b[TN];
-      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][k][4 * ty]);
-      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][k][64 + 4 * ty]);
-      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][k][4 * tx]);
-      float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][k][64 + 4 * tx]);
-      a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
-      a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
-      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
-      b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+      float a[T], b[T];
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+      for (int h = 0; h < H; ++h) {
+        const float4 av = *reinterpret_cast<const float4*>(&As[buf][k][64 * h + 4 * ty]);
+        const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][k][64 * h + 4 * tx]);
+        a[4 * h] = av.x; a[4 * h + 1] = av.y; a[4 * h + 2] = av.z; a[4 * h + 3] = av.w;
+        b[4 * h] = bv.x; b[4 * h + 1] = bv.y; b[4 * h + 2] = bv.z; b[4 * h + 3] = bv.w;
+      }
 #pragma unroll
-        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
     if (kt + 1 < KT) store_tile(buf ^ 1);
     __syncthreads();
@@ -124,11 +132,11 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
   }
   float m = 0.f;
 #pragma unroll
-  for (int i = 0; i < TM; ++i) {
-    const int r = m0 + (i < 4 ? 4 * ty + i : 64 + 4 * ty + i - 4);
+  for (int i = 0; i < T; ++i) {
+    const int r = m0 + 64 * (i / 4) + 4 * ty + (i & 3);
     if (r >= N) continue;
 #pragma unroll
-    for (int hb = 0; hb < 2; ++hb) {
+    for (int hb = 0; hb < H; ++hb) {
       const int c = n0 + 64 * hb + 4 * tx;
       float v[4];
 #pragma unroll
@@ -165,13 +173,15 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
   }
 }
 
+template <int E>
 __global__ void __launch_bounds__(simt::THREADS, 2)
     simt_pair_kernel(const GemmPair g, Scale* scales, unsigned* status) {
   int t = blockIdx.x;
   int which = (g.count > 1 && t >= g.d[1].tile_begin) ? 1 : 0;
-  simt_tile(g.d[which], t - g.d[which].tile_begin, scales, status);
+  simt_tile<E>(g.d[which], t - g.d[which].tile_begin, scales, status);
 }
 
+template <int E>
 __global__ void __launch_bounds__(simt::THREADS, 2)
     simt_group_kernel(const GemmDesc* __restrict__ descs, int count, Scale* scales,
                       unsigned* status) {
@@ -182,17 +192,23 @@ __global__ void __launch_bounds__(simt::THREADS, 2)
     if (descs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
   }
   GemmDesc d = descs[lo];
-  simt_tile(d, t - d.tile_begin, scales, status);
+  simt_tile<E>(d, t - d.tile_begin, scales, status);
 }
 
-cudaError_t launch_simt_pair(const GemmPair& g, Scale* scales, unsigned* status, cudaStream_t s) {
-  simt_pair_kernel<<<g.tiles_total, simt::THREADS, 0, s>>>(g, scales, status);
+cudaError_t launch_simt_pair(const GemmPair& g, int edge, Scale* scales, unsigned* status, cudaStream_t s) {
+  if (edge == 64)
+    simt_pair_kernel<64><<<g.tiles_total, simt::THREADS, 0, s>>>(g, scales, status);
+  else
+    simt_pair_kernel<128><<<g.tiles_total, simt::THREADS, 0, s>>>(g, scales, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_total, Scale* scales,
+cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_total, int edge, Scale* scales,
                               unsigned* status, cudaStream_t s) {
-  simt_group_kernel<<<tiles_total, simt::THREADS, 0, s>>>(d_descs, count, scales, status);
+  if (edge == 64)
+    simt_group_kernel<64><<<tiles_total, simt::THREADS, 0, s>>>(d_descs, count, scales, status);
+  else
+    simt_group_kernel<128><<<tiles_total, simt::THREADS, 0, s>>>(d_descs, count, scales, status);
   return cudaGetLastError();
 }
 

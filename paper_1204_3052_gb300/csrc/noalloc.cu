@@ -125,7 +125,9 @@ extern "C" matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, 
 
   // right-to-left square-and-multiply over fixed arrays (no host allocation)
   const int ld = ld_for(N, FMT_F32);
-  const int tn = (N + simt_tile_edge() - 1) / simt_tile_edge();
+  // N <= 512: at most 16 tiles of 128, so 64-wide SIMT tiles (four times the CTAs)
+  constexpr int edge = 64;
+  const int tn = (N + edge - 1) / edge;
   int refs[4] = {1, 0, 0, 0};
   auto take = [&]() {
     for (int i = 0; i < 4; ++i)
@@ -183,7 +185,7 @@ extern "C" matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, 
         t += tn * tn;
       }
       g.tiles_total = t;
-      CK(launch_simt_pair(g, scales, status, s));
+      CK(launch_simt_pair(g, edge, scales, status, s));
     }
     if (newRb >= 0) {
       refs[Rb]--;

@@ -284,7 +284,8 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
             gw.push_back(d);
           }
         } else {
-          d.tiles_n = (r.N + simt_tile_edge() - 1) / simt_tile_edge();
+          // 128-wide SIMT tiles: a level's requests are gathered one by one
+          d.tiles_n = (r.N + 127) / 128;
           d.tile_begin = tiles_f;
           tiles_f += d.tiles_n * d.tiles_n;
           gf.push_back(d);
@@ -394,7 +395,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
                            s->d_maps, 64, fmt_slices(s->fmt), maxn_f, s->num_sms, true, s->scales, st0,
                            s->stream);
     else
-      e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, s->scales, st0,
+      e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, 128, s->scales, st0,
                             s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
   }
