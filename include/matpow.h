@@ -14,7 +14,16 @@
  * Conventions for every call:
  *  - Matrices are row-major, N x N, densely packed (leading dimension N).
  *  - "device" pointers are CUDA global-memory addresses on the plan's device;
- *    "host" pointers are ordinary process memory.  The caller owns all memory
+ *    "host" pointers are ordinary process memory.  Wherever a matrix is a
+ *    "device" pointer it may also be page-locked host memory that the device
+ *    addresses at the same pointer (cudaHostAlloc / cudaMallocHost memory
+ *    under unified addressing; matpow_host_accessible() tells): the kernels
+ *    then read A and write the result across the host link themselves (on a
+ *    GB300, the NVLink-C2C to the Grace CPU).  Only the input read and the
+ *    final result write touch such memory; every intermediate stays in the
+ *    plan's device workspace.  Results are bit-identical to those of device
+ *    buffers; for large transfers, copies by the copy engines into device
+ *    buffers were measured faster.  The caller owns all memory
  *    it passes in; the library never frees it and keeps no reference after
  *    the work enqueued by the call has finished.
  *  - `stream` is a cudaStream_t (NULL: the legacy default stream).  Work is
@@ -333,6 +342,16 @@ matpow_status matpow_selftest_ffma(matpow_plan_t plan, int64_t iters, void* stre
 
 /* Streaming multiprocessors of the plan's device (sizes the probe above). */
 int matpow_plan_sm_count(matpow_plan_t plan);
+
+/*
+ * 1 if `device` can address `ptr` at the same pointer, so that it may be
+ * passed where a call takes a device matrix: global memory of that device,
+ * managed memory, or page-locked host memory mapped at its host address.
+ * 0 otherwise (pageable host memory, another device's memory, NULL, or a
+ * failed query).  A host-side query (cudaPointerGetAttributes); no work is
+ * enqueued.
+ */
+int matpow_host_accessible(const void* ptr, int device);
 
 /* G(n) = floor(log2 n) + popcount(n) - 1 (0 for n <= 1): products that A^n takes. */
 int matpow_gemm_count(uint64_t n);

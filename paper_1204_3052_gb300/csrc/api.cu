@@ -344,6 +344,25 @@ extern "C" int64_t matpow_launch_count(matpow_plan_t p) { return p ? p->launches
 
 extern "C" int matpow_plan_sm_count(matpow_plan_t p) { return p ? p->num_sms : 0; }
 
+extern "C" int matpow_host_accessible(const void* ptr, int device) {
+  if (!ptr) return 0;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  switch (a.type) {
+    case cudaMemoryTypeDevice:
+      return a.device == device ? 1 : 0;
+    case cudaMemoryTypeManaged:
+      return 1;
+    case cudaMemoryTypeHost:  // page-locked: usable when mapped at its host address
+      return a.devicePointer == ptr ? 1 : 0;
+    default:
+      return 0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // scheduling one power
 
@@ -559,7 +578,7 @@ static matpow_status enqueue_modp(matpow_plan_s* p, const uint32_t* dA, int N, u
   p->launches++;
   if (n == 1) {
     CK(p, cudaMemcpy2DAsync(dOut, (size_t)N * 4, p->buf[0], (size_t)ld * 4, (size_t)N * 4, N,
-                            cudaMemcpyDeviceToDevice, s));
+                            cudaMemcpyDefault, s));  // dOut: device or mapped host memory
     return MATPOW_OK;
   }
   std::vector<LevelOps> levels;

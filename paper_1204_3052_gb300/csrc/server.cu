@@ -386,7 +386,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
                                     s->stream);
     if (e == cudaSuccess && q->r.n == 1)
       e = cudaMemcpy2DAsync(q->r.dOut, (size_t)q->r.N * 4, base, (size_t)ld_for(q->r.N, FMT_U32) * 4,
-                            (size_t)q->r.N * 4, q->r.N, cudaMemcpyDeviceToDevice, s->stream);
+                            (size_t)q->r.N * 4, q->r.N, cudaMemcpyDefault, s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: mod-p prep");
   }
   if (!gf.empty()) {

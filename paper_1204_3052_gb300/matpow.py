@@ -41,7 +41,7 @@ EXPORTS = [
     "matpow_submit", "matpow_poll", "matpow_server_latencies", "matpow_server_destroy",
     "matpow_f32_noalloc", "matpow_selftest_wait_timeout", "matpow_expm",
     "matpow_plan_set_tile_table", "matpow_plan_load_tile_table", "matpow_tile_table_parse",
-    "matpow_tile_rule_lookup", "matpow_selftest_ffma", "matpow_plan_sm_count",
+    "matpow_tile_rule_lookup", "matpow_selftest_ffma", "matpow_plan_sm_count", "matpow_host_accessible",
 ]
 
 # The tile table tuned on a GB300 (written by autotune.py); plans load it when
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "matpow_expm": (i32, [vp, vp, i32, vp, vp, vp]),
             "matpow_selftest_ffma": (i32, [vp, i64, vp]),
             "matpow_plan_sm_count": (i32, [vp]),
+            "matpow_host_accessible": (i32, [vp, i32]),
             "matpow_plan_set_tile_table": (i32, [vp, ctypes.POINTER(TileRule), i32]),
             "matpow_plan_load_tile_table": (i32, [vp, ctypes.c_char_p]),
             "matpow_tile_table_parse": (i32, [ctypes.c_char_p, ctypes.POINTER(TileRule), i32,
@@ -269,6 +270,12 @@ def matpow_selftest_ffma(plan: int, iters: int, stream=None) -> int:
 
 def matpow_plan_sm_count(plan: int) -> int:
     return int(load().matpow_plan_sm_count(plan))
+
+
+def matpow_host_accessible(buf, device: int = 0) -> bool:
+    """Whether `device` addresses `buf` (a tensor or an address) at the same
+    pointer, so that it may stand where a call takes a device matrix."""
+    return bool(load().matpow_host_accessible(_ptr(buf), int(device)))
 
 
 def measure_fp32_peak(plan: int, iters: int = 1 << 16, reps: int = 5, stream=None) -> float:
