@@ -413,28 +413,31 @@ __global__ void __launch_bounds__(persist::THREADS, 1)
         fxb::transpose8x8(T, lane);
         const int col = c0 + 8 * (lane & 7);
         const int r0 = ti.m0 + 32 * q + 8 * (lane >> 3);
-        // one row chunk per pass, T[0..7], then the rest moves down: a short
+        // two row chunks per pass, T[0..15], then the rest moves down: a short
         // loop body instead of eight unrolled copies (instruction fetch is
         // this kernel's largest stall)
 #pragma unroll 1
-        for (int j = 0; j < 8; ++j) {
-          if (r0 + j < N && col < N) {
-            uint32_t w[NSL][4];
+        for (int j = 0; j < 8; j += 2) {
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-              float x0[NSL], x1[NSL];
-              fxb::slice_n<NSL>(T[2 * hh], ex, x0);
-              fxb::slice_n<NSL>(T[2 * hh + 1], ex, x1);
+          for (int jj = 0; jj < 2; ++jj) {
+            if (r0 + j + jj < N && col < N) {
+              uint32_t w[NSL][4];
 #pragma unroll
-              for (int k = 0; k < NSL; ++k) w[k][hh] = fxb::pack_bf16_exact(x0[k], x1[k]);
+              for (int hh = 0; hh < 4; ++hh) {
+                float x0[NSL], x1[NSL];
+                fxb::slice_n<NSL>(T[8 * jj + 2 * hh], ex, x0);
+                fxb::slice_n<NSL>(T[8 * jj + 2 * hh + 1], ex, x1);
+#pragma unroll
+                for (int k = 0; k < NSL; ++k) w[k][hh] = fxb::pack_bf16_exact(x0[k], x1[k]);
+              }
+              __nv_bfloat16* p1 = (__nv_bfloat16*)Cp + (size_t)(r0 + j + jj) * ld + col;
+#pragma unroll
+              for (int k = 0; k < NSL; ++k)
+                *reinterpret_cast<uint4*>(p1 + k * plane) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
             }
-            __nv_bfloat16* p1 = (__nv_bfloat16*)Cp + (size_t)(r0 + j) * ld + col;
-#pragma unroll
-            for (int k = 0; k < NSL; ++k)
-              *reinterpret_cast<uint4*>(p1 + k * plane) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
           }
 #pragma unroll
-          for (int i = 0; i < WC - 8; ++i) T[i] = T[i + 8];
+          for (int i = 0; i < WC - 16; ++i) T[i] = T[i + 16];
         }
         grp_bar(grp);  // red may be reused
       } else {
