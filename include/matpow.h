@@ -129,7 +129,11 @@ const char* matpow_last_error(matpow_plan_t plan);
  *                       CTAs of a thread-block cluster per tile when a level
  *                       has few tiles (results then equal the level path's
  *                       to rounding, not bit for bit); 2: the same without
- *                       split-K (bit-for-bit equal to the level path);
+ *                       split-K (bit-for-bit equal to the level path), and
+ *                       MATPOW_FP32_SIMT products without their split-K over
+ *                       two-CTA clusters (used when a launch has fewer
+ *                       64 x 64 tiles than SMs), so that every result equals
+ *                       that of the same matrix in a batch bit for bit;
  *                       0: one launch per level.
  *   MATPOW_OPT_MODP_TC  1 (default): matpow_mod_p with 64 < N <= 16384 runs on the
  *                       tensor cores (balanced byte digits of the residues,

@@ -477,6 +477,8 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
     g.count = (int)lv.ops.size();
     const int t128 = tiles_for(N, 128);
     const int edge = simt_tile_edge(g.count * t128 * t128, p->num_sms);  // SIMT tiles
+    const int te = tiles_for(N, edge);
+    const int split = p->chain_mode == 2 ? 1 : simt_split(edge, g.count * te * te, p->num_sms);
     int t = 0;
     for (int i = 0; i < g.count; ++i) {
       const Op& op = lv.ops[i];
@@ -515,7 +517,7 @@ static matpow_status enqueue_f32(matpow_plan_s* p, const float* dA, int N, uint6
       if (st != MATPOW_OK) return st;
       timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
     } else {
-      CK(p, launch_simt_pair(g, edge, p->scales, p->status, s));
+      CK(p, launch_simt_pair(g, edge, split, p->scales, p->status, s));
       timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
     }
     p->launches++;
@@ -669,7 +671,8 @@ matpow_status mp::enqueue_product_f32(matpow_plan_s* p, const float* X, const fl
     const int edge = simt_tile_edge(t128 * t128, p->num_sms);
     d.tiles_n = tiles_for(N, edge);
     g.tiles_total = d.tiles_n * d.tiles_n;
-    CK(p, launch_simt_pair(g, edge, p->scales, p->status, s));
+    const int split = p->chain_mode == 2 ? 1 : simt_split(edge, g.tiles_total, p->num_sms);
+    CK(p, launch_simt_pair(g, edge, split, p->scales, p->status, s));
     timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
   }
   p->launches++;

@@ -402,7 +402,8 @@ extern "C" matpow_status matpow_batched(matpow_plan_t p, int count, const float*
           return st;
         timed_end(p, s, ev, MATPOW_KERNEL_TC, flop);
       } else {
-        CK(p, launch_simt_group(g, la.count, la.tiles, la.bn, p->batch.scales, p->status, s));
+        const int split = tc || p->chain_mode == 2 ? 1 : simt_split(la.bn, la.tiles, p->num_sms);
+        CK(p, launch_simt_group(g, la.count, la.tiles, la.bn, split, p->batch.scales, p->status, s));
         timed_end(p, s, ev, MATPOW_KERNEL_SIMT, flop);
       }
       p->launches++;

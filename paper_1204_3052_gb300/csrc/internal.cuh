@@ -182,10 +182,14 @@ cudaError_t launch_identity(void* out, int N, int is_u32, unsigned one, long lon
 cudaError_t launch_copy(const void* A, void* out, int N, long long* log2, cudaStream_t s);
 // SIMT products on E x E tiles, E = simt_tile_edge(tiles of the launch at
 // E = 128, SMs): 128 or 64; every descriptor's tiles_n counts E-wide tiles.
-cudaError_t launch_simt_pair(const GemmPair& g, int edge, Scale* scales, unsigned* status, cudaStream_t s);
-cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_total, int edge, Scale* scales,
-                              unsigned* status, cudaStream_t s);
+// split = simt_split(E, tiles of the launch at E, SMs): 2 runs each tile on a
+// cluster of two CTAs, each summing half of k.
+cudaError_t launch_simt_pair(const GemmPair& g, int edge, int split, Scale* scales, unsigned* status,
+                             cudaStream_t s);
+cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_total, int edge, int split,
+                              Scale* scales, unsigned* status, cudaStream_t s);
 int simt_tile_edge(int tiles128, int num_sms);
+int simt_split(int edge, int tiles, int num_sms);
 // Whole-chain kernel for small N: one CTA per matrix.
 struct TinyDesc {
   const float* A;

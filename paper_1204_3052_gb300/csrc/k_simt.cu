@@ -17,6 +17,24 @@ namespace mp {
 
 namespace simt {
 constexpr int BK = 16, THREADS = 256, PAD = 4;
+// split-K over a cluster of two CTAs (64-wide tiles)
+__device__ __forceinline__ uint32_t ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// both CTAs of the cluster execute the same two of these, so none waits for a
+// thread that never arrives
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t peer(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
 }  // namespace simt
 
 // The tile edge E of a launch: 128 x 128 tiles (an 8 x 8 register tile per
@@ -24,19 +42,31 @@ constexpr int BK = 16, THREADS = 256, PAD = 4;
 // orders up to ~1500 -- then 64 x 64 tiles (4 x 4 per thread, four times the
 // CTAs).
 int simt_tile_edge(int tiles128, int num_sms) { return tiles128 < num_sms ? 64 : 128; }
+// Split-K over clusters of two CTAs for 64-wide tiles that still number fewer
+// than the SMs.
+int simt_split(int edge, int tiles, int num_sms) { return edge == 64 && tiles < num_sms ? 2 : 1; }
 
 // One E x E tile of one product (256 threads as 16 x 16, each holding an
 // (E / 16) x (E / 16) register tile: rows 4 ty + 64 h + i, columns
-// 4 tx + 64 h + j).
-template <int E>
+// 4 tx + 64 h + j).  SPLIT = 2 (64-wide tiles, clusters of two CTAs): CTA
+// rank r sums the k-steps of its half of k; rank 1 then stores its partial
+// tile into rank 0's operand buffers through distributed shared memory and
+// rank 0 adds it (rank 0's half + rank 1's half, in that order) and runs the
+// epilogue.
+template <int E, int SPLIT = 1>
 __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* scales,
                                           unsigned* status) {
   using namespace simt;
   static_assert(E == 64 || E == 128, "tile edge");
+  static_assert(SPLIT == 1 || (SPLIT == 2 && E == 64), "split-K on 64-wide tiles");
   constexpr int T = E / 16;  // register tile edge
   constexpr int H = E / 64;  // 4-wide groups per register-tile edge
-  __shared__ __align__(16) float As[2][BK][E + PAD];
-  __shared__ __align__(16) float Bs[2][BK][E + PAD];
+  // the operand buffers As [2][BK][E + PAD] and Bs (likewise), one array so
+  // that a split tile's partial sums (T T THREADS floats) fit in them
+  __shared__ __align__(16) float ops[2 * 2 * BK * (E + PAD)];
+  static_assert(SPLIT == 1 || T * T * THREADS <= 2 * 2 * BK * (E + PAD), "partial tile fits");
+  float (*As)[BK][E + PAD] = reinterpret_cast<float (*)[BK][E + PAD]>(ops);
+  float (*Bs)[BK][E + PAD] = reinterpret_cast<float (*)[BK][E + PAD]>(ops + 2 * BK * (E + PAD));
   __shared__ float red[THREADS / 32];
 
   const int N = d.N, ld = d.ld;
@@ -96,12 +126,20 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
     for (int j = 0; j < T; ++j) acc[i][j] = 0.f;
 
   const int KT = (N + BK - 1) / BK;
-  load_tile(0);
+  int kt0 = 0, kt1 = KT;
+  uint32_t rank = 0;
+  if constexpr (SPLIT == 2) {
+    rank = ctarank();
+    const int half = (KT + 1) / 2;
+    kt0 = rank == 0 ? 0 : half;
+    kt1 = rank == 0 ? half : KT;
+  }
+  load_tile(kt0 * BK);  // past N it loads zeros
   store_tile(0);
   __syncthreads();
-  for (int kt = 0; kt < KT; ++kt) {
-    const int buf = kt & 1;
-    if (kt + 1 < KT) load_tile((kt + 1) * BK);
+  for (int kt = kt0; kt < kt1; ++kt) {
+    const int buf = (kt - kt0) & 1;
+    if (kt + 1 < kt1) load_tile((kt + 1) * BK);
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
       float a[T], b[T];
@@ -117,8 +155,27 @@ __device__ __forceinline__ void simt_tile(const GemmDesc& d, int tile, Scale* sc
 #pragma unroll
         for (int j = 0; j < T; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
     }
-    if (kt + 1 < KT) store_tile(buf ^ 1);
+    if (kt + 1 < kt1) store_tile(buf ^ 1);
     __syncthreads();
+  }
+  if constexpr (SPLIT == 2) {
+    cluster_barrier();  // both k-loops are done: rank 0's operand buffers are free
+    if (rank == 1) {
+      const uint32_t dst = peer(ops, 0);
+#pragma unroll
+      for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j)
+          asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(dst + (uint32_t)(((i * T + j) * THREADS + tid) * 4)),
+                       "f"(acc[i][j])
+                       : "memory");
+    }
+    cluster_barrier();  // rank 1's partial tile is visible in rank 0's shared memory
+    if (rank == 1) return;
+#pragma unroll
+    for (int i = 0; i < T; ++i)
+#pragma unroll
+      for (int j = 0; j < T; ++j) acc[i][j] += ops[(i * T + j) * THREADS + tid];
   }
 
   // ---- epilogue: lagged scale, store, max
@@ -181,6 +238,14 @@ __global__ void __launch_bounds__(simt::THREADS, 2)
   simt_tile<E>(g.d[which], t - g.d[which].tile_begin, scales, status);
 }
 
+// 64-wide tiles split over clusters of two CTAs (CTAs 2 t and 2 t + 1: tile t)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(simt::THREADS, 2)
+    simt_pair_split_kernel(const GemmPair g, Scale* scales, unsigned* status) {
+  int t = blockIdx.x >> 1;
+  int which = (g.count > 1 && t >= g.d[1].tile_begin) ? 1 : 0;
+  simt_tile<64, 2>(g.d[which], t - g.d[which].tile_begin, scales, status);
+}
+
 template <int E>
 __global__ void __launch_bounds__(simt::THREADS, 2)
     simt_group_kernel(const GemmDesc* __restrict__ descs, int count, Scale* scales,
@@ -195,17 +260,34 @@ __global__ void __launch_bounds__(simt::THREADS, 2)
   simt_tile<E>(d, t - d.tile_begin, scales, status);
 }
 
-cudaError_t launch_simt_pair(const GemmPair& g, int edge, Scale* scales, unsigned* status, cudaStream_t s) {
-  if (edge == 64)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(simt::THREADS, 2)
+    simt_group_split_kernel(const GemmDesc* __restrict__ descs, int count, Scale* scales, unsigned* status) {
+  int t = blockIdx.x >> 1;
+  int lo = 0, hi = count - 1;  // last desc with tile_begin <= t
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (descs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+  }
+  GemmDesc d = descs[lo];
+  simt_tile<64, 2>(d, t - d.tile_begin, scales, status);
+}
+
+cudaError_t launch_simt_pair(const GemmPair& g, int edge, int split, Scale* scales, unsigned* status,
+                             cudaStream_t s) {
+  if (edge == 64 && split == 2)
+    simt_pair_split_kernel<<<2 * g.tiles_total, simt::THREADS, 0, s>>>(g, scales, status);
+  else if (edge == 64)
     simt_pair_kernel<64><<<g.tiles_total, simt::THREADS, 0, s>>>(g, scales, status);
   else
     simt_pair_kernel<128><<<g.tiles_total, simt::THREADS, 0, s>>>(g, scales, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_total, int edge, Scale* scales,
-                              unsigned* status, cudaStream_t s) {
-  if (edge == 64)
+cudaError_t launch_simt_group(const GemmDesc* d_descs, int count, int tiles_total, int edge, int split,
+                              Scale* scales, unsigned* status, cudaStream_t s) {
+  if (edge == 64 && split == 2)
+    simt_group_split_kernel<<<2 * tiles_total, simt::THREADS, 0, s>>>(d_descs, count, scales, status);
+  else if (edge == 64)
     simt_group_kernel<64><<<tiles_total, simt::THREADS, 0, s>>>(d_descs, count, scales, status);
   else
     simt_group_kernel<128><<<tiles_total, simt::THREADS, 0, s>>>(d_descs, count, scales, status);

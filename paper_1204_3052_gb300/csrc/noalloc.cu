@@ -185,7 +185,7 @@ extern "C" matpow_status matpow_f32_noalloc(const float* dA, int N, uint64_t n, 
         t += tn * tn;
       }
       g.tiles_total = t;
-      CK(launch_simt_pair(g, edge, scales, status, s));
+      CK(launch_simt_pair(g, edge, 1, scales, status, s));
     }
     if (newRb >= 0) {
       refs[Rb]--;

@@ -395,7 +395,7 @@ static matpow_status run_step(matpow_server_s* s, std::vector<Req*>& act, uint64
                            s->d_maps, 64, fmt_slices(s->fmt), maxn_f, s->num_sms, true, s->scales, st0,
                            s->stream);
     else
-      e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, 128, s->scales, st0,
+      e = launch_simt_group((const GemmDesc*)(dd + o_f), (int)gf.size(), tiles_f, 128, 1, s->scales, st0,
                             s->stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "server: float level");
   }
